@@ -1,0 +1,402 @@
+"""Benchmark: edge-based median-dual nabla operators on O1280 x 137 levels.
+
+One step = the whole operator path on one synthetic batch: gradient of a
+scalar, divergence and curl of a wind, and the Laplacian of the scalar
+(gradient pass + divergence pass), FP32 storage and arithmetic with
+compensated accumulation, FP64 geometry.  Throughput is node-levels per
+second summed over the four operators.  Inputs (3.7 GB scalar, 7.4 GB wind)
+are far larger than the 126 MB L2, so no L2 flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample (a few levels of the same grid) with the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+OPS = ("grad", "div", "curl", "lap")
+METRIC = "Gnode-levels/s per nabla op (O1280x137, fp32 vs fp64), % HBM roofline; p99 ms"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--grid", type=int, default=1280)
+    p.add_argument("--nlev", type=int, default=137)
+    p.add_argument("--lmax", type=int, default=40)
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--fp64-steps", type=int, default=3)
+    p.add_argument("--cpu-levels", type=int, default=24,
+                   help="levels of the oracle's bounded CPU sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--variant", type=int, default=0, help="kernel variant (0 auto, 1 direct, 2 tiled)")
+    p.add_argument("--tile", type=int, default=0)
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for ln in open(self.path):
+                c = [x.strip() for x in ln.split(",")]
+                if len(c) < 9:
+                    continue
+                try:
+                    sm.append(float(c[1]))
+                    mx.append(float(c[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, c[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+            os.remove(self.path)
+        except Exception:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_bytes(op, V, E, L, elem):
+    """Bytes a launch must move at minimum: each input value read once, each
+    output written once, the connectivity and weights read once per node."""
+    P = 2 * E
+    if op == "grad":
+        return V * L * elem * (1 + 2) + (V + 1) * 4 + P * (4 + 2 * elem)
+    # div / curl: vector in, scalar out, plus per-node self weights
+    return V * L * elem * (2 + 1) + (V + 1) * 4 + P * (4 + 2 * elem) + V * 2 * elem
+
+
+# ------------------------------------------------------------- our arm
+
+def make_inputs(nabla, synth, grid, mesh, method, nlev, lmax, dtype, device):
+    import torch
+    ll = torch.as_tensor(grid.lonlat(), device=device)
+    perm = torch.as_tensor(mesh.permutation().astype("int64"), device=device)
+    lat, lon = ll[perm, 1].contiguous(), ll[perm, 0].contiguous()
+    fs = nabla.NodeColumns(method, nlev, dtype)
+    f = fs.create_field(device=device)
+    uv = fs.create_field(nvar=2, device=device)
+    basis = synth.scalar_basis(lat, lon, lmax, synth.BASE_SEED, device=device)
+    w = torch.as_tensor(synth.level_weights(nlev, synth.BASE_SEED + 1), device=device)
+    wb = synth.wind_basis(lat, lon, lmax, synth.BASE_SEED, method.radius, device=device)
+    ww = torch.as_tensor(synth.level_weights(nlev, synth.BASE_SEED + 2), device=device)
+    for k0 in range(0, nlev, 16):
+        k1 = min(nlev, k0 + 16)
+        f[:, k0:k1].copy_(basis @ w[k0:k1].T)
+        uv[:, k0:k1].copy_(torch.einsum("vbc,kb->vkc", wb, ww[k0:k1]))
+    del basis, wb
+    return fs, f, uv
+
+
+def run_step(nabla, method, f, uv, outs, scratch, stream, ev=None):
+    g, d, z, l = outs
+    if ev is not None:
+        ev[0].record(stream)
+    nabla.apply(method, "grad", f, g, stream=stream)
+    if ev is not None:
+        ev[1].record(stream)
+    nabla.apply(method, "div", uv, d, stream=stream)
+    if ev is not None:
+        ev[2].record(stream)
+    nabla.apply(method, "curl", uv, z, stream=stream)
+    if ev is not None:
+        ev[3].record(stream)
+    nabla.apply(method, "lap", f, l, scratch=scratch, stream=stream)
+    if ev is not None:
+        ev[4].record(stream)
+
+
+def bench_ours(a):
+    import torch
+    import torch.distributed as dist
+    from paper_1908_06091_b300 import nabla, synth
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    device = f"cuda:{local}"
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device(device))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    t0 = time.time()
+    grid = nabla.Grid(a.grid)
+    mesh = nabla.Mesh(grid, 1)
+    method = nabla.Method(mesh)
+    method.set_kernel(a.variant, a.tile)
+    setup_s = time.time() - t0
+    V, E, L = mesh.V, mesh.E, a.nlev
+    fs, f, uv = make_inputs(nabla, synth, grid, mesh, method, L, a.lmax, torch.float32, device)
+    outs = (fs.create_field(nvar=2, device=device), fs.create_field(device=device),
+            fs.create_field(device=device), fs.create_field(device=device))
+    scratch = fs.create_field(nvar=2, device=device)
+    stream = torch.cuda.Stream(device=device)
+    with torch.cuda.stream(stream):
+        for _ in range(max(a.warmup, 3)):
+            run_step(nabla, method, f, uv, outs, scratch, stream)
+    stream.synchronize()
+
+    # timed region: K steps, per-op CUDA events on the launching stream
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(a.steps)]
+    launches0 = nabla.launch_count()
+    barrier()
+    with Clocks(local) as clk:
+        start = torch.cuda.Event(enable_timing=True)
+        stop = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        with torch.cuda.stream(stream):
+            for k in range(a.steps):
+                run_step(nabla, method, f, uv, outs, scratch, stream, evs[k])
+        stop.record(stream)
+        stream.synchronize()
+    barrier()
+    launches = nabla.launch_count() - launches0
+    ms_total = start.elapsed_time(stop)
+    t_max = torch.tensor([ms_total], device=device)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    ms_total = float(t_max.item())
+    ms_step = ms_total / a.steps
+    per_op_ms = {op: statistics.median(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(a.steps))
+                 for i, op in enumerate(OPS)}
+    nl = V * L
+    value = world * 4 * nl * a.steps / (ms_total * 1e-3) / 1e9
+    hbm, peak_kind = peaks()
+    elem = 4
+    kern_ms = {"grad": per_op_ms["grad"], "div": per_op_ms["div"], "curl": per_op_ms["curl"]}
+    # the gradient and divergence kernels also form the two Laplacian passes
+    share = {"grad": 2 * kern_ms["grad"], "div": 2 * kern_ms["div"], "curl": kern_ms["curl"]}
+    dom = max(share, key=share.get)
+    algo = algorithmic_bytes(dom, V, E, L, elem)
+    achieved = algo / (kern_ms[dom] * 1e-3) / 1e9
+    per_op = {}
+    for op in OPS:
+        b = algorithmic_bytes(op, V, E, L, elem) if op != "lap" else \
+            algorithmic_bytes("grad", V, E, L, elem) + algorithmic_bytes("div", V, E, L, elem)
+        per_op[op] = {"ms": round(per_op_ms[op], 4), "gnl_s": round(nl / per_op_ms[op] / 1e6, 1),
+                      "algo_GBs": round(b / per_op_ms[op] / 1e6, 1),
+                      "frac_hbm": round(b / per_op_ms[op] / 1e6 / hbm, 3)}
+
+    # FP64 GPU path on the same workload (the plain reference GPU path)
+    fp64 = None
+    if a.fp64_steps > 0:
+        fs64 = nabla.NodeColumns(method, L, torch.float64)
+        f64 = fs64.create_field(device=device)
+        uv64 = fs64.create_field(nvar=2, device=device)
+        f64.copy_(f)
+        uv64.copy_(uv)
+        outs64 = (fs64.create_field(nvar=2, device=device), fs64.create_field(device=device),
+                  fs64.create_field(device=device), fs64.create_field(device=device))
+        scr64 = fs64.create_field(nvar=2, device=device)
+        with torch.cuda.stream(stream):
+            run_step(nabla, method, f64, uv64, outs64, scr64, stream)
+            ev64 = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(a.fp64_steps)]
+            for k in range(a.fp64_steps):
+                run_step(nabla, method, f64, uv64, outs64, scr64, stream, ev64[k])
+        stream.synchronize()
+        ms64 = {op: statistics.median(ev64[k][i].elapsed_time(ev64[k][i + 1]) for k in range(a.fp64_steps))
+                for i, op in enumerate(OPS)}
+        fp64 = {"ms_per_step": round(sum(ms64.values()), 3),
+                "value": round(4 * nl / (sum(ms64.values()) * 1e-3) / 1e9, 2),
+                "per_op": {op: {"ms": round(ms64[op], 3), "gnl_s": round(nl / ms64[op] / 1e6, 1)}
+                           for op in OPS}}
+        del f64, uv64, outs64, scr64
+        torch.cuda.empty_cache()
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    e2e = None
+    if a.e2e_steps > 0:
+        hf = f._base.cpu().pin_memory()
+        huv = uv._base.cpu().pin_memory()
+        hout = {op: torch.empty_like(o._base, device="cpu").pin_memory() for op, o in zip(OPS, outs)}
+        ins = {"grad": (hf, f), "div": (huv, uv), "curl": (huv, uv), "lap": (hf, f)}
+        h2d = sum(ins[op][0].numel() * ins[op][0].element_size() for op in OPS)
+        d2h = sum(hout[op].numel() * hout[op].element_size() for op in OPS)
+
+        def e2e_step():
+            for op, o in zip(OPS, outs):
+                hi, di = ins[op]
+                nabla.apply_host(method, op, hi, hout[op], di, o,
+                                 scratch=scratch if op == "lap" else None, stream=stream)
+        e2e_step()
+        barrier()
+        t1 = time.perf_counter()
+        for _ in range(a.e2e_steps):
+            e2e_step()
+        barrier()
+        dt = time.perf_counter() - t1
+        e2e = {"value": round(world * 4 * nl * a.e2e_steps / dt / 1e9, 3), "unit": "Gnode-levels/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "steps": a.e2e_steps}
+
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": "Gnode-levels/s",
+        "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic: seeded spherical-harmonic fields (degree<=40), levels mixed from 8 bases",
+        "config": {"workload": f"O{a.grid}x{L} grad+div+curl+lap FP32, compensated accumulation, FP64 geometry",
+                   "grid": f"O{a.grid}", "nodes": V, "edges": E, "levels": L, "level_stride": fs.lp,
+                   "ops_per_step": list(OPS), "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": f"replicas x{world} (independent fields per GPU)",
+                   "setup_s": round(setup_s, 2)},
+        "per_op": per_op,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
+                     "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                     "peak_kind": peak_kind, "algorithmic_bytes": int(algo), "traffic": None},
+        "fp64": fp64,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not a.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(a, samples=1)
+    if world > 1:
+        dist.destroy_process_group()
+    return line if rank == 0 else None
+
+
+# ---------------------------------------------------------- oracle timing
+
+def cpu_baseline(a, samples=1):
+    """The FP64 oracle (as it stands) on the host cores: all four operators
+    on the first `cpu_levels` levels of the same grid."""
+    import numpy as np
+    import oracle
+    from paper_1908_06091_b300 import synth
+    m = oracle.build_mesh(a.grid, oracle.EARTH_RADIUS_M)
+    L = a.cpu_levels
+    f = synth.scalar_field(m.lat, m.lon, L, a.lmax).numpy()
+    uv = synth.wind_field(m.lat, m.lon, L, a.lmax, m.R).numpy()
+    ts = []
+    for _ in range(samples):
+        t = time.perf_counter()
+        oracle.grad(m, f)
+        oracle.div(m, uv)
+        oracle.curl(m, uv)
+        oracle.lap(m, f)
+        ts.append(time.perf_counter() - t)
+    dt = statistics.median(ts)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": round(4 * m.V * L / dt / 1e9, 5), "unit": "Gnode-levels/s", "cores": cores,
+            "kind": "oracle", "seconds": round(dt, 2),
+            "sample": f"O{a.grid}, first {L} of {a.nlev} levels, grad+div+curl+lap, FP64 C + OpenMP"}
+
+
+def bench_reference(a):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return None
+    steps = []
+    import numpy as np
+    import oracle
+    from paper_1908_06091_b300 import synth
+    m = oracle.build_mesh(a.grid, oracle.EARTH_RADIUS_M)
+    L = max(1, min(a.cpu_levels, 8))
+    f = synth.scalar_field(m.lat, m.lon, L, a.lmax).numpy()
+    uv = synth.wind_field(m.lat, m.lon, L, a.lmax, m.R).numpy()
+
+    def step():
+        oracle.grad(m, f)
+        oracle.div(m, uv)
+        oracle.curl(m, uv)
+        oracle.lap(m, f)
+    for _ in range(a.warmup):
+        step()
+    t = time.perf_counter()
+    for _ in range(a.steps):
+        step()
+    dt = time.perf_counter() - t
+    value = 4 * m.V * L * a.steps / dt / 1e9
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = f"O{a.grid}, {L} of {a.nlev} levels per step, grad+div+curl+lap, FP64 C + OpenMP"
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "Gnode-levels/s",
+            "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": round(dt / a.steps * 1e3, 2), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"O{a.grid}x{a.nlev} grad+div+curl+lap (oracle sample: {L} levels)",
+                       "grid": f"O{a.grid}", "levels": a.nlev},
+            "cpu_baseline": {"value": round(value, 5), "unit": "Gnode-levels/s", "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 5), "unit": "Gnode-levels/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    a = parse()
+    line = bench_reference(a) if a.impl == "reference" else bench_ours(a)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,226 @@
+/*
+ * nabla_b300.h -- C ABI of the B300 (sm_103a) library for edge-based
+ * median-dual finite-volume nabla operators on octahedral reduced Gaussian
+ * grids.
+ *
+ * The calls follow the paper's concept chain (Sec. 1 Fig. 1-2, Sec. 4.7
+ * Listing 12): grid -> mesh -> method (median-dual geometry) ->
+ * functionspace (NodeColumns) -> field -> nabla operator.  Every C++ object
+ * sits behind a C function, as the paper's Fortran interface does
+ * (Sec. 4.1, Fig. 3).
+ *
+ * Conventions
+ *   - Every function returns an int status (NB_OK on success).  No C++
+ *     exception crosses this interface.  nb_last_error() returns a
+ *     thread-local, human-readable message for the last failing call of the
+ *     calling thread.
+ *   - Handles are opaque and reference counted.  A mesh keeps its grid alive,
+ *     a method its mesh, a functionspace its method.  *_release drops the
+ *     caller's reference; passing NULL is a no-op.
+ *   - The library owns mesh and geometry memory (host and device).  Field
+ *     memory is NEVER owned: an nb_field is a view of caller memory (for
+ *     example a torch tensor).  Outputs are preallocated by the caller.
+ *   - Operators are asynchronous on the caller's CUDA stream, passed as
+ *     `void *stream` (a cudaStream_t; NULL = the legacy default stream).
+ *   - Node order of fields is the functionspace (reordered) order, see
+ *     nb_mesh_permutation.  Layout is [node][level][var]: a vertical column
+ *     is contiguous (Sec. 4.5, Fig. 31) and vector fields carry their local
+ *     (east, north) components innermost (Listing 12: variables(2)).
+ *   - Sizes and strides are in elements, not bytes.
+ */
+#ifndef NABLA_B300_H
+#define NABLA_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+enum {
+  NB_OK = 0,
+  NB_EINVAL = 1,   /* bad handle, NULL pointer or out-of-range argument */
+  NB_ESHAPE = 2,   /* field shape, stride or alignment does not fit */
+  NB_EDTYPE = 3,   /* field dtype does not match the functionspace/op */
+  NB_EOOM = 4,     /* host or device allocation failed */
+  NB_ECUDA = 5,    /* a CUDA runtime call failed (message has the name) */
+  NB_ETIMEOUT = 6, /* a bounded device wait ran out */
+  NB_EBUDGET = 7   /* request exceeds the server's HBM budget */
+};
+
+typedef enum { NB_F32 = 0, NB_F64 = 1 } nb_dtype;
+
+typedef enum {
+  NB_OP_GRAD = 0, /* gradient:   scalar [V][L]    -> vector [V][L][2] */
+  NB_OP_DIV = 1,  /* divergence: vector [V][L][2] -> scalar [V][L]    */
+  NB_OP_CURL = 2, /* curl:       vector [V][L][2] -> scalar [V][L]    */
+  NB_OP_LAP = 3   /* Laplacian:  scalar [V][L]    -> scalar [V][L]    */
+} nb_op;
+
+typedef struct nb_grid nb_grid;
+typedef struct nb_mesh nb_mesh;
+typedef struct nb_method nb_method;
+typedef struct nb_fs nb_fs;
+
+/* A non-owning view of a field in device memory (Sec. 4.6, Fig. 32). */
+typedef struct nb_field {
+  void *data;          /* device pointer, caller owned */
+  int32_t dtype;       /* nb_dtype */
+  int32_t nvar;        /* 1 = scalar, 2 = (east, north) vector */
+  int64_t nnodes;      /* number of mesh nodes */
+  int32_t nlev;        /* number of vertical levels */
+  int32_t reserved;    /* zero */
+  int64_t node_stride; /* elements from one node's column to the next */
+  int64_t lev_stride;  /* elements from one level to the next; == nvar */
+} nb_field;
+
+/* Library version string, e.g. "nabla_b300 0.1.0 sm_103a". */
+const char *nb_version(void);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *nb_last_error(void);
+
+/* ------------------------------------------------------------------ grid */
+
+/* Octahedral reduced Gaussian grid O<N> (Sec. 4.2.3.7, Listing 6): 2N
+ * latitude rows on the roots of the Legendre polynomial of degree 2N
+ * (Sec. 4.2.3.5), row j holding 20 + 4j points counted from the nearer pole,
+ * the first point of every row at longitude 0.  N in [1, 8000].
+ * Errors: NB_EINVAL (N out of range or out == NULL), NB_EOOM. */
+int nb_grid_create_octahedral(int N, nb_grid **out);
+int nb_grid_release(nb_grid *grid);
+
+/* Number of grid points V = 4N^2 + 36N. */
+int nb_grid_size(const nb_grid *grid, int64_t *nodes);
+
+/* Gaussian number N of the grid. */
+int nb_grid_gaussian_number(const nb_grid *grid, int *N);
+
+/* Longitude and latitude in radians of every point, original grid order
+ * (rows north to south, points west to east; Sec. 4.2.3, Listing 5).
+ * lonlat: caller-owned host array [V][2] = (lon, lat). */
+int nb_grid_lonlat(const nb_grid *grid, double *lonlat);
+
+/* ------------------------------------------------------------------ mesh */
+
+/* Triangulate the grid (structured mesh generator, Sec. 4.3, Listing 7,
+ * Fig. 25b): row strips joined by an exact integer longitude merge, pole
+ * caps closed with no extra node, so F = 2V - 4 and E = 3V - 6.
+ * reorder: 0 keeps grid order, 1 renumbers nodes along a 3-D Hilbert curve
+ * for memory locality; in both the nodes of the first and last row come
+ * last (see nb_mesh_cap_begin).  Runs on the host, multi-threaded.
+ * Errors: NB_EINVAL, NB_EOOM. */
+int nb_mesh_create(const nb_grid *grid, int reorder, nb_mesh **out);
+int nb_mesh_release(nb_mesh *mesh);
+
+int nb_mesh_sizes(const nb_mesh *mesh, int64_t *nodes, int64_t *edges, int64_t *triangles);
+
+/* perm[new] = old: the grid index (global_index, Sec. 4.4) of every node in
+ * functionspace order.  perm: caller-owned host int32[V]. */
+int nb_mesh_permutation(const nb_mesh *mesh, int32_t *perm);
+
+/* Counter-clockwise triangles [F][3] in functionspace numbering (host). */
+int nb_mesh_triangles(const nb_mesh *mesh, int32_t *tri);
+
+/* Edges [E][2] (a < b, functionspace numbering) (host). */
+int nb_mesh_edges(const nb_mesh *mesh, int32_t *edge);
+
+/* First node of the pole-row block: nodes [cap_begin, V) are the nodes of
+ * the first and last grid rows, which the FP32 kernels treat in FP64. */
+int nb_mesh_cap_begin(const nb_mesh *mesh, int64_t *cap_begin);
+
+/* -------------------------------------------------------------- method */
+
+/* fvm::Method (Sec. 4.7): build the median-dual geometry of the mesh on a
+ * sphere of radius radius_m (FP64, host), upload it once to the current
+ * CUDA device and derive the per-edge operator weights there in FP64 (plus
+ * their FP32 roundings).  radius_m <= 0 selects 6.37122e6 m.
+ * Errors: NB_EINVAL, NB_EOOM, NB_ECUDA. */
+int nb_method_create(const nb_mesh *mesh, double radius_m, nb_method **out);
+int nb_method_release(nb_method *method);
+
+/* Dual volumes V_i (m^2), functionspace order, host double[V]. */
+int nb_method_dual_volumes(const nb_method *method, double *host_out);
+
+/* Device bytes held by the method (geometry, weights, tile plans). */
+int nb_method_device_bytes(const nb_method *method, int64_t *bytes);
+
+/* ------------------------------------------------------- functionspace */
+
+/* NodeColumns function space (Sec. 4.5): nlev levels of dtype.  Reports the
+ * padded level stride Lp that fields should use: nlev rounded up to a
+ * multiple of 4 (FP32) or 2 (FP64), so that every column starts on a
+ * 16-byte boundary.  Errors: NB_EINVAL (nlev < 1), NB_EDTYPE. */
+int nb_fs_nodecolumns(const nb_method *method, int nlev, nb_dtype dtype, nb_fs **out);
+int nb_fs_release(nb_fs *fs);
+int nb_fs_level_stride(const nb_fs *fs, int64_t *lp);
+
+/* Fill an nb_field view of caller memory for this functionspace.
+ * nvar 1 or 2.  node_stride >= nlev * nvar, lev_stride == nvar.
+ * Errors: NB_EINVAL, NB_ESHAPE. */
+int nb_field_view(const nb_fs *fs, void *dev_ptr, int nvar, int64_t node_stride,
+                  int64_t lev_stride, nb_field *out);
+
+/* --------------------------------------------------------- operators
+ * fvm::Nabla (Sec. 4.7, Fig. 33, Listing 12).  In and out must have the
+ * same dtype, node count and level count; out must not alias in.  FP64
+ * fields run the FP64 kernels; FP32 fields run FP32 arithmetic with
+ * compensated per-node accumulation and FP64 for the pole-row nodes.
+ * Errors (before any launch): NB_EINVAL, NB_ESHAPE, NB_EDTYPE;
+ * NB_ECUDA if the launch fails. */
+
+/* Gradient, horizontal components only (Listing 12): f [V][L] -> g [V][L][2]
+ * in 1/m times f's unit, (east, north). */
+int nb_nabla_gradient(const nb_method *method, const nb_field *f, const nb_field *g, void *stream);
+
+/* Divergence of a (east, north) vector field: uv [V][L][2] -> d [V][L]. */
+int nb_nabla_divergence(const nb_method *method, const nb_field *uv, const nb_field *d,
+                        void *stream);
+
+/* Vertical curl (vorticity, positive counter-clockwise seen from outside):
+ * uv [V][L][2] -> z [V][L]. */
+int nb_nabla_curl(const nb_method *method, const nb_field *uv, const nb_field *z, void *stream);
+
+/* Laplacian = divergence of the gradient: f [V][L] -> lap [V][L].
+ * scratch: a [V][L][2] field of f's dtype receiving the intermediate
+ * gradient, or NULL to let the library take stream-ordered memory from the
+ * CUDA default pool for the call. */
+int nb_nabla_laplacian(const nb_method *method, const nb_field *f, const nb_field *lap,
+                       const nb_field *scratch, void *stream);
+
+/* Generic entry: op is an nb_op; for NB_OP_LAP scratch may be NULL. */
+int nb_nabla_apply(const nb_method *method, int op, const nb_field *in, const nb_field *out,
+                   const nb_field *scratch, void *stream);
+
+/* End-to-end call on HOST buffers: copy host_in (laid out exactly like
+ * dev_in, node_stride included) to dev_in, apply op, copy dev_out back to
+ * host_out and wait for the stream.  Pinned host memory gives full link
+ * bandwidth.  dev_in/dev_out are caller-owned device fields. */
+int nb_nabla_apply_host(const nb_method *method, int op, const void *host_in, void *host_out,
+                        const nb_field *dev_in, const nb_field *dev_out,
+                        const nb_field *scratch, void *stream);
+
+/* ------------------------------------------------------ kernel control */
+
+/* Kernel variant used for a call: NB_KERNEL_AUTO lets the library choose
+ * (tuned table, else a size heuristic). */
+enum { NB_KERNEL_AUTO = 0, NB_KERNEL_DIRECT = 1, NB_KERNEL_TILED = 2 };
+
+/* Force a kernel variant for subsequent calls on this method (tests and
+ * tuning).  tile_nodes is the tiled variant's nodes per tile (0 = default). */
+int nb_method_set_kernel(nb_method *method, int variant, int tile_nodes);
+
+/* Accumulation mode of the FP32 path: 1 = compensated (Kahan, default),
+ * 0 = plain FP32 FMA chain (for accuracy/throughput comparison). */
+int nb_method_set_compensated(nb_method *method, int on);
+
+/* Number of this library's kernel launches since load (all devices). */
+int nb_launch_count(int64_t *count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NABLA_B300_H */

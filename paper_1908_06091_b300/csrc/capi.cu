@@ -1,0 +1,447 @@
+// capi.cu -- extern "C" boundary of the library (declared in
+// include/nabla_b300.h): handle lifetimes, argument validation and the
+// dispatch of each nabla operator to its kernels.  No C++ exception crosses
+// this file's functions.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <stdexcept>
+#include <string>
+
+#include "internal.h"
+#include "kernels_common.cuh"
+
+namespace nb {
+
+static thread_local std::string t_last_error;
+void set_error(const std::string &msg) { t_last_error = msg; }
+
+int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, cudaStream_t st,
+                 bool *handled);
+
+}  // namespace nb
+
+nb_method::~nb_method() {
+  nb::method_free_device(this);
+  nb::release(mesh);
+}
+
+using nb::set_error;
+
+#define NB_GUARD_BEGIN try {
+#define NB_GUARD_END                                      \
+  }                                                       \
+  catch (const std::bad_alloc &) {                        \
+    set_error("host allocation failed");                  \
+    return NB_EOOM;                                       \
+  }                                                       \
+  catch (const std::exception &ex) {                      \
+    set_error(ex.what());                                 \
+    return NB_EINVAL;                                     \
+  }                                                       \
+  catch (...) {                                           \
+    set_error("unknown C++ exception");                   \
+    return NB_EINVAL;                                     \
+  }
+
+#define NB_REQUIRE(cond, code, msg) \
+  do {                              \
+    if (!(cond)) {                  \
+      set_error(msg);               \
+      return code;                  \
+    }                               \
+  } while (0)
+
+extern "C" {
+
+const char *nb_version(void) { return "nabla_b300 0.1.0 sm_103a"; }
+
+const char *nb_last_error(void) { return nb::t_last_error.c_str(); }
+
+int nb_launch_count(int64_t *count) {
+  NB_REQUIRE(count, NB_EINVAL, "nb_launch_count: NULL");
+  *count = nb::launch_count();
+  return NB_OK;
+}
+
+// ------------------------------------------------------------------ grid
+
+int nb_grid_create_octahedral(int N, nb_grid **out) {
+  NB_REQUIRE(out, NB_EINVAL, "nb_grid_create_octahedral: out is NULL");
+  NB_REQUIRE(N >= 1 && N <= 8000, NB_EINVAL, "nb_grid_create_octahedral: N must be in [1, 8000]");
+  NB_GUARD_BEGIN
+  *out = nb::build_grid(N);
+  return NB_OK;
+  NB_GUARD_END
+}
+
+int nb_grid_release(nb_grid *g) {
+  nb::release(g);
+  return NB_OK;
+}
+
+int nb_grid_size(const nb_grid *g, int64_t *nodes) {
+  NB_REQUIRE(g && nodes, NB_EINVAL, "nb_grid_size: NULL argument");
+  *nodes = g->V;
+  return NB_OK;
+}
+
+int nb_grid_gaussian_number(const nb_grid *g, int *N) {
+  NB_REQUIRE(g && N, NB_EINVAL, "nb_grid_gaussian_number: NULL argument");
+  *N = g->N;
+  return NB_OK;
+}
+
+int nb_grid_lonlat(const nb_grid *g, double *lonlat) {
+  NB_REQUIRE(g && lonlat, NB_EINVAL, "nb_grid_lonlat: NULL argument");
+  const double pi = 3.14159265358979323846;
+  for (int j = 0; j < 2 * g->N; ++j) {
+    const double phi = std::asin(g->mu[j]);
+    for (int i = 0; i < g->nx[j]; ++i) {
+      const int64_t id = g->row_off[j] + i;
+      lonlat[2 * id] = 2.0 * pi * (double)i / (double)g->nx[j];
+      lonlat[2 * id + 1] = phi;
+    }
+  }
+  return NB_OK;
+}
+
+// ------------------------------------------------------------------ mesh
+
+int nb_mesh_create(const nb_grid *g, int reorder, nb_mesh **out) {
+  NB_REQUIRE(g && out, NB_EINVAL, "nb_mesh_create: NULL argument");
+  NB_REQUIRE(reorder == 0 || reorder == 1, NB_EINVAL, "nb_mesh_create: reorder must be 0 or 1");
+  NB_GUARD_BEGIN
+  *out = nb::build_mesh(const_cast<nb_grid *>(g), reorder);
+  return NB_OK;
+  NB_GUARD_END
+}
+
+int nb_mesh_release(nb_mesh *m) {
+  nb::release(m);
+  return NB_OK;
+}
+
+int nb_mesh_sizes(const nb_mesh *m, int64_t *nodes, int64_t *edges, int64_t *tris) {
+  NB_REQUIRE(m, NB_EINVAL, "nb_mesh_sizes: NULL mesh");
+  if (nodes) *nodes = m->V;
+  if (edges) *edges = m->E;
+  if (tris) *tris = m->F;
+  return NB_OK;
+}
+
+int nb_mesh_permutation(const nb_mesh *m, int32_t *perm) {
+  NB_REQUIRE(m && perm, NB_EINVAL, "nb_mesh_permutation: NULL argument");
+  std::memcpy(perm, m->perm.data(), sizeof(int32_t) * m->V);
+  return NB_OK;
+}
+
+int nb_mesh_triangles(const nb_mesh *m, int32_t *tri) {
+  NB_REQUIRE(m && tri, NB_EINVAL, "nb_mesh_triangles: NULL argument");
+  std::memcpy(tri, m->tri.data(), sizeof(int32_t) * 3 * m->F);
+  return NB_OK;
+}
+
+int nb_mesh_edges(const nb_mesh *m, int32_t *edge) {
+  NB_REQUIRE(m && edge, NB_EINVAL, "nb_mesh_edges: NULL argument");
+  std::memcpy(edge, m->edge.data(), sizeof(int32_t) * 2 * m->E);
+  return NB_OK;
+}
+
+int nb_mesh_cap_begin(const nb_mesh *m, int64_t *cap_begin) {
+  NB_REQUIRE(m && cap_begin, NB_EINVAL, "nb_mesh_cap_begin: NULL argument");
+  *cap_begin = m->cap_begin;
+  return NB_OK;
+}
+
+// ---------------------------------------------------------------- method
+
+int nb_method_create(const nb_mesh *mesh, double radius_m, nb_method **out) {
+  NB_REQUIRE(mesh && out, NB_EINVAL, "nb_method_create: NULL argument");
+  NB_GUARD_BEGIN
+  auto *m = new nb_method();
+  m->mesh = nb::retain(const_cast<nb_mesh *>(mesh));
+  m->R = radius_m > 0 ? radius_m : 6.37122e6;
+  nb::build_geometry(mesh, m->R, m->vol, m->S, m->T, m->east, m->north);
+  const int st = nb::method_upload(m);
+  if (st != NB_OK) {
+    nb::release(m);
+    return st;
+  }
+  *out = m;
+  return NB_OK;
+  NB_GUARD_END
+}
+
+int nb_method_release(nb_method *m) {
+  nb::release(m);
+  return NB_OK;
+}
+
+int nb_method_dual_volumes(const nb_method *m, double *host_out) {
+  NB_REQUIRE(m && host_out, NB_EINVAL, "nb_method_dual_volumes: NULL argument");
+  std::memcpy(host_out, m->vol.data(), sizeof(double) * m->vol.size());
+  return NB_OK;
+}
+
+int nb_method_device_bytes(const nb_method *m, int64_t *bytes) {
+  NB_REQUIRE(m && bytes, NB_EINVAL, "nb_method_device_bytes: NULL argument");
+  int64_t b = m->device_bytes;
+  for (auto &kv : m->plans) b += kv.second->bytes;
+  *bytes = b;
+  return NB_OK;
+}
+
+int nb_method_set_kernel(nb_method *m, int variant, int tile_nodes) {
+  NB_REQUIRE(m, NB_EINVAL, "nb_method_set_kernel: NULL method");
+  NB_REQUIRE(variant >= NB_KERNEL_AUTO && variant <= NB_KERNEL_TILED, NB_EINVAL,
+             "nb_method_set_kernel: unknown variant");
+  NB_REQUIRE(tile_nodes == 0 || (tile_nodes >= 8 && tile_nodes <= 1024), NB_EINVAL,
+             "nb_method_set_kernel: tile_nodes must be 0 or in [8, 1024]");
+  m->kernel_variant = variant;
+  m->tile_nodes = tile_nodes;
+  return NB_OK;
+}
+
+int nb_method_set_compensated(nb_method *m, int on) {
+  NB_REQUIRE(m, NB_EINVAL, "nb_method_set_compensated: NULL method");
+  m->compensated = on ? 1 : 0;
+  return NB_OK;
+}
+
+// --------------------------------------------------------- functionspace
+
+int nb_fs_nodecolumns(const nb_method *m, int nlev, nb_dtype dtype, nb_fs **out) {
+  NB_REQUIRE(m && out, NB_EINVAL, "nb_fs_nodecolumns: NULL argument");
+  NB_REQUIRE(nlev >= 1 && nlev <= 65536, NB_EINVAL, "nb_fs_nodecolumns: nlev must be in [1, 65536]");
+  NB_REQUIRE(dtype == NB_F32 || dtype == NB_F64, NB_EDTYPE, "nb_fs_nodecolumns: dtype must be NB_F32 or NB_F64");
+  NB_GUARD_BEGIN
+  auto *fs = new nb_fs();
+  fs->method = nb::retain(const_cast<nb_method *>(m));
+  fs->nlev = nlev;
+  fs->dtype = dtype;
+  const int q = dtype == NB_F32 ? 4 : 2;
+  fs->lp = (int64_t)((nlev + q - 1) / q) * q;
+  *out = fs;
+  return NB_OK;
+  NB_GUARD_END
+}
+
+int nb_fs_release(nb_fs *fs) {
+  nb::release(fs);
+  return NB_OK;
+}
+
+int nb_fs_level_stride(const nb_fs *fs, int64_t *lp) {
+  NB_REQUIRE(fs && lp, NB_EINVAL, "nb_fs_level_stride: NULL argument");
+  *lp = fs->lp;
+  return NB_OK;
+}
+
+int nb_field_view(const nb_fs *fs, void *dev_ptr, int nvar, int64_t node_stride,
+                  int64_t lev_stride, nb_field *out) {
+  NB_REQUIRE(fs && out, NB_EINVAL, "nb_field_view: NULL argument");
+  NB_REQUIRE(dev_ptr || fs->method->mesh->V == 0, NB_EINVAL, "nb_field_view: NULL data");
+  NB_REQUIRE(nvar == 1 || nvar == 2, NB_EINVAL, "nb_field_view: nvar must be 1 or 2");
+  NB_REQUIRE(lev_stride == nvar, NB_ESHAPE, "nb_field_view: lev_stride must equal nvar");
+  NB_REQUIRE(node_stride >= (int64_t)fs->nlev * nvar, NB_ESHAPE,
+             "nb_field_view: node_stride < nlev * nvar");
+  out->data = dev_ptr;
+  out->dtype = fs->dtype;
+  out->nvar = nvar;
+  out->nnodes = fs->method->mesh->V;
+  out->nlev = fs->nlev;
+  out->reserved = 0;
+  out->node_stride = node_stride;
+  out->lev_stride = lev_stride;
+  return NB_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------- operators
+
+namespace nb {
+
+static int check_field(const nb_method *m, const nb_field *f, int nvar, const char *what) {
+  if (!f) {
+    set_error(std::string(what) + ": field is NULL");
+    return NB_EINVAL;
+  }
+  if (!f->data && m->mesh->V > 0) {
+    set_error(std::string(what) + ": field data is NULL");
+    return NB_EINVAL;
+  }
+  if (f->dtype != NB_F32 && f->dtype != NB_F64) {
+    set_error(std::string(what) + ": unknown dtype");
+    return NB_EDTYPE;
+  }
+  if (f->nvar != nvar) {
+    set_error(std::string(what) + ": expected nvar = " + std::to_string(nvar));
+    return NB_ESHAPE;
+  }
+  if (f->nnodes != m->mesh->V) {
+    set_error(std::string(what) + ": node count differs from the mesh");
+    return NB_ESHAPE;
+  }
+  if (f->nlev < 1 || f->lev_stride != nvar || f->node_stride < (int64_t)f->nlev * nvar) {
+    set_error(std::string(what) + ": bad level count or strides");
+    return NB_ESHAPE;
+  }
+  const int64_t elem = f->dtype == NB_F64 ? 8 : 4;
+  if (((uintptr_t)f->data) % elem) {
+    set_error(std::string(what) + ": data not aligned to its element size");
+    return NB_ESHAPE;
+  }
+  return NB_OK;
+}
+
+static int validate(const nb_method *m, int op, const nb_field *in, const nb_field *out,
+                    const nb_field *scratch) {
+  if (!m) {
+    set_error("nabla: method is NULL");
+    return NB_EINVAL;
+  }
+  if (op < NB_OP_GRAD || op > NB_OP_LAP) {
+    set_error("nabla: unknown op");
+    return NB_EINVAL;
+  }
+  const int nin = (op == NB_OP_DIV || op == NB_OP_CURL) ? 2 : 1;
+  const int nout = op == NB_OP_GRAD ? 2 : 1;
+  int st = check_field(m, in, nin, "nabla input");
+  if (st) return st;
+  if ((st = check_field(m, out, nout, "nabla output"))) return st;
+  if (in->dtype != out->dtype) {
+    set_error("nabla: input and output dtypes differ");
+    return NB_EDTYPE;
+  }
+  if (in->nlev != out->nlev) {
+    set_error("nabla: input and output level counts differ");
+    return NB_ESHAPE;
+  }
+  const int64_t elem = in->dtype == NB_F64 ? 8 : 4;
+  auto span = [&](const nb_field *f) {
+    const char *b = static_cast<const char *>(f->data);
+    return std::make_pair(b, b + ((f->nnodes - 1) * f->node_stride + (int64_t)f->nlev * f->nvar) * elem);
+  };
+  auto overlap = [&](const nb_field *a, const nb_field *b) {
+    auto x = span(a), y = span(b);
+    return x.first < y.second && y.first < x.second;
+  };
+  if (m->mesh->V > 0 && overlap(in, out)) {
+    set_error("nabla: output aliases input");
+    return NB_EINVAL;
+  }
+  if (op == NB_OP_LAP && scratch) {
+    if ((st = check_field(m, scratch, 2, "laplacian scratch"))) return st;
+    if (scratch->dtype != in->dtype || scratch->nlev != in->nlev) {
+      set_error("laplacian scratch: dtype or level count differs from input");
+      return NB_ESHAPE;
+    }
+    if (overlap(scratch, in) || overlap(scratch, out)) {
+      set_error("laplacian scratch aliases input or output");
+      return NB_EINVAL;
+    }
+  }
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != m->device) {
+    set_error("nabla: current CUDA device differs from the method's device");
+    return NB_EINVAL;
+  }
+  return NB_OK;
+}
+
+// One of grad, div, curl on the chosen kernel variant.
+static int launch_single(nb_method *m, int op, const nb_field *in, const nb_field *out,
+                         cudaStream_t st) {
+  if (m->kernel_variant != NB_KERNEL_DIRECT) {
+    bool handled = false;
+    const int rc = launch_tiled(m, op, in, out, st, &handled);
+    if (handled || rc != NB_OK) return rc;
+  }
+  return launch_direct(m, op, in, out, st);
+}
+
+int launch_op(nb_method *m, int op, const nb_field *in, const nb_field *out,
+              const nb_field *scratch, void *stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (m->mesh->V == 0) return NB_OK;
+  if (op != NB_OP_LAP) return launch_single(m, op, in, out, st);
+  // Laplacian: gradient into scratch, then the divergence of it
+  nb_field tmp;
+  void *owned = nullptr;
+  if (scratch) {
+    tmp = *scratch;
+  } else {
+    const int64_t elem = in->dtype == NB_F64 ? 8 : 4;
+    const int q = in->dtype == NB_F64 ? 2 : 4;
+    const int64_t stride = 2 * (int64_t)((in->nlev + q - 1) / q) * q;
+    NB_CUDA(cudaMallocAsync(&owned, (size_t)(stride * in->nnodes * elem), st));
+    tmp = *in;
+    tmp.data = owned;
+    tmp.nvar = 2;
+    tmp.node_stride = stride;
+    tmp.lev_stride = 2;
+  }
+  int rc = launch_single(m, NB_OP_GRAD, in, &tmp, st);
+  if (rc == NB_OK) rc = launch_single(m, NB_OP_DIV, &tmp, out, st);
+  if (owned) {
+    const cudaError_t e = cudaFreeAsync(owned, st);
+    if (rc == NB_OK && e != cudaSuccess) rc = cuda_fail(e, "cudaFreeAsync");
+  }
+  return rc;
+}
+
+}  // namespace nb
+
+extern "C" {
+
+int nb_nabla_apply(const nb_method *m, int op, const nb_field *in, const nb_field *out,
+                   const nb_field *scratch, void *stream) {
+  const int st = nb::validate(m, op, in, out, scratch);
+  if (st != NB_OK) return st;
+  NB_GUARD_BEGIN
+  return nb::launch_op(const_cast<nb_method *>(m), op, in, out, scratch, stream);
+  NB_GUARD_END
+}
+
+int nb_nabla_gradient(const nb_method *m, const nb_field *f, const nb_field *g, void *stream) {
+  return nb_nabla_apply(m, NB_OP_GRAD, f, g, nullptr, stream);
+}
+
+int nb_nabla_divergence(const nb_method *m, const nb_field *uv, const nb_field *d, void *stream) {
+  return nb_nabla_apply(m, NB_OP_DIV, uv, d, nullptr, stream);
+}
+
+int nb_nabla_curl(const nb_method *m, const nb_field *uv, const nb_field *z, void *stream) {
+  return nb_nabla_apply(m, NB_OP_CURL, uv, z, nullptr, stream);
+}
+
+int nb_nabla_laplacian(const nb_method *m, const nb_field *f, const nb_field *lap,
+                       const nb_field *scratch, void *stream) {
+  return nb_nabla_apply(m, NB_OP_LAP, f, lap, scratch, stream);
+}
+
+int nb_nabla_apply_host(const nb_method *m, int op, const void *host_in, void *host_out,
+                        const nb_field *dev_in, const nb_field *dev_out,
+                        const nb_field *scratch, void *stream) {
+  NB_REQUIRE(host_in && host_out, NB_EINVAL, "nb_nabla_apply_host: NULL host buffer");
+  int st = nb::validate(m, op, dev_in, dev_out, scratch);
+  if (st != NB_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t elem = dev_in->dtype == NB_F64 ? 8 : 4;
+  const size_t bin = (size_t)(dev_in->nnodes * dev_in->node_stride * elem);
+  const size_t bout = (size_t)(dev_out->nnodes * dev_out->node_stride * elem);
+  NB_CUDA(cudaMemcpyAsync(dev_in->data, host_in, bin, cudaMemcpyHostToDevice, s));
+  NB_GUARD_BEGIN
+  st = nb::launch_op(const_cast<nb_method *>(m), op, dev_in, dev_out, scratch, stream);
+  NB_GUARD_END
+  if (st != NB_OK) return st;
+  NB_CUDA(cudaMemcpyAsync(host_out, dev_out->data, bout, cudaMemcpyDeviceToHost, s));
+  NB_CUDA(cudaStreamSynchronize(s));
+  return NB_OK;
+}
+
+}  // extern "C"

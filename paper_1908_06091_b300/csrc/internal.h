@@ -1,0 +1,138 @@
+// internal.h -- library-private types shared by the host builder, the CUDA
+// kernels and the C ABI implementation.
+#pragma once
+
+#include <atomic>
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/nabla_b300.h"
+
+namespace nb {
+
+void set_error(const std::string &msg);
+
+// Intrusive reference count shared by every handle type.
+struct RefCounted {
+  std::atomic<int> refs{1};
+  virtual ~RefCounted() = default;
+};
+template <class T>
+inline T *retain(T *p) {
+  if (p) p->refs.fetch_add(1);
+  return p;
+}
+template <class T>
+inline void release(T *p) {
+  if (p && p->refs.fetch_sub(1) == 1) delete p;
+}
+
+}  // namespace nb
+
+// Octahedral reduced Gaussian grid (Sec. 4.2.3.7).
+struct nb_grid : nb::RefCounted {
+  int N = 0;
+  int64_t V = 0;
+  std::vector<int32_t> nx;       // points per row, 2N rows north to south
+  std::vector<int64_t> row_off;  // first grid index of each row, 2N+1
+  std::vector<double> mu;        // sin(latitude) of each row (Legendre roots)
+};
+
+// Triangulated mesh in functionspace numbering.
+struct nb_mesh : nb::RefCounted {
+  nb_grid *grid = nullptr;
+  int64_t V = 0, E = 0, F = 0;
+  int64_t cap_begin = 0;             // nodes [cap_begin, V) are pole-row nodes
+  std::vector<int32_t> perm;         // new -> old (grid index)
+  std::vector<int32_t> iperm;        // old -> new
+  std::vector<double> xyz;           // [V][3] unit position, new order
+  std::vector<double> lat, lon;      // per node, new order
+  std::vector<int32_t> tri;          // [F][3] CCW, new numbering
+  // node -> neighbour CSR, neighbours ascending
+  std::vector<int64_t> row_ptr;      // V+1
+  std::vector<int32_t> nbr;          // 2E neighbour node
+  std::vector<int32_t> nbr_edge;     // 2E edge id
+  std::vector<int32_t> nbr_left;     // 2E triangle left of (i -> j)
+  std::vector<int32_t> nbr_right;    // 2E triangle right of (i -> j)
+  std::vector<int32_t> edge;         // [E][2] a < b
+  std::vector<int32_t> edge_tri;     // [E][2] (left, right) of a -> b
+  ~nb_mesh() override { nb::release(grid); }
+};
+
+// Per-tile halo plan of the tiled kernels for one tile size.
+struct TilePlan {
+  int tile_nodes = 0;
+  int ntiles = 0;
+  int ntiles_main = 0;               // tiles before the pole block
+  int max_halo = 0;
+  int max_entries = 0;
+  int64_t bytes = 0;
+  int32_t *d_tile_node0 = nullptr;   // ntiles+1: tile t = [node0[t], node0[t+1])
+  int32_t *d_halo_ptr = nullptr;     // ntiles+1
+  int32_t *d_halo = nullptr;         // halo node ids
+  uint16_t *d_lnbr = nullptr;        // 2E: shared-memory row of each CSR neighbour
+};
+
+// fvm::Method: geometry and operator weights resident on one device.
+struct nb_method : nb::RefCounted {
+  nb_mesh *mesh = nullptr;
+  double R = 0;
+  int device = 0;
+  std::vector<double> vol;          // [V]
+  std::vector<double> S, T;         // [E][3]
+  std::vector<double> east, north;  // [V][3]
+  // device: connectivity
+  int32_t *d_row_ptr = nullptr;     // V+1 (2E < 2^31 for N <= 8000)
+  int32_t *d_nbr = nullptr;         // 2E
+  int32_t *d_nbr_edge = nullptr;    // 2E
+  // device: FP64 raw geometry
+  double *d_vol = nullptr, *d_S = nullptr, *d_T = nullptr, *d_east = nullptr, *d_north = nullptr;
+  // device: per CSR entry operator weights (FP64 and FP32 rounding)
+  //   grad: (gx, gy); div: (du, dv); curl: (cu, cv); per node self (su, sv), (tu, tv)
+  double *d_wgrad64 = nullptr, *d_wdiv64 = nullptr, *d_wcurl64 = nullptr;
+  double *d_sdiv64 = nullptr, *d_scurl64 = nullptr;
+  float *d_wgrad32 = nullptr, *d_wdiv32 = nullptr, *d_wcurl32 = nullptr;
+  float *d_sdiv32 = nullptr, *d_scurl32 = nullptr;
+  int64_t device_bytes = 0;
+  // kernel control
+  int kernel_variant = 0;  // NB_KERNEL_*
+  int tile_nodes = 0;
+  int compensated = 1;
+  std::mutex plan_mu;
+  std::map<int, std::unique_ptr<TilePlan>> plans;
+  ~nb_method() override;
+};
+
+struct nb_fs : nb::RefCounted {
+  nb_method *method = nullptr;
+  int nlev = 0;
+  nb_dtype dtype = NB_F32;
+  int64_t lp = 0;
+  ~nb_fs() override { nb::release(method); }
+};
+
+namespace nb {
+
+// host builders (host_mesh.cpp)
+nb_grid *build_grid(int N);
+nb_mesh *build_mesh(nb_grid *grid, int reorder);
+void build_geometry(const nb_mesh *m, double R, std::vector<double> &vol, std::vector<double> &S,
+                    std::vector<double> &T, std::vector<double> &east, std::vector<double> &north);
+// host side of a tile plan: node0[ntiles+1], halo_ptr[ntiles+1], halo[], lnbr[2E]
+void build_tile_plan_host(const nb_mesh *m, int tile_nodes, std::vector<int32_t> &node0,
+                          std::vector<int32_t> &halo_ptr, std::vector<int32_t> &halo,
+                          std::vector<uint16_t> &lnbr, int &max_halo, int &max_entries,
+                          int &ntiles_main);
+
+// device side (nabla_kernels.cu)
+int method_upload(nb_method *m);            // returns NB_* status
+void method_free_device(nb_method *m);
+int launch_op(nb_method *m, int op, const nb_field *in, const nb_field *out,
+              const nb_field *scratch, void *stream);
+int64_t launch_count();
+
+}  // namespace nb

@@ -1,0 +1,494 @@
+// nabla_kernels.cu -- sm_103a kernels of the edge-based median-dual nabla
+// operators (Sec. 4.7, Fig. 33, Listing 12) and the device side of the
+// fvm::Method (geometry upload and FP64 weight setup).
+//
+// Discretisation (one level; sums over the edges e = (i, j) at node i, with
+// S_e^(i), T_e^(i) the face normal / tangent integrals seen from i and V_i
+// the dual volume):
+//   grad  G_i = (1/V_i) sum 1/2 (f_j - f_i) S_e^(i)      -> (G.e_i, G.n_i)
+//   div   D_i = (1/V_i) sum 1/2 (W_i + W_j) . S_e^(i)    W = u e + v n
+//   curl  Z_i = (1/V_i) sum 1/2 (W_i + W_j) . T_e^(i)
+//   lap   L_i = div(grad f)_i
+// The weights are projected once per method in FP64 on the device:
+//   grad  (gx, gy)_p = 1/2 S.(e_i, n_i) / V_i
+//   div   (du, dv)_p = 1/2 S.(e_j, n_j) / V_i,
+//         self (su, sv)_i = sum_p 1/2 S.(e_i + e_j, n_i + n_j) / V_i
+//   curl  the same with T,
+// so that div and curl are evaluated in difference form,
+//   D_i = sum_p du_p (u_j - u_i) + dv_p (v_j - v_i) + su_i u_i + sv_i v_i,
+// algebraically the flux form, but with every FP32 term of the size of the
+// result (no cancellation between large edge fluxes).  Pole-row nodes, whose
+// cap chords join nodes with nearly opposite local frames, are evaluated in
+// FP64 inside the FP32 kernels.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "internal.h"
+#include "kernels_common.cuh"
+
+namespace nb {
+
+static std::atomic<int64_t> g_launches{0};
+int64_t launch_count() { return g_launches.load(); }
+void count_launch(int n) { g_launches.fetch_add(n); }
+
+int cuda_fail(cudaError_t e, const char *what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return NB_ECUDA;
+}
+
+// ------------------------------------------------------------ weight setup
+
+// One thread per node: project the FP64 face integrals onto the local frames
+// and divide by the dual volume (all in FP64), then round to FP32.
+__global__ void __launch_bounds__(256) setup_weights_kernel(
+    int64_t V, const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ nbr,
+    const int32_t *__restrict__ nbr_edge, const double *__restrict__ vol,
+    const double *__restrict__ S, const double *__restrict__ T, const double *__restrict__ east,
+    const double *__restrict__ north, double2 *wgrad64, double2 *wdiv64, double2 *wcurl64,
+    double2 *sdiv64, double2 *scurl64, float2 *wgrad32, float2 *wdiv32, float2 *wcurl32,
+    float2 *sdiv32, float2 *scurl32) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= V) return;
+  const double h = 0.5 / vol[i];
+  const double ei[3] = {east[3 * i], east[3 * i + 1], east[3 * i + 2]};
+  const double ni[3] = {north[3 * i], north[3 * i + 1], north[3 * i + 2]};
+  double su = 0, sv = 0, tu = 0, tv = 0;
+  for (int32_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) {
+    const int32_t j = nbr[p], e = nbr_edge[p];
+    const double sg = (i < j) ? h : -h;  // S_e, T_e are stored as seen from the lower id
+    const double s[3] = {sg * S[3 * e], sg * S[3 * e + 1], sg * S[3 * e + 2]};
+    const double t[3] = {sg * T[3 * e], sg * T[3 * e + 1], sg * T[3 * e + 2]};
+    const double ej[3] = {east[3 * j], east[3 * j + 1], east[3 * j + 2]};
+    const double nj[3] = {north[3 * j], north[3 * j + 1], north[3 * j + 2]};
+    auto dot = [](const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; };
+    const double gx = dot(s, ei), gy = dot(s, ni);
+    const double du = dot(s, ej), dv = dot(s, nj);
+    const double cu = dot(t, ej), cv = dot(t, nj);
+    su += du + gx;
+    sv += dv + gy;
+    tu += cu + dot(t, ei);
+    tv += cv + dot(t, ni);
+    wgrad64[p] = make_double2(gx, gy);
+    wdiv64[p] = make_double2(du, dv);
+    wcurl64[p] = make_double2(cu, cv);
+    wgrad32[p] = make_float2((float)gx, (float)gy);
+    wdiv32[p] = make_float2((float)du, (float)dv);
+    wcurl32[p] = make_float2((float)cu, (float)cv);
+  }
+  sdiv64[i] = make_double2(su, sv);
+  scurl64[i] = make_double2(tu, tv);
+  sdiv32[i] = make_float2((float)su, (float)sv);
+  scurl32[i] = make_float2((float)tu, (float)tv);
+}
+
+template <class T>
+static int dev_upload(T **dst, const void *src, size_t n, int64_t &bytes) {
+  NB_CUDA(cudaMalloc((void **)dst, n * sizeof(T)));
+  bytes += (int64_t)(n * sizeof(T));
+  if (src) NB_CUDA(cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice));
+  return NB_OK;
+}
+
+int method_upload(nb_method *m) {
+  const nb_mesh *mesh = m->mesh;
+  const int64_t V = mesh->V, E = mesh->E, P = 2 * E;
+  NB_CUDA(cudaGetDevice(&m->device));
+  int64_t &b = m->device_bytes;
+  std::vector<int32_t> rp(V + 1);
+  for (int64_t i = 0; i <= V; ++i) rp[i] = (int32_t)mesh->row_ptr[i];
+  int st;
+#define UP(dst, src, n) \
+  if ((st = dev_upload(&(dst), (src), (n), b)) != NB_OK) return st;
+  UP(m->d_row_ptr, rp.data(), V + 1);
+  UP(m->d_nbr, mesh->nbr.data(), P);
+  UP(m->d_nbr_edge, mesh->nbr_edge.data(), P);
+  UP(m->d_vol, m->vol.data(), V);
+  UP(m->d_S, m->S.data(), 3 * E);
+  UP(m->d_T, m->T.data(), 3 * E);
+  UP(m->d_east, m->east.data(), 3 * V);
+  UP(m->d_north, m->north.data(), 3 * V);
+  UP(m->d_wgrad64, nullptr, 2 * P);
+  UP(m->d_wdiv64, nullptr, 2 * P);
+  UP(m->d_wcurl64, nullptr, 2 * P);
+  UP(m->d_sdiv64, nullptr, 2 * V);
+  UP(m->d_scurl64, nullptr, 2 * V);
+  UP(m->d_wgrad32, nullptr, 2 * P);
+  UP(m->d_wdiv32, nullptr, 2 * P);
+  UP(m->d_wcurl32, nullptr, 2 * P);
+  UP(m->d_sdiv32, nullptr, 2 * V);
+  UP(m->d_scurl32, nullptr, 2 * V);
+#undef UP
+  const int threads = 256;
+  const int64_t blocks = (V + threads - 1) / threads;
+  setup_weights_kernel<<<(unsigned)blocks, threads>>>(
+      V, m->d_row_ptr, m->d_nbr, m->d_nbr_edge, m->d_vol, m->d_S, m->d_T, m->d_east, m->d_north,
+      (double2 *)m->d_wgrad64, (double2 *)m->d_wdiv64, (double2 *)m->d_wcurl64,
+      (double2 *)m->d_sdiv64, (double2 *)m->d_scurl64, (float2 *)m->d_wgrad32,
+      (float2 *)m->d_wdiv32, (float2 *)m->d_wcurl32, (float2 *)m->d_sdiv32,
+      (float2 *)m->d_scurl32);
+  count_launch(1);
+  NB_CUDA(cudaGetLastError());
+  NB_CUDA(cudaDeviceSynchronize());
+  return NB_OK;
+}
+
+void method_free_device(nb_method *m) {
+  void *ptrs[] = {m->d_row_ptr, m->d_nbr, m->d_nbr_edge, m->d_vol, m->d_S, m->d_T, m->d_east,
+                  m->d_north, m->d_wgrad64, m->d_wdiv64, m->d_wcurl64, m->d_sdiv64,
+                  m->d_scurl64, m->d_wgrad32, m->d_wdiv32, m->d_wcurl32, m->d_sdiv32,
+                  m->d_scurl32};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  for (auto &kv : m->plans) {
+    TilePlan *tp = kv.second.get();
+    void *q[] = {tp->d_tile_node0, tp->d_halo_ptr, tp->d_halo, tp->d_lnbr};
+    for (void *p : q)
+      if (p) cudaFree(p);
+  }
+  m->plans.clear();
+}
+
+// ------------------------------------------------------------- direct kernels
+//
+// One thread per (node, group of LPT levels).  Consecutive threads take
+// consecutive level groups of one node, so a node's column and each
+// neighbour's column are read as contiguous 16-byte vectors.  Neighbour
+// columns are gathered through L1/L2 (the tiled kernels stage them in shared
+// memory instead).
+
+struct DirectArgs {
+  int64_t V;
+  int64_t cap_begin;
+  int nlev;
+  int ngroups;  // level groups per node
+  const int32_t *row_ptr;
+  const int32_t *nbr;
+  const void *w32;  // float2 per CSR entry (op weights)
+  const void *w64;  // double2 per CSR entry
+  const void *s32;  // float2 per node (div / curl self weights)
+  const void *s64;  // double2 per node
+  const void *in;
+  int64_t in_stride;
+  void *out;
+  int64_t out_stride;
+};
+
+// Load LPT consecutive values of a scalar column starting at level l0;
+// values at levels >= nlev are returned as 0 and never read past the row.
+template <int LPT>
+__device__ __forceinline__ void load_scalar_f32(const float *col, int l0, int nlev, float (&v)[LPT]) {
+  if constexpr (LPT == 4) {
+    if (l0 < nlev) {
+      const float4 x = __ldg(reinterpret_cast<const float4 *>(col + l0));
+      v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+    } else {
+      v[0] = v[1] = v[2] = v[3] = 0.f;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < LPT; ++k) v[k] = (l0 + k < nlev) ? __ldg(col + l0 + k) : 0.f;
+  }
+}
+// Load LPT levels of a (u, v) column.
+template <int LPT>
+__device__ __forceinline__ void load_vector_f32(const float *col, int l0, int nlev, float (&u)[LPT],
+                                                float (&v)[LPT]) {
+  if constexpr (LPT == 4) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (l0 + 2 * h < nlev) {
+        const float4 x = __ldg(reinterpret_cast<const float4 *>(col + 2 * (l0 + 2 * h)));
+        u[2 * h] = x.x; v[2 * h] = x.y; u[2 * h + 1] = x.z; v[2 * h + 1] = x.w;
+      } else {
+        u[2 * h] = v[2 * h] = u[2 * h + 1] = v[2 * h + 1] = 0.f;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < LPT; ++k) {
+      if (l0 + k < nlev) {
+        u[k] = __ldg(col + 2 * (l0 + k));
+        v[k] = __ldg(col + 2 * (l0 + k) + 1);
+      } else {
+        u[k] = v[k] = 0.f;
+      }
+    }
+  }
+}
+
+// op 0: grad.  FP32 arithmetic, compensated or plain accumulation.
+template <int LPT, class Acc>
+__global__ void __launch_bounds__(256) grad_direct_f32(DirectArgs a) {
+  const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = item / a.ngroups;
+  if (i >= a.V) return;
+  const int l0 = (int)(item - i * a.ngroups) * LPT;
+  const float *f = static_cast<const float *>(a.in);
+  float *g = static_cast<float *>(a.out);
+  const int32_t p0 = __ldg(a.row_ptr + i), p1 = __ldg(a.row_ptr + i + 1);
+  float gx[LPT], gy[LPT], fi[LPT];
+  load_scalar_f32<LPT>(f + i * a.in_stride, l0, a.nlev, fi);
+  if (i < a.cap_begin) {
+    Acc ax[LPT], ay[LPT];
+    const float2 *w = static_cast<const float2 *>(a.w32);
+    for (int32_t p = p0; p < p1; ++p) {
+      const int32_t j = __ldg(a.nbr + p);
+      const float2 wp = __ldg(w + p);
+      float fj[LPT];
+      load_scalar_f32<LPT>(f + (int64_t)j * a.in_stride, l0, a.nlev, fj);
+#pragma unroll
+      for (int k = 0; k < LPT; ++k) {
+        const float d = __fsub_rn(fj[k], fi[k]);
+        ax[k].add_prod(wp.x, d);
+        ay[k].add_prod(wp.y, d);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < LPT; ++k) {
+      gx[k] = ax[k].value();
+      gy[k] = ay[k].value();
+    }
+  } else {
+    // pole-row node: FP64 weights and FP64 accumulation
+    const double2 *w = static_cast<const double2 *>(a.w64);
+    double sx[LPT] = {}, sy[LPT] = {};
+    for (int32_t p = p0; p < p1; ++p) {
+      const int32_t j = __ldg(a.nbr + p);
+      const double2 wp = __ldg(w + p);
+      float fj[LPT];
+      load_scalar_f32<LPT>(f + (int64_t)j * a.in_stride, l0, a.nlev, fj);
+#pragma unroll
+      for (int k = 0; k < LPT; ++k) {
+        const double d = (double)fj[k] - (double)fi[k];
+        sx[k] = fma(wp.x, d, sx[k]);
+        sy[k] = fma(wp.y, d, sy[k]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < LPT; ++k) {
+      gx[k] = (float)sx[k];
+      gy[k] = (float)sy[k];
+    }
+  }
+  float *go = g + i * a.out_stride + 2 * l0;
+  if (LPT == 4 && l0 + 4 <= a.nlev) {
+    reinterpret_cast<float4 *>(go)[0] = make_float4(gx[0], gy[0], gx[1], gy[1]);
+    reinterpret_cast<float4 *>(go)[1] = make_float4(gx[2], gy[2], gx[3], gy[3]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < LPT; ++k)
+      if (l0 + k < a.nlev) {
+        go[2 * k] = gx[k];
+        go[2 * k + 1] = gy[k];
+      }
+  }
+}
+
+// op 1 / 2: div or curl (same stencil, different weights).
+template <int LPT, class Acc>
+__global__ void __launch_bounds__(256) divcurl_direct_f32(DirectArgs a) {
+  const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = item / a.ngroups;
+  if (i >= a.V) return;
+  const int l0 = (int)(item - i * a.ngroups) * LPT;
+  const float *uv = static_cast<const float *>(a.in);
+  float *o = static_cast<float *>(a.out);
+  const int32_t p0 = __ldg(a.row_ptr + i), p1 = __ldg(a.row_ptr + i + 1);
+  float ui[LPT], vi[LPT], r[LPT];
+  load_vector_f32<LPT>(uv + i * a.in_stride, l0, a.nlev, ui, vi);
+  if (i < a.cap_begin) {
+    const float2 *w = static_cast<const float2 *>(a.w32);
+    const float2 sw = __ldg(static_cast<const float2 *>(a.s32) + i);
+    Acc acc[LPT];
+    for (int32_t p = p0; p < p1; ++p) {
+      const int32_t j = __ldg(a.nbr + p);
+      const float2 wp = __ldg(w + p);
+      float uj[LPT], vj[LPT];
+      load_vector_f32<LPT>(uv + (int64_t)j * a.in_stride, l0, a.nlev, uj, vj);
+#pragma unroll
+      for (int k = 0; k < LPT; ++k) {
+        const float du = __fsub_rn(uj[k], ui[k]), dv = __fsub_rn(vj[k], vi[k]);
+        acc[k].add(__fmaf_rn(wp.x, du, __fmul_rn(wp.y, dv)));
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < LPT; ++k) {
+      acc[k].add(__fmaf_rn(sw.x, ui[k], __fmul_rn(sw.y, vi[k])));
+      r[k] = acc[k].value();
+    }
+  } else {
+    const double2 *w = static_cast<const double2 *>(a.w64);
+    const double2 sw = __ldg(static_cast<const double2 *>(a.s64) + i);
+    double s[LPT] = {};
+    for (int32_t p = p0; p < p1; ++p) {
+      const int32_t j = __ldg(a.nbr + p);
+      const double2 wp = __ldg(w + p);
+      float uj[LPT], vj[LPT];
+      load_vector_f32<LPT>(uv + (int64_t)j * a.in_stride, l0, a.nlev, uj, vj);
+#pragma unroll
+      for (int k = 0; k < LPT; ++k) {
+        s[k] = fma(wp.x, (double)uj[k] - (double)ui[k], s[k]);
+        s[k] = fma(wp.y, (double)vj[k] - (double)vi[k], s[k]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < LPT; ++k) {
+      s[k] = fma(sw.x, (double)ui[k], s[k]);
+      s[k] = fma(sw.y, (double)vi[k], s[k]);
+      r[k] = (float)s[k];
+    }
+  }
+  float *oo = o + i * a.out_stride + l0;
+  if (LPT == 4 && l0 + 4 <= a.nlev) {
+    *reinterpret_cast<float4 *>(oo) = make_float4(r[0], r[1], r[2], r[3]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < LPT; ++k)
+      if (l0 + k < a.nlev) oo[k] = r[k];
+  }
+}
+
+// FP64 path: plain FP64 arithmetic everywhere (the reference GPU path).
+template <int LPT>
+__global__ void __launch_bounds__(256) grad_direct_f64(DirectArgs a) {
+  const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = item / a.ngroups;
+  if (i >= a.V) return;
+  const int l0 = (int)(item - i * a.ngroups) * LPT;
+  const double *f = static_cast<const double *>(a.in);
+  double *g = static_cast<double *>(a.out);
+  const double2 *w = static_cast<const double2 *>(a.w64);
+  const int32_t p0 = __ldg(a.row_ptr + i), p1 = __ldg(a.row_ptr + i + 1);
+  double fi[LPT], sx[LPT] = {}, sy[LPT] = {};
+  const double *ci = f + i * a.in_stride;
+#pragma unroll
+  for (int k = 0; k < LPT; ++k) fi[k] = (l0 + k < a.nlev) ? __ldg(ci + l0 + k) : 0.0;
+  for (int32_t p = p0; p < p1; ++p) {
+    const int32_t j = __ldg(a.nbr + p);
+    const double2 wp = __ldg(w + p);
+    const double *cj = f + (int64_t)j * a.in_stride;
+#pragma unroll
+    for (int k = 0; k < LPT; ++k) {
+      const double d = ((l0 + k < a.nlev) ? __ldg(cj + l0 + k) : 0.0) - fi[k];
+      sx[k] = fma(wp.x, d, sx[k]);
+      sy[k] = fma(wp.y, d, sy[k]);
+    }
+  }
+  double *go = g + i * a.out_stride + 2 * l0;
+#pragma unroll
+  for (int k = 0; k < LPT; ++k)
+    if (l0 + k < a.nlev) {
+      go[2 * k] = sx[k];
+      go[2 * k + 1] = sy[k];
+    }
+}
+
+template <int LPT>
+__global__ void __launch_bounds__(256) divcurl_direct_f64(DirectArgs a) {
+  const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = item / a.ngroups;
+  if (i >= a.V) return;
+  const int l0 = (int)(item - i * a.ngroups) * LPT;
+  const double *uv = static_cast<const double *>(a.in);
+  double *o = static_cast<double *>(a.out);
+  const double2 *w = static_cast<const double2 *>(a.w64);
+  const double2 sw = __ldg(static_cast<const double2 *>(a.s64) + i);
+  const int32_t p0 = __ldg(a.row_ptr + i), p1 = __ldg(a.row_ptr + i + 1);
+  double ui[LPT], vi[LPT], s[LPT] = {};
+  const double *ci = uv + i * a.in_stride;
+#pragma unroll
+  for (int k = 0; k < LPT; ++k) {
+    const bool ok = l0 + k < a.nlev;
+    ui[k] = ok ? __ldg(ci + 2 * (l0 + k)) : 0.0;
+    vi[k] = ok ? __ldg(ci + 2 * (l0 + k) + 1) : 0.0;
+  }
+  for (int32_t p = p0; p < p1; ++p) {
+    const int32_t j = __ldg(a.nbr + p);
+    const double2 wp = __ldg(w + p);
+    const double *cj = uv + (int64_t)j * a.in_stride;
+#pragma unroll
+    for (int k = 0; k < LPT; ++k) {
+      const bool ok = l0 + k < a.nlev;
+      const double uj = ok ? __ldg(cj + 2 * (l0 + k)) : 0.0;
+      const double vj = ok ? __ldg(cj + 2 * (l0 + k) + 1) : 0.0;
+      s[k] = fma(wp.x, uj - ui[k], s[k]);
+      s[k] = fma(wp.y, vj - vi[k], s[k]);
+    }
+  }
+  double *oo = o + i * a.out_stride + l0;
+#pragma unroll
+  for (int k = 0; k < LPT; ++k) {
+    s[k] = fma(sw.x, ui[k], s[k]);
+    s[k] = fma(sw.y, vi[k], s[k]);
+    if (l0 + k < a.nlev) oo[k] = s[k];
+  }
+}
+
+// ------------------------------------------------------------------ launch
+
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Launch one op (0 grad, 1 div, 2 curl) with the direct kernels.
+int launch_direct(const nb_method *m, int op, const nb_field *in, const nb_field *out,
+                  cudaStream_t st) {
+  const nb_mesh *mesh = m->mesh;
+  const bool f64 = in->dtype == NB_F64;
+  DirectArgs a;
+  a.V = mesh->V;
+  a.cap_begin = mesh->cap_begin;
+  a.nlev = in->nlev;
+  a.row_ptr = m->d_row_ptr;
+  a.nbr = m->d_nbr;
+  a.w32 = op == 0 ? (const void *)m->d_wgrad32 : op == 1 ? (const void *)m->d_wdiv32 : (const void *)m->d_wcurl32;
+  a.w64 = op == 0 ? (const void *)m->d_wgrad64 : op == 1 ? (const void *)m->d_wdiv64 : (const void *)m->d_wcurl64;
+  a.s32 = op == 2 ? (const void *)m->d_scurl32 : (const void *)m->d_sdiv32;
+  a.s64 = op == 2 ? (const void *)m->d_scurl64 : (const void *)m->d_sdiv64;
+  a.in = in->data;
+  a.in_stride = in->node_stride;
+  a.out = out->data;
+  a.out_stride = out->node_stride;
+  // 16-byte vectors need aligned bases and strides that are multiples of 4 floats
+  const bool vec = !f64 && in->nlev >= 4 && aligned16(in->data) && aligned16(out->data) &&
+                   in->node_stride % 4 == 0 && out->node_stride % 4 == 0;
+  const int LPT = f64 ? 2 : (vec ? 4 : 1);
+  a.ngroups = (in->nlev + LPT - 1) / LPT;
+  const int threads = 256;
+  const int64_t items = a.V * a.ngroups;
+  const int64_t blocks = (items + threads - 1) / threads;
+  if (blocks > 0x7fffffff) {
+    set_error("launch: problem too large for one grid");
+    return NB_EINVAL;
+  }
+  const bool comp = m->compensated != 0;
+  const unsigned nb = (unsigned)blocks;
+  if (f64) {
+    if (op == 0) grad_direct_f64<2><<<nb, threads, 0, st>>>(a);
+    else divcurl_direct_f64<2><<<nb, threads, 0, st>>>(a);
+  } else if (vec) {
+    if (op == 0) {
+      if (comp) grad_direct_f32<4, KahanAcc><<<nb, threads, 0, st>>>(a);
+      else grad_direct_f32<4, PlainAcc><<<nb, threads, 0, st>>>(a);
+    } else {
+      if (comp) divcurl_direct_f32<4, KahanAcc><<<nb, threads, 0, st>>>(a);
+      else divcurl_direct_f32<4, PlainAcc><<<nb, threads, 0, st>>>(a);
+    }
+  } else {
+    if (op == 0) {
+      if (comp) grad_direct_f32<1, KahanAcc><<<nb, threads, 0, st>>>(a);
+      else grad_direct_f32<1, PlainAcc><<<nb, threads, 0, st>>>(a);
+    } else {
+      if (comp) divcurl_direct_f32<1, KahanAcc><<<nb, threads, 0, st>>>(a);
+      else divcurl_direct_f32<1, PlainAcc><<<nb, threads, 0, st>>>(a);
+    }
+  }
+  count_launch(1);
+  NB_CUDA(cudaGetLastError());
+  return NB_OK;
+}
+
+}  // namespace nb

@@ -1,0 +1,311 @@
+"""Thin ctypes binding of the C ABI in ``include/nabla_b300.h``.
+
+Argument marshalling only: every step of the operators runs in the library's
+CUDA kernels.  PyTorch provides device memory and streams.  Loading fails
+loudly if the shared object has not been built (``build.py``); there is no
+CPU fallback.
+
+Concept chain (Sec. 4.7, Listing 12):
+
+    grid = Grid(1280)                  # O1280 (Sec. 4.2.3.7)
+    mesh = Mesh(grid)                  # structured triangulation (Sec. 4.3)
+    method = Method(mesh)              # fvm::Method: median-dual geometry
+    fs = NodeColumns(method, 137, torch.float32)   # Sec. 4.5
+    f = fs.create_field()              # [V, 137] view of a [V, Lp] tensor
+    g = fs.create_field(nvar=2)        # [V, 137, 2]
+    gradient(method, f, g)             # fvm::Nabla::gradient
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libnabla_b300.so")
+
+NB_OK, NB_EINVAL, NB_ESHAPE, NB_EDTYPE, NB_EOOM, NB_ECUDA, NB_ETIMEOUT, NB_EBUDGET = range(8)
+NB_F32, NB_F64 = 0, 1
+OP_GRAD, OP_DIV, OP_CURL, OP_LAP = 0, 1, 2, 3
+OPS = {"grad": OP_GRAD, "div": OP_DIV, "curl": OP_CURL, "lap": OP_LAP}
+KERNEL_AUTO, KERNEL_DIRECT, KERNEL_TILED = 0, 1, 2
+EARTH_RADIUS_M = 6.37122e6
+
+
+class NablaError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[nabla status {code}] {msg}")
+        self.code = code
+
+
+class nb_field(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("dtype", ctypes.c_int32), ("nvar", ctypes.c_int32),
+                ("nnodes", ctypes.c_int64), ("nlev", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("node_stride", ctypes.c_int64), ("lev_stride", ctypes.c_int64)]
+
+
+_lib = None
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_I64P = ctypes.POINTER(ctypes.c_int64)
+_FP = ctypes.POINTER(nb_field)
+
+# name -> argtypes; every function returns int except the two string getters
+SIGNATURES = {
+    "nb_grid_create_octahedral": [_I, ctypes.POINTER(_P)],
+    "nb_grid_release": [_P],
+    "nb_grid_size": [_P, _I64P],
+    "nb_grid_gaussian_number": [_P, ctypes.POINTER(_I)],
+    "nb_grid_lonlat": [_P, _P],
+    "nb_mesh_create": [_P, _I, ctypes.POINTER(_P)],
+    "nb_mesh_release": [_P],
+    "nb_mesh_sizes": [_P, _I64P, _I64P, _I64P],
+    "nb_mesh_permutation": [_P, _P],
+    "nb_mesh_triangles": [_P, _P],
+    "nb_mesh_edges": [_P, _P],
+    "nb_mesh_cap_begin": [_P, _I64P],
+    "nb_method_create": [_P, ctypes.c_double, ctypes.POINTER(_P)],
+    "nb_method_release": [_P],
+    "nb_method_dual_volumes": [_P, _P],
+    "nb_method_device_bytes": [_P, _I64P],
+    "nb_method_set_kernel": [_P, _I, _I],
+    "nb_method_set_compensated": [_P, _I],
+    "nb_fs_nodecolumns": [_P, _I, _I, ctypes.POINTER(_P)],
+    "nb_fs_release": [_P],
+    "nb_fs_level_stride": [_P, _I64P],
+    "nb_field_view": [_P, _P, _I, ctypes.c_int64, ctypes.c_int64, _FP],
+    "nb_nabla_gradient": [_P, _FP, _FP, _P],
+    "nb_nabla_divergence": [_P, _FP, _FP, _P],
+    "nb_nabla_curl": [_P, _FP, _FP, _P],
+    "nb_nabla_laplacian": [_P, _FP, _FP, _FP, _P],
+    "nb_nabla_apply": [_P, _I, _FP, _FP, _FP, _P],
+    "nb_nabla_apply_host": [_P, _I, _P, _P, _FP, _FP, _FP, _P],
+    "nb_launch_count": [_I64P],
+}
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded library; raises if it was not built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"nabla_b300 CUDA library missing: {LIB_PATH} "
+                               "(run `python -m paper_1908_06091_b300.build`)")
+        L = ctypes.CDLL(LIB_PATH)
+        L.nb_version.restype = ctypes.c_char_p
+        L.nb_last_error.restype = ctypes.c_char_p
+        for name, args in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def check(rc: int) -> None:
+    if rc != NB_OK:
+        raise NablaError(rc, lib().nb_last_error().decode())
+
+
+def version() -> str:
+    return lib().nb_version().decode()
+
+
+def launch_count() -> int:
+    c = ctypes.c_int64()
+    check(lib().nb_launch_count(ctypes.byref(c)))
+    return c.value
+
+
+class _Handle:
+    _release = ""
+
+    def __init__(self):
+        self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and h.value and _lib is not None:
+            getattr(_lib, self._release)(h)
+            self._h = ctypes.c_void_p()
+
+    @property
+    def handle(self):
+        return self._h
+
+
+class Grid(_Handle):
+    """Octahedral reduced Gaussian grid O<N> (Sec. 4.2.3.7)."""
+    _release = "nb_grid_release"
+
+    def __init__(self, N: int):
+        super().__init__()
+        check(lib().nb_grid_create_octahedral(int(N), ctypes.byref(self._h)))
+        self.N = int(N)
+
+    @property
+    def size(self) -> int:
+        v = ctypes.c_int64()
+        check(lib().nb_grid_size(self._h, ctypes.byref(v)))
+        return v.value
+
+    def lonlat(self) -> np.ndarray:
+        out = np.zeros((self.size, 2))
+        check(lib().nb_grid_lonlat(self._h, out.ctypes.data))
+        return out
+
+
+class Mesh(_Handle):
+    """Structured triangulation of a grid (Sec. 4.3), Hilbert-ordered by default."""
+    _release = "nb_mesh_release"
+
+    def __init__(self, grid: Grid, reorder: int = 1):
+        super().__init__()
+        self.grid = grid
+        check(lib().nb_mesh_create(grid.handle, int(reorder), ctypes.byref(self._h)))
+        v, e, t = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        check(lib().nb_mesh_sizes(self._h, ctypes.byref(v), ctypes.byref(e), ctypes.byref(t)))
+        self.V, self.E, self.F = v.value, e.value, t.value
+        c = ctypes.c_int64()
+        check(lib().nb_mesh_cap_begin(self._h, ctypes.byref(c)))
+        self.cap_begin = c.value
+
+    def permutation(self) -> np.ndarray:
+        out = np.zeros(self.V, dtype=np.int32)
+        check(lib().nb_mesh_permutation(self._h, out.ctypes.data))
+        return out
+
+    def triangles(self) -> np.ndarray:
+        out = np.zeros((self.F, 3), dtype=np.int32)
+        check(lib().nb_mesh_triangles(self._h, out.ctypes.data))
+        return out
+
+    def edges(self) -> np.ndarray:
+        out = np.zeros((self.E, 2), dtype=np.int32)
+        check(lib().nb_mesh_edges(self._h, out.ctypes.data))
+        return out
+
+
+class Method(_Handle):
+    """fvm::Method (Sec. 4.7): median-dual geometry resident on the current device."""
+    _release = "nb_method_release"
+
+    def __init__(self, mesh: Mesh, radius: float = EARTH_RADIUS_M):
+        super().__init__()
+        self.mesh = mesh
+        self.radius = float(radius)
+        check(lib().nb_method_create(mesh.handle, self.radius, ctypes.byref(self._h)))
+
+    def dual_volumes(self) -> np.ndarray:
+        out = np.zeros(self.mesh.V)
+        check(lib().nb_method_dual_volumes(self._h, out.ctypes.data))
+        return out
+
+    def device_bytes(self) -> int:
+        b = ctypes.c_int64()
+        check(lib().nb_method_device_bytes(self._h, ctypes.byref(b)))
+        return b.value
+
+    def set_kernel(self, variant: int, tile_nodes: int = 0) -> None:
+        check(lib().nb_method_set_kernel(self._h, int(variant), int(tile_nodes)))
+
+    def set_compensated(self, on: bool) -> None:
+        check(lib().nb_method_set_compensated(self._h, 1 if on else 0))
+
+
+_DT = {torch.float32: NB_F32, torch.float64: NB_F64}
+
+
+class NodeColumns(_Handle):
+    """NodeColumns function space (Sec. 4.5): nlev levels, padded stride Lp."""
+    _release = "nb_fs_release"
+
+    def __init__(self, method: Method, nlev: int, dtype=torch.float32):
+        super().__init__()
+        self.method = method
+        self.nlev = int(nlev)
+        self.dtype = dtype
+        check(lib().nb_fs_nodecolumns(method.handle, self.nlev, _DT[dtype], ctypes.byref(self._h)))
+        lp = ctypes.c_int64()
+        check(lib().nb_fs_level_stride(self._h, ctypes.byref(lp)))
+        self.lp = lp.value
+
+    def create_field(self, nvar: int = 1, device="cuda", fill=None) -> torch.Tensor:
+        """[V, nlev] (nvar 1) or [V, nlev, 2] view of a padded [V, Lp(, 2)] tensor."""
+        V = self.method.mesh.V
+        shape = (V, self.lp) if nvar == 1 else (V, self.lp, 2)
+        t = torch.empty(shape, dtype=self.dtype, device=device) if fill is None else \
+            torch.full(shape, float(fill), dtype=self.dtype, device=device)
+        return t[:, :self.nlev]
+
+
+def field_view(t: torch.Tensor, nvar: int) -> nb_field:
+    """nb_field describing a [V, L] or [V, L, 2] tensor (levels contiguous)."""
+    if t.dtype not in _DT:
+        raise TypeError(f"unsupported dtype {t.dtype}")
+    f = nb_field()
+    f.data = t.data_ptr()
+    f.dtype = _DT[t.dtype]
+    f.nvar = nvar
+    f.nnodes = t.shape[0]
+    f.nlev = t.shape[1]
+    f.reserved = 0
+    f.node_stride = t.stride(0)
+    f.lev_stride = t.stride(1)
+    if nvar == 1 and t.dim() != 2:
+        raise ValueError("scalar field must be [V, L]")
+    if nvar == 2 and (t.dim() != 3 or t.shape[2] != 2 or t.stride(2) != 1):
+        raise ValueError("vector field must be [V, L, 2] with components innermost")
+    return f
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def apply(method: Method, op, inp: torch.Tensor, out: torch.Tensor, scratch=None, stream=None):
+    """fvm::Nabla operator `op` ('grad', 'div', 'curl', 'lap' or an OP_* code)."""
+    code = OPS[op] if isinstance(op, str) else int(op)
+    nin = 2 if code in (OP_DIV, OP_CURL) else 1
+    nout = 2 if code == OP_GRAD else 1
+    fi, fo = field_view(inp, nin), field_view(out, nout)
+    fs = ctypes.byref(field_view(scratch, 2)) if scratch is not None else None
+    check(lib().nb_nabla_apply(method.handle, code, ctypes.byref(fi), ctypes.byref(fo), fs,
+                               ctypes.c_void_p(_stream(stream))))
+    return out
+
+
+def gradient(method, f, g, stream=None):
+    return apply(method, OP_GRAD, f, g, stream=stream)
+
+
+def divergence(method, uv, d, stream=None):
+    return apply(method, OP_DIV, uv, d, stream=stream)
+
+
+def curl(method, uv, z, stream=None):
+    return apply(method, OP_CURL, uv, z, stream=stream)
+
+
+def laplacian(method, f, lap, scratch=None, stream=None):
+    return apply(method, OP_LAP, f, lap, scratch=scratch, stream=stream)
+
+
+def apply_host(method: Method, op, host_in: torch.Tensor, host_out: torch.Tensor,
+               dev_in: torch.Tensor, dev_out: torch.Tensor, scratch=None, stream=None):
+    """End-to-end call on host buffers laid out like dev_in / dev_out (their
+    padded storage: pass the base tensors, e.g. ``t._base`` of a view)."""
+    code = OPS[op] if isinstance(op, str) else int(op)
+    nin = 2 if code in (OP_DIV, OP_CURL) else 1
+    nout = 2 if code == OP_GRAD else 1
+    fi, fo = field_view(dev_in, nin), field_view(dev_out, nout)
+    fs = ctypes.byref(field_view(scratch, 2)) if scratch is not None else None
+    check(lib().nb_nabla_apply_host(method.handle, code, ctypes.c_void_p(host_in.data_ptr()),
+                                    ctypes.c_void_p(host_out.data_ptr()), ctypes.byref(fi),
+                                    ctypes.byref(fo), fs, ctypes.c_void_p(_stream(stream))))
+    return host_out

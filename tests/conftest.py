@@ -8,6 +8,14 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
+def pytest_sessionstart(session):
+    """Build the CUDA library and the oracle in-tree if they are missing or stale."""
+    from paper_1908_06091_b300 import build as lib_build
+    import oracle
+    lib_build.build()
+    oracle.build()
+
+
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (B300) and the built CUDA library")
     config.addinivalue_line("markers", "slow: larger CPU cases")

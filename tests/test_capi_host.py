@@ -1,0 +1,110 @@
+"""Host-side C-ABI checks (no GPU): the library loads, exports every symbol
+its header declares, and its host mesh builder reproduces the oracle's grid
+and triangulation (two independent implementations)."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1908_06091_b300 import nabla
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(nb_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol():
+    L = nabla.lib()
+    names = _declared_functions()
+    assert len(names) >= 25
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+    # and the binding declares each of them
+    assert set(names) <= set(nabla.SIGNATURES) | {"nb_version", "nb_last_error"}
+
+
+def test_version_and_error_reporting():
+    assert "sm_103a" in nabla.version()
+    with pytest.raises(nabla.NablaError) as ei:
+        nabla.Grid(0)
+    assert ei.value.code == nabla.NB_EINVAL and "N must be" in str(ei.value)
+
+
+@pytest.mark.parametrize("N", [1, 16, 32, 80])
+def test_grid_matches_oracle(N):
+    g = nabla.Grid(N)
+    assert g.size == oracle.num_nodes(N)
+    ll = g.lonlat()
+    lat, lon = oracle.grid_lonlat(N)
+    assert np.abs(ll[:, 0] - lon).max() == 0.0
+    # Legendre roots agree to an ulp; asin magnifies that near the poles
+    assert np.abs(np.sin(ll[:, 1]) - np.sin(lat)).max() < 4e-16
+    assert np.abs(ll[:, 1] - lat).max() < 1e-14
+
+
+@pytest.mark.parametrize("N,reorder", [(1, 0), (16, 0), (16, 1), (48, 1)])
+def test_mesh_matches_oracle_triangulation(N, reorder):
+    g = nabla.Grid(N)
+    m = nabla.Mesh(g, reorder)
+    assert (m.V, m.E, m.F) == (g.size, 3 * g.size - 6, 2 * g.size - 4)
+    perm = m.permutation()
+    assert np.array_equal(np.sort(perm), np.arange(m.V))
+    tri = perm[m.triangles()]                       # back to grid numbering
+    ot = oracle.triangulate(N)
+    canon = lambda t: {tuple(np.roll(r, -int(np.argmin(r)))) for r in t}
+    assert canon(tri) == canon(ot)                  # same oriented triangles
+    e = perm[m.edges()]
+    oe, _ = oracle.edges(g.size, ot)
+    assert {tuple(sorted(x)) for x in e} == {tuple(sorted(x)) for x in oe}
+
+
+def test_pole_rows_come_last():
+    N = 24
+    m = nabla.Mesh(nabla.Grid(N), 1)
+    perm = m.permutation()
+    nx = oracle.row_nx(N)
+    assert m.cap_begin == m.V - nx[0] - nx[-1]
+    tail = set(perm[m.cap_begin:].tolist())
+    assert tail == set(range(nx[0])) | set(range(m.V - nx[-1], m.V))
+
+
+def test_hilbert_order_is_local():
+    """Consecutive nodes in the reordered mesh are close on the sphere."""
+    N = 64
+    g = nabla.Grid(N)
+    m = nabla.Mesh(g, 1)
+    ll = g.lonlat()[m.permutation()]
+    xyz = np.stack([np.cos(ll[:, 1]) * np.cos(ll[:, 0]), np.cos(ll[:, 1]) * np.sin(ll[:, 0]),
+                    np.sin(ll[:, 1])], 1)
+    step = np.linalg.norm(np.diff(xyz[:m.cap_begin], axis=0), axis=1)
+    h = np.pi / (2 * N)
+    assert np.median(step) < 1.5 * h
+    m0 = nabla.Mesh(g, 0)
+    ll0 = g.lonlat()[m0.permutation()]
+    # tiles of 64 consecutive nodes: Hilbert tiles are much more compact
+    def spread(llx):
+        x = np.stack([np.cos(llx[:, 1]) * np.cos(llx[:, 0]), np.cos(llx[:, 1]) * np.sin(llx[:, 0]),
+                      np.sin(llx[:, 1])], 1)[: (m.cap_begin // 64) * 64].reshape(-1, 64, 3)
+        return np.linalg.norm(x - x.mean(1, keepdims=True), axis=2).max(1).mean()
+    assert spread(ll) < 0.5 * spread(ll0)
+
+
+def test_method_requires_a_device_and_reports_it():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("GPU present: covered by the GPU tests")
+    m = nabla.Mesh(nabla.Grid(4), 1)
+    with pytest.raises(nabla.NablaError) as ei:
+        nabla.Method(m)
+    assert ei.value.code == nabla.NB_ECUDA

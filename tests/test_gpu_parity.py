@@ -1,0 +1,181 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs, element by element in grid order.
+
+Gates: relative L2 <= 1e-12 on the FP64 path and <= 1e-5 on the FP32 path
+(inputs rounded to FP32 first and given to the oracle exactly, so the
+comparison measures arithmetic error, not input rounding)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1908_06091_b300 import nabla
+from gpu_helpers import (inputs, oracle_mesh, oracle_op, product, rel_l2, run_op, to_device,
+                         to_grid)
+
+pytestmark = pytest.mark.gpu
+
+TOL = {torch.float64: 1e-12, torch.float32: 1e-5}
+OPS = ["grad", "div", "curl", "lap"]
+
+
+def _case(N, nlev, dtype, lmax=10, reorder=1, variant=nabla.KERNEL_AUTO, comp=True, pad=True,
+          ops=OPS, levels=None):
+    g, m, meth = product(N, reorder)
+    meth.set_kernel(variant)
+    meth.set_compensated(comp)
+    om = oracle_mesh(N)
+    f, uv = inputs(om, nlev, lmax, dtype)
+    perm = m.permutation()
+    fs = nabla.NodeColumns(meth, nlev, dtype)
+    fd = to_device(fs, f, perm, 1, pad)
+    uvd = to_device(fs, uv, perm, 2, pad)
+    errs = {}
+    for op in ops:
+        xin = fd if op in ("grad", "lap") else uvd
+        out = to_grid(run_op(meth, fs, op, xin), perm)
+        xo = f if op in ("grad", "lap") else uv
+        if levels is not None:
+            out = out[:, levels]
+            xo = xo[:, levels]
+        ref = oracle_op(om, op, xo.astype(np.float64))
+        assert np.isfinite(out).all(), op
+        errs[op] = rel_l2(out, ref)
+    meth.set_kernel(nabla.KERNEL_AUTO)
+    meth.set_compensated(True)
+    return errs
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["f64", "f32"])
+@pytest.mark.parametrize("nlev", [1, 7, 137])
+def test_o32_all_ops(nlev, dtype):
+    errs = _case(32, nlev, dtype)
+    assert max(errs.values()) <= TOL[dtype], errs
+
+
+@pytest.mark.parametrize("nlev", [1, 2, 3, 5, 6, 9])
+@pytest.mark.parametrize("pad", [True, False], ids=["padded", "unpadded"])
+def test_ragged_levels_and_layouts(nlev, pad):
+    for dtype in (torch.float32, torch.float64):
+        errs = _case(16, nlev, dtype, pad=pad)
+        assert max(errs.values()) <= TOL[dtype], (dtype, errs)
+
+
+@pytest.mark.parametrize("variant", [nabla.KERNEL_DIRECT, nabla.KERNEL_TILED])
+def test_kernel_variants_agree_with_oracle(variant):
+    for dtype in (torch.float32, torch.float64):
+        errs = _case(48, 40, dtype, variant=variant)
+        assert max(errs.values()) <= TOL[dtype], (variant, dtype, errs)
+
+
+def test_grid_order_mesh():
+    errs = _case(24, 9, torch.float32, reorder=0)
+    assert max(errs.values()) <= 1e-5, errs
+
+
+def test_plain_fp32_accumulation_also_within_gate():
+    errs = _case(32, 9, torch.float32, comp=False)
+    assert max(errs.values()) <= 1e-5, errs
+
+
+def test_o640_137_levels_fp32_and_fp64():
+    """O640 x 137: every node, every level (the workload of the second
+    configuration), both precisions."""
+    for dtype in (torch.float32, torch.float64):
+        errs = _case(640, 137, dtype, lmax=40)
+        print(dtype, errs)
+        assert max(errs.values()) <= TOL[dtype], (dtype, errs)
+
+
+def test_o1280_137_levels_sampled_levels():
+    """O1280 x 137 (the benchmark workload, same launch configuration): the
+    GPU computes all levels; levels {0, 68, 136} are compared with the
+    oracle element by element over all nodes."""
+    errs = _case(1280, 137, torch.float32, lmax=40, ops=["grad", "div", "curl"],
+                 levels=[0, 68, 136])
+    print(errs)
+    assert max(errs.values()) <= 1e-5, errs
+
+
+def test_gradient_of_constant_is_zero_on_gpu():
+    g, m, meth = product(32)
+    for dtype in (torch.float32, torch.float64):
+        fs = nabla.NodeColumns(meth, 9, dtype)
+        f = fs.create_field(fill=2.5)
+        out = run_op(meth, fs, "grad", f)
+        assert torch.count_nonzero(out).item() == 0
+
+
+def test_conservation_on_gpu():
+    g, m, meth = product(32)
+    vol = torch.as_tensor(meth.dual_volumes(), device="cuda")
+    fs = nabla.NodeColumns(meth, 3, torch.float64)
+    uv = fs.create_field(nvar=2)
+    uv.copy_(torch.randn(uv.shape, dtype=torch.float64, generator=torch.Generator().manual_seed(1)))
+    for op in ("div", "curl"):
+        d = run_op(meth, fs, op, uv)
+        r = (vol[:, None] * d).sum(0).abs() / (vol[:, None] * d.abs()).sum(0)
+        assert r.max().item() < 1e-13
+
+
+def test_results_are_deterministic():
+    g, m, meth = product(48)
+    om = oracle_mesh(48)
+    f, uv = inputs(om, 37, 10, torch.float32)
+    fs = nabla.NodeColumns(meth, 37, torch.float32)
+    perm = m.permutation()
+    fd, uvd = to_device(fs, f, perm, 1), to_device(fs, uv, perm, 2)
+    for op, x in (("grad", fd), ("div", uvd), ("curl", uvd), ("lap", fd)):
+        a = run_op(meth, fs, op, x)
+        b = run_op(meth, fs, op, x)
+        assert torch.equal(a, b), op
+
+
+def test_laplacian_with_caller_scratch_equals_library_scratch():
+    g, m, meth = product(32)
+    om = oracle_mesh(32)
+    f, _ = inputs(om, 13, 10, torch.float32)
+    fs = nabla.NodeColumns(meth, 13, torch.float32)
+    fd = to_device(fs, f, m.permutation(), 1)
+    scratch = fs.create_field(nvar=2)
+    a = run_op(meth, fs, "lap", fd, scratch=scratch)
+    b = run_op(meth, fs, "lap", fd)
+    assert torch.equal(a, b)
+
+
+def test_errors_are_reported_before_launch():
+    g, m, meth = product(16)
+    fs = nabla.NodeColumns(meth, 4, torch.float32)
+    fs64 = nabla.NodeColumns(meth, 4, torch.float64)
+    f = fs.create_field()
+    before = nabla.launch_count()
+    with pytest.raises(nabla.NablaError) as e:      # wrong nvar for the output
+        nabla.apply(meth, "grad", f, fs.create_field())
+    assert e.value.code in (nabla.NB_ESHAPE, nabla.NB_EINVAL)
+    with pytest.raises(nabla.NablaError) as e:      # dtype mismatch
+        nabla.apply(meth, "grad", f, fs64.create_field(nvar=2))
+    assert e.value.code == nabla.NB_EDTYPE
+    with pytest.raises(nabla.NablaError) as e:      # output aliases input
+        big = fs.create_field(nvar=2)
+        nabla.apply(meth, "div", big, big[:, :, 0])
+    assert e.value.code in (nabla.NB_ESHAPE, nabla.NB_EINVAL)
+    g2, m2, meth2 = product(24)
+    fs2 = nabla.NodeColumns(meth2, 4, torch.float32)
+    with pytest.raises(nabla.NablaError) as e:      # field of another mesh
+        nabla.apply(meth, "grad", fs2.create_field(), fs2.create_field(nvar=2))
+    assert e.value.code == nabla.NB_ESHAPE
+    assert nabla.launch_count() == before
+
+
+def test_host_buffer_entry_point_matches_device_call():
+    g, m, meth = product(32)
+    om = oracle_mesh(32)
+    f, _ = inputs(om, 9, 10, torch.float32)
+    fs = nabla.NodeColumns(meth, 9, torch.float32)
+    fd = to_device(fs, f, m.permutation(), 1)
+    ref = run_op(meth, fs, "lap", fd)
+    host_in = fd._base.cpu().pin_memory()
+    out = fs.create_field()
+    host_out = torch.empty_like(out._base, device="cpu").pin_memory()
+    nabla.apply_host(meth, "lap", host_in, host_out, fd, out)
+    assert torch.equal(host_out[:, :9], ref.cpu())
