@@ -64,36 +64,40 @@ void or_row_nx(int N, int *nx) {
 }
 
 /* Legendre polynomial P_n(x) and its derivative, from the three-term
- * recurrence (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1}. */
-static void legendre(int n, double x, double *pn, double *dpn) {
-  double pm1 = 1.0, p = x;
+ * recurrence (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1}, in extended
+ * precision (long double). */
+static void legendre(int n, long double x, long double *pn, long double *dpn) {
+  long double pm1 = 1.0L, p = x;
   for (int k = 1; k < n; ++k) {
-    double pp1 = ((2.0 * k + 1.0) * x * p - k * pm1) / (k + 1.0);
+    long double pp1 = ((2.0L * k + 1.0L) * x * p - k * pm1) / (k + 1.0L);
     pm1 = p;
     p = pp1;
   }
   *pn = p;
-  *dpn = n * (x * p - pm1) / (x * x - 1.0);
+  *dpn = n * (x * p - pm1) / (x * x - 1.0L);
 }
 
 /* Gaussian latitudes: the 2N roots mu_j of P_{2N}, ordered from north to
  * south (Sec. 4.2.3.5), with their Gauss-Legendre weights.  Newton's method
- * from the classical first guess cos(pi (j + 3/4) / (2N + 1/2)). */
+ * from the classical first guess cos(pi (j + 3/4) / (2N + 1/2)), carried out
+ * in extended precision and rounded once, so that each root is the double
+ * nearest to the true root.  (The median-dual geometry is sensitive to node
+ * positions at the last bit, so a correctly rounded grid matters.) */
 void or_gaussian_rows(int N, double *mu, double *weight) {
   int n = 2 * N;
   for (int j = 0; j < N; ++j) {
-    double x = cos(OR_PI * (j + 0.75) / (n + 0.5));
-    double p, dp;
+    long double x = cosl(3.14159265358979323846264338327950288L * (j + 0.75L) / (n + 0.5L));
+    long double p, dp;
     for (int it = 0; it < 100; ++it) {
       legendre(n, x, &p, &dp);
-      double dx = p / dp;
+      long double dx = p / dp;
       x -= dx;
-      if (fabs(dx) < 1e-16) break;
+      if (fabsl(dx) < 1e-19L) break;
     }
     legendre(n, x, &p, &dp);
-    mu[j] = x;
-    mu[n - 1 - j] = -x;
-    double w = 2.0 / ((1.0 - x * x) * dp * dp);
+    mu[j] = (double)x;
+    mu[n - 1 - j] = -(double)x;
+    double w = (double)(2.0L / ((1.0L - x * x) * dp * dp));
     weight[j] = w;
     weight[n - 1 - j] = w;
   }

@@ -24,8 +24,24 @@ static constexpr double kPi = 3.14159265358979323846;
 // Points on row j of O<N>: 20 + 4 * (distance in rows from the nearer pole).
 static inline int32_t octa_nx(int N, int j) { return 20 + 4 * std::min(j, 2 * N - 1 - j); }
 
-// Positive roots of P_n (n = 2N) by Newton on the Legendre recurrence,
-// northernmost first.  First guess: Tricomi's asymptotic estimate.
+// Positive roots of P_n (n = 2N), northernmost first: Newton on the Legendre
+// recurrence in double from Tricomi's asymptotic first guess, then polished
+// by Newton steps in extended precision and rounded once, so each root is
+// the double nearest the true root.  The median-dual geometry reacts to
+// node positions at the last bit (a one-ulp shift of the latitudes moves
+// O640 dual volumes by ~1e-12), so the rows are computed correctly rounded.
+template <class F>
+static F legendre_newton_step(int n, F x) {
+  F p0 = 1, p1 = x;
+  for (int l = 2; l <= n; ++l) {
+    const F p2 = ((F)(2 * l - 1) * x * p1 - (F)(l - 1) * p0) / (F)l;
+    p0 = p1;
+    p1 = p2;
+  }
+  const F dp = (F)n * (p0 - x * p1) / ((F)1 - x * x);
+  return p1 / dp;
+}
+
 static void legendre_roots(int N, std::vector<double> &mu) {
   const int n = 2 * N;
   mu.assign(n, 0.0);
@@ -34,19 +50,14 @@ static void legendre_roots(int N, std::vector<double> &mu) {
     const double th = kPi * (4.0 * (k + 1) - 1.0) / (4.0 * n + 2.0);
     double x = (1.0 - (n - 1.0) / (8.0 * n * (double)n * n)) * std::cos(th);
     for (int it = 0; it < 50; ++it) {
-      double p0 = 1.0, p1 = x;
-      for (int l = 2; l <= n; ++l) {
-        const double p2 = ((2 * l - 1) * x * p1 - (l - 1) * p0) / l;
-        p0 = p1;
-        p1 = p2;
-      }
-      const double dp = n * (p0 - x * p1) / (1.0 - x * x);
-      const double step = p1 / dp;
+      const double step = legendre_newton_step<double>(n, x);
       x -= step;
-      if (std::fabs(step) <= 1e-17) break;
+      if (std::fabs(step) <= 1e-15) break;
     }
-    mu[k] = x;
-    mu[n - 1 - k] = -x;
+    long double xl = x;
+    for (int it = 0; it < 3; ++it) xl -= legendre_newton_step<long double>(n, xl);
+    mu[k] = (double)xl;
+    mu[n - 1 - k] = -(double)xl;
   }
 }
 
