@@ -127,6 +127,20 @@ int nb_mesh_triangles(const nb_mesh *mesh, int32_t *tri);
 /* Edges [E][2] (a < b, functionspace numbering) (host). */
 int nb_mesh_edges(const nb_mesh *mesh, int32_t *edge);
 
+/* Node -> neighbour CSR in functionspace numbering (host): row_ptr[V+1],
+ * nbr[2E], neighbours of each node ascending. */
+int nb_mesh_csr(const nb_mesh *mesh, int64_t *row_ptr, int32_t *nbr);
+
+/* Tile plan of the shared-memory staged kernels (host, for inspection):
+ * tiles of consecutive nodes, grown while own nodes + halo nodes <= rcap and
+ * nodes <= nmax.  Call with NULL arrays to get *ntiles and *nhalo; then pass
+ * node0[ntiles+1], halo_ptr[ntiles+1], halo[nhalo] and lnbr[2E] (staged row
+ * of every CSR neighbour: k < n is the tile's node k, n + h its halo node h).
+ * *ntiles_main counts the tiles before the pole block. */
+int nb_mesh_tile_plan(const nb_mesh *mesh, int rcap, int nmax, int32_t *ntiles,
+                      int32_t *ntiles_main, int64_t *nhalo, int32_t *node0, int32_t *halo_ptr,
+                      int32_t *halo, uint16_t *lnbr);
+
 /* First node of the pole-row block: nodes [cap_begin, V) are the nodes of
  * the first and last grid rows, which the FP32 kernels treat in FP64. */
 int nb_mesh_cap_begin(const nb_mesh *mesh, int64_t *cap_begin);
@@ -218,6 +232,13 @@ int nb_method_set_compensated(nb_method *method, int on);
 
 /* Number of this library's kernel launches since load (all devices). */
 int nb_launch_count(int64_t *count);
+
+/* Device status word of the current device: 0 if every kernel so far ran
+ * normally, else the NB_* code a kernel recorded (NB_ETIMEOUT when a bounded
+ * wait inside a kernel ran out; the kernel then returned early and its
+ * outputs are incomplete).  Synchronises the device.  clear != 0 resets the
+ * word to 0 after reading it. */
+int nb_device_status(int clear, int32_t *code);
 
 #ifdef __cplusplus
 }

@@ -20,6 +20,7 @@ void set_error(const std::string &msg) { t_last_error = msg; }
 
 int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, cudaStream_t st,
                  bool *handled);
+int device_status(int clear, int *code);
 
 }  // namespace nb
 
@@ -64,6 +65,14 @@ int nb_launch_count(int64_t *count) {
   NB_REQUIRE(count, NB_EINVAL, "nb_launch_count: NULL");
   *count = nb::launch_count();
   return NB_OK;
+}
+
+int nb_device_status(int clear, int32_t *code) {
+  NB_REQUIRE(code, NB_EINVAL, "nb_device_status: NULL");
+  int c = 0;
+  const int st = nb::device_status(clear, &c);
+  *code = c;
+  return st;
 }
 
 // ------------------------------------------------------------------ grid
@@ -148,6 +157,35 @@ int nb_mesh_edges(const nb_mesh *m, int32_t *edge) {
   NB_REQUIRE(m && edge, NB_EINVAL, "nb_mesh_edges: NULL argument");
   std::memcpy(edge, m->edge.data(), sizeof(int32_t) * 2 * m->E);
   return NB_OK;
+}
+
+int nb_mesh_csr(const nb_mesh *m, int64_t *row_ptr, int32_t *nbr) {
+  NB_REQUIRE(m && row_ptr && nbr, NB_EINVAL, "nb_mesh_csr: NULL argument");
+  std::memcpy(row_ptr, m->row_ptr.data(), sizeof(int64_t) * (m->V + 1));
+  std::memcpy(nbr, m->nbr.data(), sizeof(int32_t) * m->nbr.size());
+  return NB_OK;
+}
+
+int nb_mesh_tile_plan(const nb_mesh *m, int rcap, int nmax, int32_t *ntiles, int32_t *ntiles_main,
+                      int64_t *nhalo, int32_t *node0, int32_t *halo_ptr, int32_t *halo,
+                      uint16_t *lnbr) {
+  NB_REQUIRE(m && ntiles && ntiles_main && nhalo, NB_EINVAL, "nb_mesh_tile_plan: NULL argument");
+  NB_REQUIRE(rcap >= 1 && rcap <= 65535 && nmax >= 1 && nmax <= 1024, NB_EINVAL,
+             "nb_mesh_tile_plan: rcap in [1, 65535], nmax in [1, 1024]");
+  NB_GUARD_BEGIN
+  std::vector<int32_t> n0, hp, h;
+  std::vector<uint16_t> ln;
+  int mh = 0, me = 0, nm = 0;
+  nb::build_tile_plan_host(m, rcap, nmax, n0, hp, h, ln, mh, me, nm);
+  *ntiles = (int32_t)n0.size() - 1;
+  *ntiles_main = nm;
+  *nhalo = (int64_t)h.size();
+  if (node0) std::memcpy(node0, n0.data(), sizeof(int32_t) * n0.size());
+  if (halo_ptr) std::memcpy(halo_ptr, hp.data(), sizeof(int32_t) * hp.size());
+  if (halo) std::memcpy(halo, h.data(), sizeof(int32_t) * h.size());
+  if (lnbr) std::memcpy(lnbr, ln.data(), sizeof(uint16_t) * ln.size());
+  return NB_OK;
+  NB_GUARD_END
 }
 
 int nb_mesh_cap_begin(const nb_mesh *m, int64_t *cap_begin) {

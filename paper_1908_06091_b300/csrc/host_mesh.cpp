@@ -479,22 +479,55 @@ void build_geometry(const nb_mesh *m, double R, std::vector<double> &vol, std::v
 
 // ------------------------------------------------------------- tile plans
 
-// Tiles of `tile_nodes` consecutive nodes over [0, cap_begin), then the pole
-// block [cap_begin, V) in tiles of its own.  halo[t] = sorted neighbours of
-// tile t outside it; lnbr[p] = shared-memory row of CSR neighbour p
-// (0..n-1 inside the tile, n + k for halo entry k).
-void build_tile_plan_host(const nb_mesh *m, int tile_nodes, std::vector<int32_t> &node0,
+// Variable-size tiles of consecutive nodes for the shared-memory staged
+// kernels.  Tiles are grown greedily along the node order while the tile's
+// own nodes plus its halo (neighbours outside the tile) fit `rcap` staged
+// rows and the tile has at most `nmax` nodes.  Main tiles cover
+// [0, cap_begin), pole tiles [cap_begin, V).  halo[t] lists the sorted halo
+// nodes of tile t; lnbr[p] is the staged row of CSR neighbour p (0..n-1 the
+// tile's own nodes, n + k halo entry k).
+void build_tile_plan_host(const nb_mesh *m, int rcap, int nmax, std::vector<int32_t> &node0,
                           std::vector<int32_t> &halo_ptr, std::vector<int32_t> &halo,
                           std::vector<uint16_t> &lnbr, int &max_halo, int &max_entries,
                           int &ntiles_main) {
+  const int64_t V = m->V;
+  std::vector<int32_t> mark(V, -1);
   node0.clear();
-  for (int64_t s = 0; s < m->cap_begin; s += tile_nodes) node0.push_back((int32_t)s);
+  int32_t stamp = 0;
+  auto cover = [&](int64_t a, int64_t b) {
+    int64_t n0 = a;
+    while (n0 < b) {
+      ++stamp;
+      int64_t n1 = n0, H = 0;
+      while (n1 < b && n1 - n0 < nmax) {
+        const int64_t v = n1;
+        int64_t add = 0;
+        for (int64_t p = m->row_ptr[v]; p < m->row_ptr[v + 1]; ++p) {
+          const int32_t j = m->nbr[p];
+          if ((j < n0 || j > v) && mark[j] != stamp) ++add;
+        }
+        const int64_t inhalo = (mark[v] == stamp) ? 1 : 0;
+        const int64_t newH = H + add - inhalo;
+        if (n1 > n0 && (n1 - n0 + 1) + newH > rcap) break;
+        for (int64_t p = m->row_ptr[v]; p < m->row_ptr[v + 1]; ++p) {
+          const int32_t j = m->nbr[p];
+          if (j < n0 || j > v) mark[j] = stamp;
+        }
+        mark[v] = -2;  // inside the tile now
+        H = newH;
+        ++n1;
+      }
+      node0.push_back((int32_t)n0);
+      n0 = n1;
+    }
+  };
+  cover(0, m->cap_begin);
   ntiles_main = (int)node0.size();
-  for (int64_t s = m->cap_begin; s < m->V; s += tile_nodes) node0.push_back((int32_t)s);
-  node0.push_back((int32_t)m->V);
+  cover(m->cap_begin, V);
+  node0.push_back((int32_t)V);
   const int nt = (int)node0.size() - 1;
   std::vector<std::vector<int32_t>> hal(nt);
-  lnbr.assign(m->row_ptr[m->V], 0);
+  lnbr.assign(m->row_ptr[V], 0);
   std::vector<int> hmax(nt, 0), emax(nt, 0);
 #pragma omp parallel for schedule(dynamic, 64)
   for (int t = 0; t < nt; ++t) {

@@ -63,9 +63,10 @@ struct nb_mesh : nb::RefCounted {
   ~nb_mesh() override { nb::release(grid); }
 };
 
-// Per-tile halo plan of the tiled kernels for one tile size.
+// Per-tile halo plan of the staged kernels for one staged-row capacity.
 struct TilePlan {
-  int tile_nodes = 0;
+  int rcap = 0;        // staged rows per tile (own nodes + halo)
+  int nmax = 0;        // nodes per tile at most
   int ntiles = 0;
   int ntiles_main = 0;               // tiles before the pole block
   int max_halo = 0;
@@ -103,7 +104,7 @@ struct nb_method : nb::RefCounted {
   int tile_nodes = 0;
   int compensated = 1;
   std::mutex plan_mu;
-  std::map<int, std::unique_ptr<TilePlan>> plans;
+  std::map<std::pair<int, int>, std::unique_ptr<TilePlan>> plans;  // (rcap, nmax)
   ~nb_method() override;
 };
 
@@ -123,7 +124,7 @@ nb_mesh *build_mesh(nb_grid *grid, int reorder);
 void build_geometry(const nb_mesh *m, double R, std::vector<double> &vol, std::vector<double> &S,
                     std::vector<double> &T, std::vector<double> &east, std::vector<double> &north);
 // host side of a tile plan: node0[ntiles+1], halo_ptr[ntiles+1], halo[], lnbr[2E]
-void build_tile_plan_host(const nb_mesh *m, int tile_nodes, std::vector<int32_t> &node0,
+void build_tile_plan_host(const nb_mesh *m, int rcap, int nmax, std::vector<int32_t> &node0,
                           std::vector<int32_t> &halo_ptr, std::vector<int32_t> &halo,
                           std::vector<uint16_t> &lnbr, int &max_halo, int &max_entries,
                           int &ntiles_main);

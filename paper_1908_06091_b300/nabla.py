@@ -67,6 +67,9 @@ SIGNATURES = {
     "nb_mesh_triangles": [_P, _P],
     "nb_mesh_edges": [_P, _P],
     "nb_mesh_cap_begin": [_P, _I64P],
+    "nb_mesh_csr": [_P, _P, _P],
+    "nb_mesh_tile_plan": [_P, _I, _I, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                          _I64P, _P, _P, _P, _P],
     "nb_method_create": [_P, ctypes.c_double, ctypes.POINTER(_P)],
     "nb_method_release": [_P],
     "nb_method_dual_volumes": [_P, _P],
@@ -84,6 +87,7 @@ SIGNATURES = {
     "nb_nabla_apply": [_P, _I, _FP, _FP, _FP, _P],
     "nb_nabla_apply_host": [_P, _I, _P, _P, _FP, _FP, _FP, _P],
     "nb_launch_count": [_I64P],
+    "nb_device_status": [_I, ctypes.POINTER(ctypes.c_int32)],
 }
 
 
@@ -117,6 +121,13 @@ def version() -> str:
 def launch_count() -> int:
     c = ctypes.c_int64()
     check(lib().nb_launch_count(ctypes.byref(c)))
+    return c.value
+
+
+def device_status(clear: bool = False) -> int:
+    """0 if every kernel ran normally, else the NB_* code a kernel recorded."""
+    c = ctypes.c_int32()
+    check(lib().nb_device_status(1 if clear else 0, ctypes.byref(c)))
     return c.value
 
 
@@ -187,6 +198,26 @@ class Mesh(_Handle):
         out = np.zeros((self.E, 2), dtype=np.int32)
         check(lib().nb_mesh_edges(self._h, out.ctypes.data))
         return out
+
+    def csr(self):
+        rp = np.zeros(self.V + 1, dtype=np.int64)
+        nb = np.zeros(2 * self.E, dtype=np.int32)
+        check(lib().nb_mesh_csr(self._h, rp.ctypes.data, nb.ctypes.data))
+        return rp, nb
+
+    def tile_plan(self, rcap: int, nmax: int = 256):
+        """(node0, halo_ptr, halo, lnbr, ntiles_main) of the staged kernels' plan."""
+        nt, nm, nh = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        check(lib().nb_mesh_tile_plan(self._h, rcap, nmax, ctypes.byref(nt), ctypes.byref(nm),
+                                      ctypes.byref(nh), None, None, None, None))
+        node0 = np.zeros(nt.value + 1, dtype=np.int32)
+        hptr = np.zeros(nt.value + 1, dtype=np.int32)
+        halo = np.zeros(max(nh.value, 1), dtype=np.int32)
+        lnbr = np.zeros(2 * self.E, dtype=np.uint16)
+        check(lib().nb_mesh_tile_plan(self._h, rcap, nmax, ctypes.byref(nt), ctypes.byref(nm),
+                                      ctypes.byref(nh), node0.ctypes.data, hptr.ctypes.data,
+                                      halo.ctypes.data, lnbr.ctypes.data))
+        return node0, hptr, halo[:nh.value], lnbr, nm.value
 
 
 class Method(_Handle):

@@ -23,9 +23,10 @@ Vector winds are W = k x grad(psi) + grad(chi) from two harmonic sums (their
 divergence is lap(chi), their curl lap(psi)), in local (east, north)
 components, plus the solid-body wind u = U cos(lat), v = 0.
 
-Everything runs in torch float64 on any device (CPU for the oracle's inputs,
-CUDA for large benchmark inputs), one pass over the distinct latitudes of
-the grid for the Legendre part.
+Everything is torch float64.  The Legendre part runs on the CPU over the
+distinct latitudes of the grid; the per-node sums run on any device (CPU for
+the oracle's inputs, CUDA for large benchmark inputs), all basis fields of a
+kind in one pass.
 """
 from __future__ import annotations
 
@@ -79,43 +80,50 @@ def _as_t(x, device):
     return torch.as_tensor(np.asarray(x, dtype=np.float64), device=device)
 
 
-def sh_eval(lat, lon, a, b, *, deriv: str | None = None, scale_l=None,
-            device=None) -> torch.Tensor:
-    """Evaluate the harmonic sum at nodes (float64 tensor of shape [V]).
+def sh_eval_many(lat, lon, coeffs, *, deriv: str | None = None, scale_l=None,
+                 device=None) -> torch.Tensor:
+    """Evaluate K harmonic sums at V nodes: float64 tensor [V, K].
 
+    coeffs: list of (a, b) coefficient arrays of one common lmax.
     deriv: None (value), 'lat' (d/dlat, complex step) or 'lon' (d/dlon).
     scale_l: optional per-degree multipliers (e.g. -l(l+1)/R^2 for the
-    continuous Laplacian)."""
+    continuous Laplacian).  The Legendre part runs on the CPU over the
+    distinct latitudes; the per-node sum over orders m runs on `device`."""
     device = device or (lat.device if isinstance(lat, torch.Tensor) else "cpu")
-    lat = _as_t(lat, device)
-    lon = _as_t(lon, device)
-    lmax = a.shape[0] - 1
-    A = torch.as_tensor(a, dtype=torch.float64, device=device)
-    B = torch.as_tensor(b, dtype=torch.float64, device=device)
+    lat_c = _as_t(lat, "cpu")
+    lon_d = _as_t(lon, device)
+    lmax = coeffs[0][0].shape[0] - 1
+    A = torch.as_tensor(np.stack([c[0] for c in coeffs]), dtype=torch.float64)  # [K, l, m]
+    B = torch.as_tensor(np.stack([c[1] for c in coeffs]), dtype=torch.float64)
     if scale_l is not None:
-        sl = torch.as_tensor(np.asarray(scale_l, dtype=np.float64), device=device)[:, None]
+        sl = torch.as_tensor(np.asarray(scale_l, dtype=np.float64))[None, :, None]
         A = A * sl
         B = B * sl
-    ulat, inv = torch.unique(lat, return_inverse=True)
+    ulat, inv = torch.unique(lat_c, return_inverse=True)
     h = 1e-30
     if deriv == "lat":
-        P = legendre_bar(lmax, ulat.to(torch.complex128) + 1j * h)
-        P = P.imag / h
+        P = legendre_bar(lmax, ulat.to(torch.complex128) + 1j * h).imag / h
     else:
         P = legendre_bar(lmax, ulat)
-    # row coefficients per order m: [lmax+1 (m), rows]
-    Am = torch.einsum("lm,lmr->mr", A, P)
-    Bm = torch.einsum("lm,lmr->mr", B, P)
-    out = torch.zeros_like(lon)
-    c1, s1 = torch.cos(lon), torch.sin(lon)
-    cm, sm = torch.ones_like(lon), torch.zeros_like(lon)
+    Am = torch.einsum("klm,lmr->mrk", A, P).to(device)  # [m, rows, K]
+    Bm = torch.einsum("klm,lmr->mrk", B, P).to(device)
+    inv = inv.to(device)
+    out = torch.zeros((lon_d.shape[0], len(coeffs)), dtype=torch.float64, device=device)
+    c1, s1 = torch.cos(lon_d), torch.sin(lon_d)
+    cm, sm = torch.ones_like(lon_d), torch.zeros_like(lon_d)
     for m in range(lmax + 1):
         if deriv == "lon":
-            out += m * (-Am[m][inv] * sm + Bm[m][inv] * cm)
+            out += m * (Bm[m][inv] * cm[:, None] - Am[m][inv] * sm[:, None])
         else:
-            out += Am[m][inv] * cm + Bm[m][inv] * sm
+            out += Am[m][inv] * cm[:, None] + Bm[m][inv] * sm[:, None]
         cm, sm = cm * c1 - sm * s1, sm * c1 + cm * s1
     return out
+
+
+def sh_eval(lat, lon, a, b, *, deriv: str | None = None, scale_l=None,
+            device=None) -> torch.Tensor:
+    """Evaluate one harmonic sum at the nodes (float64 tensor of shape [V])."""
+    return sh_eval_many(lat, lon, [(a, b)], deriv=deriv, scale_l=scale_l, device=device)[:, 0]
 
 
 def level_weights(nlev: int, seed: int) -> np.ndarray:
@@ -127,11 +135,8 @@ def level_weights(nlev: int, seed: int) -> np.ndarray:
 
 def scalar_basis(lat, lon, lmax: int, seed: int, device=None) -> torch.Tensor:
     """[V][N_BASIS] float64 harmonic basis fields."""
-    cols = []
-    for bidx in range(N_BASIS):
-        a, b = sh_coeffs(lmax, seed * 1000 + bidx)
-        cols.append(sh_eval(lat, lon, a, b, device=device))
-    return torch.stack(cols, dim=1)
+    coeffs = [sh_coeffs(lmax, seed * 1000 + bidx) for bidx in range(N_BASIS)]
+    return sh_eval_many(lat, lon, coeffs, device=device)
 
 
 def scalar_field(lat, lon, nlev: int, lmax: int, seed: int = BASE_SEED, device=None) -> torch.Tensor:
@@ -144,21 +149,17 @@ def scalar_field(lat, lon, nlev: int, lmax: int, seed: int = BASE_SEED, device=N
 def wind_basis(lat, lon, lmax: int, seed: int, R: float, device=None) -> torch.Tensor:
     """[V][N_BASIS][2] float64 winds W_b = k x grad(psi_b) + grad(chi_b)."""
     device = device or (lat.device if isinstance(lat, torch.Tensor) else "cpu")
-    latt = _as_t(lat, device)
-    coslat = torch.cos(latt)
-    out = []
-    for bidx in range(N_BASIS):
-        ap, bp = sh_coeffs(lmax, seed * 1000 + 100 + bidx)
-        ac, bc = sh_coeffs(lmax, seed * 1000 + 200 + bidx)
-        ap, bp, ac, bc = (x * WIND_SCALE for x in (ap, bp, ac, bc))
-        psi_lat = sh_eval(lat, lon, ap, bp, deriv="lat", device=device)
-        psi_lon = sh_eval(lat, lon, ap, bp, deriv="lon", device=device)
-        chi_lat = sh_eval(lat, lon, ac, bc, deriv="lat", device=device)
-        chi_lon = sh_eval(lat, lon, ac, bc, deriv="lon", device=device)
-        u = (-psi_lat + chi_lon / coslat) / R
-        v = (psi_lon / coslat + chi_lat) / R
-        out.append(torch.stack([u, v], dim=1))
-    return torch.stack(out, dim=1)
+    coslat = torch.cos(_as_t(lat, device))[:, None]
+    scale = lambda c: (c[0] * WIND_SCALE, c[1] * WIND_SCALE)
+    psi = [scale(sh_coeffs(lmax, seed * 1000 + 100 + b)) for b in range(N_BASIS)]
+    chi = [scale(sh_coeffs(lmax, seed * 1000 + 200 + b)) for b in range(N_BASIS)]
+    psi_lat = sh_eval_many(lat, lon, psi, deriv="lat", device=device)
+    psi_lon = sh_eval_many(lat, lon, psi, deriv="lon", device=device)
+    chi_lat = sh_eval_many(lat, lon, chi, deriv="lat", device=device)
+    chi_lon = sh_eval_many(lat, lon, chi, deriv="lon", device=device)
+    u = (-psi_lat + chi_lon / coslat) / R
+    v = (psi_lon / coslat + chi_lat) / R
+    return torch.stack([u, v], dim=2)
 
 
 def wind_field(lat, lon, nlev: int, lmax: int, R: float, seed: int = BASE_SEED,

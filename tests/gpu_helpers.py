@@ -72,4 +72,5 @@ def run_op(meth, fs, op: str, xin: torch.Tensor, scratch=None) -> torch.Tensor:
     out = fs.create_field(nvar=nout, fill=float("nan"))
     nabla.apply(meth, op, xin, out, scratch=scratch)
     torch.cuda.synchronize()
+    assert nabla.device_status() == 0, "a kernel recorded a device error"
     return out

@@ -108,3 +108,32 @@ def test_method_requires_a_device_and_reports_it():
     with pytest.raises(nabla.NablaError) as ei:
         nabla.Method(m)
     assert ei.value.code == nabla.NB_ECUDA
+
+
+@pytest.mark.parametrize("N,rcap,nmax", [(16, 12, 256), (48, 87, 256), (64, 175, 256), (64, 40, 8)])
+def test_tile_plan_fits_stage_and_maps_every_neighbour(N, rcap, nmax):
+    """Host check of the staged kernels' plan: every tile's own nodes plus
+    halo fit the stage, tiles cover the nodes in order with the pole block
+    separate, and each staged-row index resolves to the CSR neighbour."""
+    m = nabla.Mesh(nabla.Grid(N), 1)
+    rp, nbr = m.csr()
+    node0, hptr, halo, lnbr, ntm = m.tile_plan(rcap, nmax)
+    assert node0[0] == 0 and node0[-1] == m.V and np.all(np.diff(node0) > 0)
+    assert node0[ntm] == m.cap_begin
+    n = np.diff(node0)
+    H = np.diff(hptr)
+    assert np.all(n <= nmax)
+    assert np.all(n + H <= np.maximum(rcap, 1 + np.diff(rp)[node0[:-1]]))
+    for t in range(len(n)):
+        a, b = node0[t], node0[t + 1]
+        h = halo[hptr[t]:hptr[t + 1]]
+        assert np.all(np.diff(h) > 0) and not np.any((h >= a) & (h < b))
+        p = np.arange(rp[a], rp[b])
+        loc = lnbr[p].astype(np.int64)
+        hi = np.clip(loc - (b - a), 0, max(len(h) - 1, 0))
+        res = np.where(loc < b - a, a + loc, h[hi] if len(h) else a + loc)
+        assert np.array_equal(res, nbr[p])
+    # neighbour lists agree with the edge list
+    e = m.edges()
+    deg = np.bincount(e.ravel(), minlength=m.V)
+    assert np.array_equal(np.diff(rp), deg)
