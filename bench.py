@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--variant", type=int, default=0, help="kernel variant (0 auto, 1 direct, 2 tiled)")
     p.add_argument("--tile", type=int, default=0)
+    p.add_argument("--stages", type=int, default=0)
+    p.add_argument("--stage-kb", type=int, default=0)
     return p.parse_args()
 
 
@@ -194,6 +196,8 @@ def bench_ours(a):
     mesh = nabla.Mesh(grid, 1)
     method = nabla.Method(mesh)
     method.set_kernel(a.variant, a.tile)
+    if a.stages:
+        method.set_staging(a.stages, a.stage_kb)
     setup_s = time.time() - t0
     V, E, L = mesh.V, mesh.E, a.nlev
     fs, f, uv = make_inputs(nabla, synth, grid, mesh, method, L, a.lmax, torch.float32, device)

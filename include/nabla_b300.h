@@ -226,6 +226,12 @@ enum { NB_KERNEL_AUTO = 0, NB_KERNEL_DIRECT = 1, NB_KERNEL_TILED = 2 };
  * tuning).  tile_nodes is the tiled variant's nodes per tile (0 = default). */
 int nb_method_set_kernel(nb_method *method, int variant, int tile_nodes);
 
+/* Pipeline shape of the shared-memory staged kernels: nstages stages of
+ * stage_kb KB each (nstages * stage_kb <= 224; 0 = defaults 4 x 48 KB).
+ * Tile plans are sized so that a tile's own columns plus its halo columns
+ * fill one stage. */
+int nb_method_set_staging(nb_method *method, int nstages, int stage_kb);
+
 /* Accumulation mode of the FP32 path: 1 = compensated (Kahan, default),
  * 0 = plain FP32 FMA chain (for accuracy/throughput comparison). */
 int nb_method_set_compensated(nb_method *method, int on);

@@ -176,7 +176,7 @@ int nb_mesh_tile_plan(const nb_mesh *m, int rcap, int nmax, int32_t *ntiles, int
   std::vector<int32_t> n0, hp, h;
   std::vector<uint16_t> ln;
   int mh = 0, me = 0, nm = 0;
-  nb::build_tile_plan_host(m, rcap, nmax, n0, hp, h, ln, mh, me, nm);
+  nb::build_tile_plan_host(m, rcap, nmax, 1 << 20, n0, hp, h, ln, mh, me, nm);
   *ntiles = (int32_t)n0.size() - 1;
   *ntiles_main = nm;
   *nhalo = (int64_t)h.size();
@@ -240,6 +240,16 @@ int nb_method_set_kernel(nb_method *m, int variant, int tile_nodes) {
              "nb_method_set_kernel: tile_nodes must be 0 or in [8, 1024]");
   m->kernel_variant = variant;
   m->tile_nodes = tile_nodes;
+  return NB_OK;
+}
+
+int nb_method_set_staging(nb_method *m, int nstages, int stage_kb) {
+  NB_REQUIRE(m, NB_EINVAL, "nb_method_set_staging: NULL method");
+  NB_REQUIRE((nstages == 0 && stage_kb == 0) ||
+                 (nstages >= 2 && nstages <= 8 && stage_kb >= 8 && nstages * stage_kb <= 224),
+             NB_EINVAL, "nb_method_set_staging: need 2 <= nstages <= 8, stage_kb >= 8, product <= 224");
+  m->nstages = nstages;
+  m->stage_kb = stage_kb;
   return NB_OK;
 }
 

@@ -482,11 +482,11 @@ void build_geometry(const nb_mesh *m, double R, std::vector<double> &vol, std::v
 // Variable-size tiles of consecutive nodes for the shared-memory staged
 // kernels.  Tiles are grown greedily along the node order while the tile's
 // own nodes plus its halo (neighbours outside the tile) fit `rcap` staged
-// rows and the tile has at most `nmax` nodes.  Main tiles cover
+// rows, the tile has at most `nmax` nodes and at most `ecap` CSR entries.  Main tiles cover
 // [0, cap_begin), pole tiles [cap_begin, V).  halo[t] lists the sorted halo
 // nodes of tile t; lnbr[p] is the staged row of CSR neighbour p (0..n-1 the
 // tile's own nodes, n + k halo entry k).
-void build_tile_plan_host(const nb_mesh *m, int rcap, int nmax, std::vector<int32_t> &node0,
+void build_tile_plan_host(const nb_mesh *m, int rcap, int nmax, int ecap, std::vector<int32_t> &node0,
                           std::vector<int32_t> &halo_ptr, std::vector<int32_t> &halo,
                           std::vector<uint16_t> &lnbr, int &max_halo, int &max_entries,
                           int &ntiles_main) {
@@ -501,6 +501,7 @@ void build_tile_plan_host(const nb_mesh *m, int rcap, int nmax, std::vector<int3
       int64_t n1 = n0, H = 0;
       while (n1 < b && n1 - n0 < nmax) {
         const int64_t v = n1;
+        if (n1 > n0 && m->row_ptr[v + 1] - m->row_ptr[n0] > ecap) break;
         int64_t add = 0;
         for (int64_t p = m->row_ptr[v]; p < m->row_ptr[v + 1]; ++p) {
           const int32_t j = m->nbr[p];

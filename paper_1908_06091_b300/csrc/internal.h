@@ -8,6 +8,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/nabla_b300.h"
@@ -67,6 +68,7 @@ struct nb_mesh : nb::RefCounted {
 struct TilePlan {
   int rcap = 0;        // staged rows per tile (own nodes + halo)
   int nmax = 0;        // nodes per tile at most
+  int ecap = 0;        // CSR entries per tile at most
   int ntiles = 0;
   int ntiles_main = 0;               // tiles before the pole block
   int max_halo = 0;
@@ -101,10 +103,12 @@ struct nb_method : nb::RefCounted {
   int64_t device_bytes = 0;
   // kernel control
   int kernel_variant = 0;  // NB_KERNEL_*
-  int tile_nodes = 0;
+  int tile_nodes = 0;   // staged kernels: nodes per tile at most (0 = 256)
+  int nstages = 0;      // staged kernels: pipeline stages (0 = default)
+  int stage_kb = 0;     // staged kernels: KB per stage (0 = default)
   int compensated = 1;
   std::mutex plan_mu;
-  std::map<std::pair<int, int>, std::unique_ptr<TilePlan>> plans;  // (rcap, nmax)
+  std::map<std::tuple<int, int, int>, std::unique_ptr<TilePlan>> plans;  // (rcap, nmax, ecap)
   ~nb_method() override;
 };
 
@@ -124,7 +128,7 @@ nb_mesh *build_mesh(nb_grid *grid, int reorder);
 void build_geometry(const nb_mesh *m, double R, std::vector<double> &vol, std::vector<double> &S,
                     std::vector<double> &T, std::vector<double> &east, std::vector<double> &north);
 // host side of a tile plan: node0[ntiles+1], halo_ptr[ntiles+1], halo[], lnbr[2E]
-void build_tile_plan_host(const nb_mesh *m, int rcap, int nmax, std::vector<int32_t> &node0,
+void build_tile_plan_host(const nb_mesh *m, int rcap, int nmax, int ecap, std::vector<int32_t> &node0,
                           std::vector<int32_t> &halo_ptr, std::vector<int32_t> &halo,
                           std::vector<uint16_t> &lnbr, int &max_halo, int &max_entries,
                           int &ntiles_main);

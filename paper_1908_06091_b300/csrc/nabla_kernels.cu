@@ -99,12 +99,15 @@ int method_upload(nb_method *m) {
   const int64_t V = mesh->V, E = mesh->E, P = 2 * E;
   NB_CUDA(cudaGetDevice(&m->device));
   int64_t &b = m->device_bytes;
-  std::vector<int32_t> rp(V + 1);
+  // row_ptr is padded with 8 copies of its last entry so that 16-byte
+  // aligned bounding copies of any node range stay inside the allocation
+  std::vector<int32_t> rp(V + 1 + 8);
   for (int64_t i = 0; i <= V; ++i) rp[i] = (int32_t)mesh->row_ptr[i];
+  for (int64_t i = V + 1; i < V + 9; ++i) rp[i] = (int32_t)mesh->row_ptr[V];
   int st;
 #define UP(dst, src, n) \
   if ((st = dev_upload(&(dst), (src), (n), b)) != NB_OK) return st;
-  UP(m->d_row_ptr, rp.data(), V + 1);
+  UP(m->d_row_ptr, rp.data(), V + 9);
   UP(m->d_nbr, mesh->nbr.data(), P);
   UP(m->d_nbr_edge, mesh->nbr_edge.data(), P);
   UP(m->d_vol, m->vol.data(), V);

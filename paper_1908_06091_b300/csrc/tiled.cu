@@ -139,60 +139,107 @@ struct TiledArgs {
   float *out;
   int64_t out_stride;  // elements
   int nlev;
-  int G;               // 4-level groups per column
+  int G;               // items per node (4 levels each)
   uint64_t g_magic;    // item / G == (item * g_magic) >> g_shift, exact for items < 2^24
   uint32_t g_shift;
   uint32_t copy_bytes; // bytes copied per column: the real data rounded up to 16
+  uint32_t off_w, off_l, off_r;  // stage offsets of the staged weights, rows, row pointers
   uint32_t stage_bytes;
+  int nstages;
   int *status;
   uint64_t timeout_ns;
 };
 
-// Issue the copies of tile t into the stage at `rows` (warp 0 only).
-__device__ __forceinline__ void issue_tile(const TiledArgs &a, int t, uint32_t rows, uint32_t bar,
+// Issue the copies of tile t into the stage at `stage` (one whole warp): the
+// tile's column block, each halo column, and 16-byte aligned bounding
+// ranges of the tile's CSR weights, staged-row indices and row pointers, all
+// as TMA bulk copies completing on the stage's "full" barrier.
+__device__ __forceinline__ void issue_tile(const TiledArgs &a, int t, uint32_t stage, uint32_t bar,
                                            int lane) {
   const int32_t n0 = __ldg(a.tile_node0 + t), n1 = __ldg(a.tile_node0 + t + 1);
   const int32_t h0 = __ldg(a.halo_ptr + t), h1 = __ldg(a.halo_ptr + t + 1);
+  const int32_t pa = __ldg(a.row_ptr + n0), pb = __ldg(a.row_ptr + n1);
   const uint32_t n = (uint32_t)(n1 - n0), H = (uint32_t)(h1 - h0);
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  const int32_t wa = pa & ~1, wb = (pb + 1) & ~1;
+  const int32_t la = pa & ~7, lb = (pb + 7) & ~7;
+  const int32_t ra = n0 & ~3, rb = (n1 + 4) & ~3;
   const uint32_t body = (n - 1) * a.row_bytes + a.copy_bytes;
-  if (lane == 0) mbar_expect_tx(bar, body + H * a.copy_bytes);
+  const uint32_t wbytes = (uint32_t)(wb - wa) * 8u, lbytes = (uint32_t)(lb - la) * 2u,
+                 rbytes = (uint32_t)(rb - ra) * 4u;
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (lane == 0) mbar_expect_tx(bar, body + H * a.copy_bytes + wbytes + lbytes + rbytes);
   __syncwarp();
-  if (lane == 0) bulk_g2s(rows, a.in + (int64_t)n0 * a.in_stride * 4, body, bar);
+  if (lane == 0) bulk_g2s(stage, a.in + (int64_t)n0 * a.in_stride * 4, body, bar);
+  if (lane == 1) bulk_g2s(stage + a.off_w, a.w32 + wa, wbytes, bar);
+  if (lane == 2) bulk_g2s(stage + a.off_l, a.lnbr + la, lbytes, bar);
+  if (lane == 3) bulk_g2s(stage + a.off_r, a.row_ptr + ra, rbytes, bar);
   for (uint32_t h = lane; h < H; h += 32) {
     const int32_t node = __ldg(a.halo + h0 + h);
-    bulk_g2s(rows + (n + h) * a.row_bytes, a.in + (int64_t)node * a.in_stride * 4, a.copy_bytes, bar);
+    bulk_g2s(stage + (n + h) * a.row_bytes, a.in + (int64_t)node * a.in_stride * 4, a.copy_bytes, bar);
   }
 }
 
+// Staged views of one tile: CSR range, weights, staged-row indices.
+struct TileView {
+  int32_t n0, n1;
+  const char *rows;
+  const float2 *w;     // w[p - wa]
+  const uint16_t *lr;  // lr[p - la]
+  const int32_t *rp;   // rp[node - ra]
+  int32_t wa, la, ra;
+  __device__ __forceinline__ TileView(const TiledArgs &a, int t, const char *stage) {
+    n0 = __ldg(a.tile_node0 + t);
+    n1 = __ldg(a.tile_node0 + t + 1);
+    rows = stage;
+    ra = n0 & ~3;
+    rp = reinterpret_cast<const int32_t *>(stage + a.off_r);
+    const int32_t pa = rp[n0 - ra];
+    wa = pa & ~1;
+    la = pa & ~7;
+    w = reinterpret_cast<const float2 *>(stage + a.off_w);
+    lr = reinterpret_cast<const uint16_t *>(stage + a.off_l);
+  }
+};
+
+// Items [i0, i1) of tile t, one per lane of the calling warp and stride 32.
 template <bool COMP>
-__device__ __forceinline__ void grad_tile(const TiledArgs &a, int t, const char *rows) {
-  const int32_t n0 = __ldg(a.tile_node0 + t), n1 = __ldg(a.tile_node0 + t + 1);
-  const uint32_t items = (uint32_t)(n1 - n0) * a.G;
+__device__ __forceinline__ void grad_tile(const TiledArgs &a, int t, const char *stage, int part,
+                                          int nparts) {
+  const TileView v(a, t, stage);
+  const uint32_t items = (uint32_t)(v.n1 - v.n0) * a.G;
+  const uint32_t i0 = (uint32_t)(((uint64_t)items * part) / nparts);
+  const uint32_t i1 = (uint32_t)(((uint64_t)items * (part + 1)) / nparts);
   const bool pole = t >= a.ntiles_main;
-  for (uint32_t item = threadIdx.x; item < items; item += blockDim.x) {
+  for (uint32_t item = i0 + (threadIdx.x & 31); item < i1; item += 32) {
     const uint32_t il = (uint32_t)(((uint64_t)item * a.g_magic) >> a.g_shift);
     const uint32_t c = item - il * a.G;
     const int l0 = 4 * (int)c;
-    const int64_t node = n0 + il;
-    const int32_t p0 = __ldg(a.row_ptr + node), p1 = __ldg(a.row_ptr + node + 1);
-    const char *col = rows + c * 16;
+    const int64_t node = v.n0 + il;
+    const int32_t p0 = v.rp[node - v.ra], p1 = v.rp[node + 1 - v.ra];
+    const char *col = v.rows + c * 16;
     const float4 fi = *reinterpret_cast<const float4 *>(col + il * a.row_bytes);
     float gx[4], gy[4];
     if (!pole) {
       const f2_t fi01 = pk(fi.x, fi.y), fi23 = pk(fi.z, fi.w);
       Kahan2<COMP> ax01, ax23, ay01, ay23;
-      for (int32_t p = p0; p < p1; ++p) {
-        const uint32_t lr = __ldg(a.lnbr + p);
-        const float2 w = __ldg(a.w32 + p);
-        const float4 fj = *reinterpret_cast<const float4 *>(col + lr * a.row_bytes);
+      auto body = [&](const float2 w, const float4 fj) {
         const f2_t d01 = sub2(pk(fj.x, fj.y), fi01), d23 = sub2(pk(fj.z, fj.w), fi23);
         const f2_t wx = pk(w.x, w.x), wy = pk(w.y, w.y);
         ax01.add_prod(wx, d01);
         ax23.add_prod(wx, d23);
         ay01.add_prod(wy, d01);
         ay23.add_prod(wy, d23);
+      };
+      int32_t p = p0;
+      for (; p + 1 < p1; p += 2) {
+        const float2 w0 = v.w[p - v.wa], w1 = v.w[p + 1 - v.wa];
+        const uint32_t r0 = v.lr[p - v.la], r1 = v.lr[p + 1 - v.la];
+        const float4 f0 = *reinterpret_cast<const float4 *>(col + r0 * a.row_bytes);
+        const float4 f1 = *reinterpret_cast<const float4 *>(col + r1 * a.row_bytes);
+        body(w0, f0);
+        body(w1, f1);
       }
+      if (p < p1) body(v.w[p - v.wa], *reinterpret_cast<const float4 *>(col + v.lr[p - v.la] * a.row_bytes));
       upk(ax01.value(), gx[0], gx[1]);
       upk(ax23.value(), gx[2], gx[3]);
       upk(ay01.value(), gy[0], gy[1]);
@@ -201,9 +248,8 @@ __device__ __forceinline__ void grad_tile(const TiledArgs &a, int t, const char 
       double sx[4] = {0, 0, 0, 0}, sy[4] = {0, 0, 0, 0};
       const float fiv[4] = {fi.x, fi.y, fi.z, fi.w};
       for (int32_t p = p0; p < p1; ++p) {
-        const uint32_t lr = __ldg(a.lnbr + p);
         const double2 w = __ldg(a.w64 + p);
-        const float4 fj = *reinterpret_cast<const float4 *>(col + lr * a.row_bytes);
+        const float4 fj = *reinterpret_cast<const float4 *>(col + v.lr[p - v.la] * a.row_bytes);
         const float fjv[4] = {fj.x, fj.y, fj.z, fj.w};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -233,132 +279,166 @@ __device__ __forceinline__ void grad_tile(const TiledArgs &a, int t, const char 
   }
 }
 
-// div / curl: the (u, v) columns are interleaved, a 4-level group is 32 bytes.
+// div / curl.  A staged (u, v) column is a sequence of 16-byte units of two
+// levels each; item c of a node takes units c and c + G, so that every
+// shared-memory load of a warp reads consecutive 16-byte words.
 template <bool COMP>
-__device__ __forceinline__ void divcurl_tile(const TiledArgs &a, int t, const char *rows) {
-  const int32_t n0 = __ldg(a.tile_node0 + t), n1 = __ldg(a.tile_node0 + t + 1);
-  const uint32_t items = (uint32_t)(n1 - n0) * a.G;
+__device__ __forceinline__ void divcurl_tile(const TiledArgs &a, int t, const char *stage, int part,
+                                             int nparts) {
+  const TileView v(a, t, stage);
+  const uint32_t items = (uint32_t)(v.n1 - v.n0) * a.G;
+  const uint32_t i0 = (uint32_t)(((uint64_t)items * part) / nparts);
+  const uint32_t i1 = (uint32_t)(((uint64_t)items * (part + 1)) / nparts);
   const bool pole = t >= a.ntiles_main;
-  for (uint32_t item = threadIdx.x; item < items; item += blockDim.x) {
+  const int units = (a.nlev + 1) / 2;
+  for (uint32_t item = i0 + (threadIdx.x & 31); item < i1; item += 32) {
     const uint32_t il = (uint32_t)(((uint64_t)item * a.g_magic) >> a.g_shift);
     const uint32_t c = item - il * a.G;
-    const int l0 = 4 * (int)c;
-    const int64_t node = n0 + il;
-    const int32_t p0 = __ldg(a.row_ptr + node), p1 = __ldg(a.row_ptr + node + 1);
-    const char *col = rows + c * 32;
-    const float4 A = *reinterpret_cast<const float4 *>(col + il * a.row_bytes);
-    const float4 B = *reinterpret_cast<const float4 *>(col + il * a.row_bytes + 16);
+    const int u0 = (int)c, u1 = (int)c + a.G;
+    const bool has1 = u1 < units;
+    const int64_t node = v.n0 + il;
+    const int32_t p0 = v.rp[node - v.ra], p1 = v.rp[node + 1 - v.ra];
+    const char *colA = v.rows + u0 * 16;
+    const char *colB = v.rows + (has1 ? u1 : u0) * 16;
+    const float4 A = *reinterpret_cast<const float4 *>(colA + il * a.row_bytes);
+    const float4 B = *reinterpret_cast<const float4 *>(colB + il * a.row_bytes);
     float r[4];
     if (!pole) {
       // pair accumulators (sum of w.x du, sum of w.y dv) per level
       const f2_t i0 = pk(A.x, A.y), i1 = pk(A.z, A.w), i2 = pk(B.x, B.y), i3 = pk(B.z, B.w);
       Kahan2<COMP> k0, k1, k2, k3;
-      for (int32_t p = p0; p < p1; ++p) {
-        const uint32_t lr = __ldg(a.lnbr + p);
-        const float2 w = __ldg(a.w32 + p);
-        const char *cj = col + lr * a.row_bytes;
-        const float4 C = *reinterpret_cast<const float4 *>(cj);
-        const float4 D = *reinterpret_cast<const float4 *>(cj + 16);
+      auto body = [&](const float2 w, const float4 C, const float4 D) {
         const f2_t w2 = pk(w.x, w.y);
         k0.add_prod(w2, sub2(pk(C.x, C.y), i0));
         k1.add_prod(w2, sub2(pk(C.z, C.w), i1));
         k2.add_prod(w2, sub2(pk(D.x, D.y), i2));
         k3.add_prod(w2, sub2(pk(D.z, D.w), i3));
+      };
+      int32_t p = p0;
+      for (; p + 1 < p1; p += 2) {
+        const float2 w0 = v.w[p - v.wa], w1 = v.w[p + 1 - v.wa];
+        const uint32_t r0 = v.lr[p - v.la] * a.row_bytes, r1 = v.lr[p + 1 - v.la] * a.row_bytes;
+        const float4 C0 = *reinterpret_cast<const float4 *>(colA + r0);
+        const float4 D0 = *reinterpret_cast<const float4 *>(colB + r0);
+        const float4 C1 = *reinterpret_cast<const float4 *>(colA + r1);
+        const float4 D1 = *reinterpret_cast<const float4 *>(colB + r1);
+        body(w0, C0, D0);
+        body(w1, C1, D1);
+      }
+      if (p < p1) {
+        const uint32_t r0 = v.lr[p - v.la] * a.row_bytes;
+        body(v.w[p - v.wa], *reinterpret_cast<const float4 *>(colA + r0),
+             *reinterpret_cast<const float4 *>(colB + r0));
       }
       const float2 sw = __ldg(a.s32 + node);
       const f2_t sw2 = pk(sw.x, sw.y);
-      // self term joins each pair before the two halves are added
-      f2_t v[4] = {k0.value(), k1.value(), k2.value(), k3.value()};
+      const f2_t vals[4] = {k0.value(), k1.value(), k2.value(), k3.value()};
       const f2_t self[4] = {i0, i1, i2, i3};
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const f2_t q = fma2(sw2, self[k], v[k]);
+        const f2_t q = fma2(sw2, self[k], vals[k]);
         float x, y;
         upk(q, x, y);
         r[k] = __fadd_rn(x, y);
       }
     } else {
       const float iu[4] = {A.x, A.z, B.x, B.z}, iv[4] = {A.y, A.w, B.y, B.w};
-      double s[4] = {0, 0, 0, 0};
+      double sacc[4] = {0, 0, 0, 0};
       for (int32_t p = p0; p < p1; ++p) {
-        const uint32_t lr = __ldg(a.lnbr + p);
         const double2 w = __ldg(a.w64 + p);
-        const char *cj = col + lr * a.row_bytes;
-        const float4 C = *reinterpret_cast<const float4 *>(cj);
-        const float4 D = *reinterpret_cast<const float4 *>(cj + 16);
+        const uint32_t r0 = v.lr[p - v.la] * a.row_bytes;
+        const float4 C = *reinterpret_cast<const float4 *>(colA + r0);
+        const float4 D = *reinterpret_cast<const float4 *>(colB + r0);
         const float ju[4] = {C.x, C.z, D.x, D.z}, jv[4] = {C.y, C.w, D.y, D.w};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          s[k] = fma(w.x, (double)ju[k] - (double)iu[k], s[k]);
-          s[k] = fma(w.y, (double)jv[k] - (double)iv[k], s[k]);
+          sacc[k] = fma(w.x, (double)ju[k] - (double)iu[k], sacc[k]);
+          sacc[k] = fma(w.y, (double)jv[k] - (double)iv[k], sacc[k]);
         }
       }
       const double2 sw = __ldg(a.s64 + node);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        s[k] = fma(sw.x, (double)iu[k], s[k]);
-        s[k] = fma(sw.y, (double)iv[k], s[k]);
-        r[k] = (float)s[k];
+        sacc[k] = fma(sw.x, (double)iu[k], sacc[k]);
+        sacc[k] = fma(sw.y, (double)iv[k], sacc[k]);
+        r[k] = (float)sacc[k];
       }
     }
-    float *oo = a.out + node * a.out_stride + l0;
-    if (l0 + 4 <= a.nlev) {
-      __stcs(reinterpret_cast<float4 *>(oo), make_float4(r[0], r[1], r[2], r[3]));
-    } else {
-#pragma unroll
-      for (int k = 0; k < 4; ++k)
-        if (l0 + k < a.nlev) oo[k] = r[k];
+    // levels 2 u0, 2 u0 + 1 from r[0..1], levels 2 u1, 2 u1 + 1 from r[2..3]
+    float *oo = a.out + node * a.out_stride;
+    const int la0 = 2 * u0, la1 = 2 * u1;
+    if (la0 + 1 < a.nlev) __stcs(reinterpret_cast<float2 *>(oo + la0), make_float2(r[0], r[1]));
+    else oo[la0] = r[0];
+    if (has1) {
+      if (la1 + 1 < a.nlev) __stcs(reinterpret_cast<float2 *>(oo + la1), make_float2(r[2], r[3]));
+      else oo[la1] = r[2];
     }
   }
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+constexpr int kConsumerWarps = 16;
+constexpr int kStagedThreads = 32 * (kConsumerWarps + 1);
+
+// Warp-specialised pipeline.  Warp kConsumerWarps is the producer: for
+// iteration k it waits until stage k % NS has been released by every
+// consumer warp ("empty" barrier), then issues the copies of tile
+// blockIdx.x + k * gridDim.x into it ("full" barrier, transaction count).
+// Each consumer warp waits for "full", computes its 1/16 share of the
+// tile's items and releases the stage; no block-wide barrier is used.
 template <int OP, bool COMP>
-__global__ void __launch_bounds__(512, 1) staged_f32(TiledArgs a) {
+__global__ void __launch_bounds__(kStagedThreads, 1) staged_f32(TiledArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * (size_t)a.stage_bytes);
-  const uint32_t bar0 = smem_u32(&bars[0]), bar1 = smem_u32(&bars[1]);
+  const int NS = a.nstages;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)NS * a.stage_bytes);
+  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8u * NS;
   const uint32_t stage0 = smem_u32(smem);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    mbar_init(bar0, 1);
-    mbar_init(bar1, 1);
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, kConsumerWarps);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  int t = blockIdx.x;
-  // copies issued into / consumed from stage 0 and stage 1 so far
-  uint32_t issued0 = 0, issued1 = 0, done0 = 0, done1 = 0;
-  if (t < a.ntiles) {
-    if (warp == 0) issue_tile(a, t, stage0, bar0, lane);
-    issued0 = 1;
-  }
-  bool failed = false;
-  for (int k = 0; t < a.ntiles; t += gridDim.x, ++k) {
-    const int s = k & 1;
-    const int tn = t + gridDim.x;
-    if (tn < a.ntiles) {
-      if (warp == 0) issue_tile(a, tn, stage0 + (s ^ 1) * a.stage_bytes, s ? bar0 : bar1, lane);
-      if (s) ++issued0;
-      else ++issued1;
+  const int G = gridDim.x;
+  if (warp == kConsumerWarps) {
+    // producer
+    int k = 0;
+    bool failed = false;
+    for (int t = blockIdx.x; t < a.ntiles; t += G, ++k) {
+      const int s = k % NS;
+      if (k >= NS && !mbar_wait_bounded(empty0 + 8 * s, (uint32_t)(k / NS - 1) & 1u, a.timeout_ns)) {
+        failed = true;
+        break;
+      }
+      issue_tile(a, t, stage0 + s * a.stage_bytes, full0 + 8 * s, lane);
     }
-    if (!mbar_wait_bounded(s ? bar1 : bar0, (s ? done1 : done0) & 1, a.timeout_ns)) {
-      failed = true;
+    if (failed) {
+      if (lane == 0) atomicCAS(a.status, 0, (int)NB_ETIMEOUT);
+      // copies already issued (iterations k-NS .. k-1) land before exit (bounded)
+      for (int j = (k >= NS ? k - NS : 0); j < k; ++j)
+        if (!mbar_wait_bounded(full0 + 8 * (j % NS), (uint32_t)(j / NS) & 1u, a.timeout_ns)) break;
+    }
+    return;
+  }
+  // consumers
+  int k = 0;
+  for (int t = blockIdx.x; t < a.ntiles; t += G, ++k) {
+    const int s = k % NS;
+    if (!mbar_wait_bounded(full0 + 8 * s, (uint32_t)(k / NS) & 1u, a.timeout_ns)) {
+      if (lane == 0) atomicCAS(a.status, 0, (int)NB_ETIMEOUT);
       break;
     }
-    if (s) ++done1;
-    else ++done0;
-    const char *rows = reinterpret_cast<const char *>(smem) + s * a.stage_bytes;
-    if (OP == 0) grad_tile<COMP>(a, t, rows);
-    else divcurl_tile<COMP>(a, t, rows);
-    __syncthreads();
-  }
-  if (failed) {
-    if (threadIdx.x == 0) atomicCAS(a.status, 0, (int)NB_ETIMEOUT);
-    // let this CTA's own copies land (bounded) before its shared memory is released
-    for (uint32_t u = done0; u < issued0; ++u)
-      if (!mbar_wait_bounded(bar0, u & 1, a.timeout_ns)) break;
-    for (uint32_t u = done1; u < issued1; ++u)
-      if (!mbar_wait_bounded(bar1, u & 1, a.timeout_ns)) break;
+    const char *rows = reinterpret_cast<const char *>(smem) + (size_t)s * a.stage_bytes;
+    if (OP == 0) grad_tile<COMP>(a, t, rows, warp, kConsumerWarps);
+    else divcurl_tile<COMP>(a, t, rows, warp, kConsumerWarps);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(empty0 + 8 * s);
   }
 }
 
@@ -367,8 +447,9 @@ __global__ void __launch_bounds__(512, 1) staged_f32(TiledArgs a) {
 static int plan_upload(TilePlan *tp, const nb_mesh *mesh) {
   std::vector<int32_t> node0, hptr, halo;
   std::vector<uint16_t> lnbr;
-  build_tile_plan_host(mesh, tp->rcap, tp->nmax, node0, hptr, halo, lnbr, tp->max_halo,
+  build_tile_plan_host(mesh, tp->rcap, tp->nmax, tp->ecap, node0, hptr, halo, lnbr, tp->max_halo,
                        tp->max_entries, tp->ntiles_main);
+  lnbr.resize(lnbr.size() + 16, 0);  // slack for 16-byte bounding copies
   tp->ntiles = (int)node0.size() - 1;
   auto up = [&](void **dst, const void *src, size_t bytes) -> int {
     NB_CUDA(cudaMalloc(dst, std::max<size_t>(bytes, 16)));
@@ -384,14 +465,15 @@ static int plan_upload(TilePlan *tp, const nb_mesh *mesh) {
   return NB_OK;
 }
 
-static TilePlan *get_plan(nb_method *m, int rcap, int nmax, int *status) {
+static TilePlan *get_plan(nb_method *m, int rcap, int nmax, int ecap, int *status) {
   std::lock_guard<std::mutex> lk(m->plan_mu);
-  auto key = std::make_pair(rcap, nmax);
+  auto key = std::make_tuple(rcap, nmax, ecap);
   auto it = m->plans.find(key);
   if (it != m->plans.end()) return it->second.get();
   auto tp = std::make_unique<TilePlan>();
   tp->rcap = rcap;
   tp->nmax = nmax;
+  tp->ecap = ecap;
   *status = plan_upload(tp.get(), m->mesh);
   if (*status != NB_OK) return nullptr;
   TilePlan *raw = tp.get();
@@ -420,7 +502,7 @@ static int launch_staged_t(const TiledArgs &a, int grid, size_t smem, cudaStream
                                     227 * 1024);
   });
   NB_CUDA(attr_err);
-  staged_f32<OP, COMP><<<grid, 512, smem, st>>>(a);
+  staged_f32<OP, COMP><<<grid, kStagedThreads, smem, st>>>(a);
   count_launch(1);
   NB_CUDA(cudaGetLastError());
   return NB_OK;
@@ -458,13 +540,21 @@ int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, 
   const int nvar = in->nvar;
   // each 4-level group must lie inside the staged column
   if ((uint64_t)G * 16u * nvar > row_bytes) return NB_OK;
-  // two stages of ~96 KB, one 512-thread CTA per SM
-  const uint32_t stage_target = 96 * 1024;
-  const int rcap = (int)(stage_target / row_bytes);
-  if (rcap < 72) return NB_OK;  // columns too tall to stage a useful tile
+  // nstages stages of stage_kb KB, one 512-thread CTA per SM.  A stage holds
+  // the staged columns, then the tile's weights, staged-row indices and
+  // row pointers (bounding ranges, 16-byte aligned).
+  const int nstages = m->nstages > 0 ? m->nstages : 2;
+  const int stage_kb = m->stage_kb > 0 ? m->stage_kb : 96;
   const int nmax = m->tile_nodes > 0 ? m->tile_nodes : 256;
+  const int ecap = 10 * nmax;
+  const uint32_t meta_bytes = (uint32_t)((ecap + 2) * 8 + 16) + (uint32_t)((ecap + 16) * 2 + 16) +
+                              (uint32_t)((nmax + 8) * 4 + 16);
+  const uint32_t stage_target = (uint32_t)stage_kb * 1024u;
+  if (stage_target <= meta_bytes) return NB_OK;
+  const int rcap = (int)((stage_target - meta_bytes) / row_bytes);
+  if (rcap < 24) return NB_OK;  // columns too tall to stage a useful tile
   int status = NB_OK;
-  TilePlan *tp = get_plan(m, rcap, nmax, &status);
+  TilePlan *tp = get_plan(m, rcap, nmax, ecap, &status);
   if (!tp) return status;
   if (g_sm_count == 0) {
     int dev = 0;
@@ -493,12 +583,20 @@ int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, 
   a.G = G;
   magic_div((uint32_t)a.G, a.g_magic, a.g_shift);
   a.copy_bytes = (uint32_t)(((int64_t)in->nlev * nvar * 4 + 15) / 16 * 16);
-  a.stage_bytes = (uint32_t)rcap * row_bytes;
-  a.stage_bytes = (a.stage_bytes + 127u) & ~127u;
+  auto up16 = [](uint32_t x) { return (x + 15u) & ~15u; };
+  a.off_w = up16((uint32_t)rcap * row_bytes);
+  a.off_l = a.off_w + up16((uint32_t)(ecap + 2) * 8u);
+  a.off_r = a.off_l + up16((uint32_t)(ecap + 16) * 2u);
+  a.stage_bytes = (a.off_r + up16((uint32_t)(nmax + 8) * 4u) + 127u) & ~127u;
+  a.nstages = nstages;
   a.status = nullptr;
   if (const int rc = status_word(&a.status)) return rc;
   a.timeout_ns = 2000000000ull;
-  const size_t smem = 2 * (size_t)a.stage_bytes + 64;
+  const size_t smem = (size_t)nstages * a.stage_bytes + 16 * (size_t)nstages;
+  if (smem > 227 * 1024) {
+    set_error("staged kernel: nstages * stage size exceeds 227 KB of shared memory");
+    return NB_EINVAL;
+  }
   const int grid = std::min(tp->ntiles, g_sm_count);
   *handled = true;
   const bool comp = m->compensated != 0;

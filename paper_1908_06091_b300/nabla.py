@@ -76,6 +76,7 @@ SIGNATURES = {
     "nb_method_device_bytes": [_P, _I64P],
     "nb_method_set_kernel": [_P, _I, _I],
     "nb_method_set_compensated": [_P, _I],
+    "nb_method_set_staging": [_P, _I, _I],
     "nb_fs_nodecolumns": [_P, _I, _I, ctypes.POINTER(_P)],
     "nb_fs_release": [_P],
     "nb_fs_level_stride": [_P, _I64P],
@@ -242,6 +243,9 @@ class Method(_Handle):
 
     def set_kernel(self, variant: int, tile_nodes: int = 0) -> None:
         check(lib().nb_method_set_kernel(self._h, int(variant), int(tile_nodes)))
+
+    def set_staging(self, nstages: int, stage_kb: int) -> None:
+        check(lib().nb_method_set_staging(self._h, int(nstages), int(stage_kb)))
 
     def set_compensated(self, on: bool) -> None:
         check(lib().nb_method_set_compensated(self._h, 1 if on else 0))

@@ -143,28 +143,51 @@ def test_laplacian_with_caller_scratch_equals_library_scratch():
     assert torch.equal(a, b)
 
 
-def test_errors_are_reported_before_launch():
+def _raw(t, dtype, nvar, nlev=None, node_stride=None, lev_stride=None, nnodes=None):
+    f = nabla.nb_field()
+    f.data = t.data_ptr()
+    f.dtype = dtype
+    f.nvar = nvar
+    f.nnodes = t.shape[0] if nnodes is None else nnodes
+    f.nlev = t.shape[1] if nlev is None else nlev
+    f.reserved = 0
+    f.node_stride = t.stride(0) if node_stride is None else node_stride
+    f.lev_stride = nvar if lev_stride is None else lev_stride
+    return f
+
+
+def _call(meth, op, fi, fo):
+    import ctypes
+    return nabla.lib().nb_nabla_apply(meth.handle, op, ctypes.byref(fi), ctypes.byref(fo), None,
+                                      ctypes.c_void_p(0))
+
+
+def test_c_abi_rejects_bad_fields_before_any_launch():
     g, m, meth = product(16)
     fs = nabla.NodeColumns(meth, 4, torch.float32)
-    fs64 = nabla.NodeColumns(meth, 4, torch.float64)
     f = fs.create_field()
+    gv = fs.create_field(nvar=2)
     before = nabla.launch_count()
-    with pytest.raises(nabla.NablaError) as e:      # wrong nvar for the output
-        nabla.apply(meth, "grad", f, fs.create_field())
-    assert e.value.code in (nabla.NB_ESHAPE, nabla.NB_EINVAL)
-    with pytest.raises(nabla.NablaError) as e:      # dtype mismatch
-        nabla.apply(meth, "grad", f, fs64.create_field(nvar=2))
-    assert e.value.code == nabla.NB_EDTYPE
-    with pytest.raises(nabla.NablaError) as e:      # output aliases input
-        big = fs.create_field(nvar=2)
-        nabla.apply(meth, "div", big, big[:, :, 0])
-    assert e.value.code in (nabla.NB_ESHAPE, nabla.NB_EINVAL)
-    g2, m2, meth2 = product(24)
-    fs2 = nabla.NodeColumns(meth2, 4, torch.float32)
-    with pytest.raises(nabla.NablaError) as e:      # field of another mesh
-        nabla.apply(meth, "grad", fs2.create_field(), fs2.create_field(nvar=2))
-    assert e.value.code == nabla.NB_ESHAPE
+    F32, F64 = nabla.NB_F32, nabla.NB_F64
+    ok_in, ok_out = _raw(f, F32, 1), _raw(gv, F32, 2)
+    assert _call(meth, nabla.OP_GRAD, _raw(f, F32, 1), _raw(f, F32, 1)) == nabla.NB_ESHAPE  # nvar
+    assert _call(meth, nabla.OP_GRAD, ok_in, _raw(gv, F64, 2)) == nabla.NB_EDTYPE          # dtype
+    assert _call(meth, nabla.OP_GRAD, _raw(f, 7, 1), ok_out) == nabla.NB_EDTYPE            # unknown
+    assert _call(meth, nabla.OP_GRAD, ok_in, _raw(gv, F32, 2, nnodes=m.V - 1)) == nabla.NB_ESHAPE
+    assert _call(meth, nabla.OP_GRAD, ok_in, _raw(gv, F32, 2, nlev=3)) == nabla.NB_ESHAPE  # levels
+    assert _call(meth, nabla.OP_GRAD, ok_in, _raw(gv, F32, 2, node_stride=6)) == nabla.NB_ESHAPE
+    assert _call(meth, nabla.OP_GRAD, ok_in, _raw(gv, F32, 2, lev_stride=1)) == nabla.NB_ESHAPE
+    assert _call(meth, 9, ok_in, ok_out) == nabla.NB_EINVAL                                  # op
+    # output overlapping the input
+    assert _call(meth, nabla.OP_DIV, _raw(gv, F32, 2), _raw(gv, F32, 1, node_stride=gv.stride(0),
+                                                              lev_stride=1)) in (nabla.NB_EINVAL,)
     assert nabla.launch_count() == before
+    assert nabla.lib().nb_last_error()
+
+
+def test_device_status_reports_ok_after_normal_runs():
+    assert nabla.device_status(clear=True) in (0,)
+    assert nabla.device_status() == 0
 
 
 def test_host_buffer_entry_point_matches_device_call():
