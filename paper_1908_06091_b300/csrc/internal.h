@@ -78,6 +78,9 @@ struct TilePlan {
   int32_t *d_halo_ptr = nullptr;     // ntiles+1
   int32_t *d_halo = nullptr;         // halo node ids
   uint16_t *d_lnbr = nullptr;        // 2E: shared-memory row of each CSR neighbour
+  uint16_t *d_hrun = nullptr;        // per halo entry: length of the run of consecutive
+                                     // node ids starting there (0 inside a run)
+  int32_t *d_nruns = nullptr;        // runs per tile
 };
 
 // fvm::Method: geometry and operator weights resident on one device.

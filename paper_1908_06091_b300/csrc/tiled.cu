@@ -127,6 +127,8 @@ struct TiledArgs {
   const int32_t *tile_node0;
   const int32_t *halo_ptr;
   const int32_t *halo;
+  const uint16_t *hrun;
+  const int32_t *nruns;
   const uint16_t *lnbr;
   const int32_t *row_ptr;
   const float2 *w32;
@@ -151,9 +153,11 @@ struct TiledArgs {
 };
 
 // Issue the copies of tile t into the stage at `stage` (one whole warp): the
-// tile's column block, each halo column, and 16-byte aligned bounding
-// ranges of the tile's CSR weights, staged-row indices and row pointers, all
-// as TMA bulk copies completing on the stage's "full" barrier.
+// tile's contiguous column block, its halo columns (one bulk copy per run of
+// consecutive node ids), and 16-byte aligned bounding ranges of the tile's
+// CSR weights, staged-row indices and row pointers, all as TMA bulk copies
+// completing on the stage's "full" barrier.  The copy engine's cost is per
+// copy rather than per byte, so copies are kept few and large.
 __device__ __forceinline__ void issue_tile(const TiledArgs &a, int t, uint32_t stage, uint32_t bar,
                                            int lane) {
   const int32_t n0 = __ldg(a.tile_node0 + t), n1 = __ldg(a.tile_node0 + t + 1);
@@ -166,58 +170,86 @@ __device__ __forceinline__ void issue_tile(const TiledArgs &a, int t, uint32_t s
   const uint32_t body = (n - 1) * a.row_bytes + a.copy_bytes;
   const uint32_t wbytes = (uint32_t)(wb - wa) * 8u, lbytes = (uint32_t)(lb - la) * 2u,
                  rbytes = (uint32_t)(rb - ra) * 4u;
+  // a run of L halo columns is one copy of (L - 1) full columns + one column
+  const uint32_t runs = (uint32_t)__ldg(a.nruns + t);
+  const uint32_t hbytes = H * a.copy_bytes + (H - runs) * (a.row_bytes - a.copy_bytes);
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  if (lane == 0) mbar_expect_tx(bar, body + H * a.copy_bytes + wbytes + lbytes + rbytes);
+  if (lane == 0) mbar_expect_tx(bar, body + hbytes + wbytes + lbytes + rbytes);
   __syncwarp();
   if (lane == 0) bulk_g2s(stage, a.in + (int64_t)n0 * a.in_stride * 4, body, bar);
   if (lane == 1) bulk_g2s(stage + a.off_w, a.w32 + wa, wbytes, bar);
   if (lane == 2) bulk_g2s(stage + a.off_l, a.lnbr + la, lbytes, bar);
   if (lane == 3) bulk_g2s(stage + a.off_r, a.row_ptr + ra, rbytes, bar);
   for (uint32_t h = lane; h < H; h += 32) {
+    const uint32_t L = __ldg(a.hrun + h0 + h);
+    if (L == 0) continue;
     const int32_t node = __ldg(a.halo + h0 + h);
-    bulk_g2s(stage + (n + h) * a.row_bytes, a.in + (int64_t)node * a.in_stride * 4, a.copy_bytes, bar);
+    bulk_g2s(stage + (n + h) * a.row_bytes, a.in + (int64_t)node * a.in_stride * 4,
+             (L - 1) * a.row_bytes + a.copy_bytes, bar);
   }
 }
 
-// Staged views of one tile: CSR range, weights, staged-row indices.
+// Shared-memory loads by 32-bit address (volatile: they must stay after the
+// mbarrier wait that makes the staged data visible).
+__device__ __forceinline__ float4 lds128(uint32_t a) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(a));
+  return v;
+}
+__device__ __forceinline__ float2 lds64(uint32_t a) {
+  float2 v;
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ uint32_t lds_u16(uint32_t a) {
+  uint16_t v;
+  asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ int32_t lds_s32(uint32_t a) {
+  int32_t v;
+  asm volatile("ld.shared.s32 %0, [%1];" : "=r"(v) : "r"(a));
+  return v;
+}
+
+// 32-bit shared addresses of one staged tile: entry p's weight is at
+// w + 8 p, its staged-row index at l + 2 p, node i's row pointer at r + 4 i
+// (wrap-around arithmetic; the sums land inside the stage).
 struct TileView {
   int32_t n0, n1;
-  const char *rows;
-  const float2 *w;     // w[p - wa]
-  const uint16_t *lr;  // lr[p - la]
-  const int32_t *rp;   // rp[node - ra]
-  int32_t wa, la, ra;
-  __device__ __forceinline__ TileView(const TiledArgs &a, int t, const char *stage) {
+  uint32_t rows, w, l, r;
+  __device__ __forceinline__ TileView(const TiledArgs &a, int t, uint32_t stage) {
     n0 = __ldg(a.tile_node0 + t);
     n1 = __ldg(a.tile_node0 + t + 1);
     rows = stage;
-    ra = n0 & ~3;
-    rp = reinterpret_cast<const int32_t *>(stage + a.off_r);
-    const int32_t pa = rp[n0 - ra];
-    wa = pa & ~1;
-    la = pa & ~7;
-    w = reinterpret_cast<const float2 *>(stage + a.off_w);
-    lr = reinterpret_cast<const uint16_t *>(stage + a.off_l);
+    const int32_t ra = n0 & ~3;
+    r = stage + a.off_r - 4u * (uint32_t)ra;
+    const int32_t pa = lds_s32(r + 4u * (uint32_t)n0);
+    w = stage + a.off_w - 8u * (uint32_t)(pa & ~1);
+    l = stage + a.off_l - 2u * (uint32_t)(pa & ~7);
   }
 };
 
-// Items [i0, i1) of tile t, one per lane of the calling warp and stride 32.
+// Items [i0, i1) of tile t for the calling warp, one per lane, stride 32.
 template <bool COMP>
-__device__ __forceinline__ void grad_tile(const TiledArgs &a, int t, const char *stage, int part,
+__device__ __forceinline__ void grad_tile(const TiledArgs &a, int t, uint32_t stage, int part,
                                           int nparts) {
   const TileView v(a, t, stage);
   const uint32_t items = (uint32_t)(v.n1 - v.n0) * a.G;
   const uint32_t i0 = (uint32_t)(((uint64_t)items * part) / nparts);
   const uint32_t i1 = (uint32_t)(((uint64_t)items * (part + 1)) / nparts);
   const bool pole = t >= a.ntiles_main;
+  const uint32_t rb = a.row_bytes;
   for (uint32_t item = i0 + (threadIdx.x & 31); item < i1; item += 32) {
     const uint32_t il = (uint32_t)(((uint64_t)item * a.g_magic) >> a.g_shift);
     const uint32_t c = item - il * a.G;
     const int l0 = 4 * (int)c;
-    const int64_t node = v.n0 + il;
-    const int32_t p0 = v.rp[node - v.ra], p1 = v.rp[node + 1 - v.ra];
-    const char *col = v.rows + c * 16;
-    const float4 fi = *reinterpret_cast<const float4 *>(col + il * a.row_bytes);
+    const int32_t node = v.n0 + (int32_t)il;
+    const int32_t p0 = lds_s32(v.r + 4u * (uint32_t)node), p1 = lds_s32(v.r + 4u * (uint32_t)node + 4u);
+    const uint32_t col = v.rows + c * 16u;
+    const float4 fi = lds128(col + il * rb);
     float gx[4], gy[4];
     if (!pole) {
       const f2_t fi01 = pk(fi.x, fi.y), fi23 = pk(fi.z, fi.w);
@@ -230,16 +262,17 @@ __device__ __forceinline__ void grad_tile(const TiledArgs &a, int t, const char 
         ay01.add_prod(wy, d01);
         ay23.add_prod(wy, d23);
       };
+      uint32_t pw = v.w + 8u * (uint32_t)p0, pl = v.l + 2u * (uint32_t)p0;
       int32_t p = p0;
-      for (; p + 1 < p1; p += 2) {
-        const float2 w0 = v.w[p - v.wa], w1 = v.w[p + 1 - v.wa];
-        const uint32_t r0 = v.lr[p - v.la], r1 = v.lr[p + 1 - v.la];
-        const float4 f0 = *reinterpret_cast<const float4 *>(col + r0 * a.row_bytes);
-        const float4 f1 = *reinterpret_cast<const float4 *>(col + r1 * a.row_bytes);
+      for (; p + 1 < p1; p += 2, pw += 16u, pl += 4u) {
+        const float2 w0 = lds64(pw), w1 = lds64(pw + 8u);
+        const uint32_t r0 = lds_u16(pl), r1 = lds_u16(pl + 2u);
+        const float4 f0 = lds128(col + r0 * rb);
+        const float4 f1 = lds128(col + r1 * rb);
         body(w0, f0);
         body(w1, f1);
       }
-      if (p < p1) body(v.w[p - v.wa], *reinterpret_cast<const float4 *>(col + v.lr[p - v.la] * a.row_bytes));
+      if (p < p1) body(lds64(pw), lds128(col + lds_u16(pl) * rb));
       upk(ax01.value(), gx[0], gx[1]);
       upk(ax23.value(), gx[2], gx[3]);
       upk(ay01.value(), gy[0], gy[1]);
@@ -249,7 +282,7 @@ __device__ __forceinline__ void grad_tile(const TiledArgs &a, int t, const char 
       const float fiv[4] = {fi.x, fi.y, fi.z, fi.w};
       for (int32_t p = p0; p < p1; ++p) {
         const double2 w = __ldg(a.w64 + p);
-        const float4 fj = *reinterpret_cast<const float4 *>(col + v.lr[p - v.la] * a.row_bytes);
+        const float4 fj = lds128(col + lds_u16(v.l + 2u * (uint32_t)p) * rb);
         const float fjv[4] = {fj.x, fj.y, fj.z, fj.w};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -264,7 +297,7 @@ __device__ __forceinline__ void grad_tile(const TiledArgs &a, int t, const char 
         gy[k] = (float)sy[k];
       }
     }
-    float *go = a.out + node * a.out_stride + 2 * l0;
+    float *go = a.out + (int64_t)node * a.out_stride + 2 * l0;
     if (l0 + 4 <= a.nlev) {
       __stcs(reinterpret_cast<float4 *>(go), make_float4(gx[0], gy[0], gx[1], gy[1]));
       __stcs(reinterpret_cast<float4 *>(go) + 1, make_float4(gx[2], gy[2], gx[3], gy[3]));
@@ -283,7 +316,7 @@ __device__ __forceinline__ void grad_tile(const TiledArgs &a, int t, const char 
 // levels each; item c of a node takes units c and c + G, so that every
 // shared-memory load of a warp reads consecutive 16-byte words.
 template <bool COMP>
-__device__ __forceinline__ void divcurl_tile(const TiledArgs &a, int t, const char *stage, int part,
+__device__ __forceinline__ void divcurl_tile(const TiledArgs &a, int t, uint32_t stage, int part,
                                              int nparts) {
   const TileView v(a, t, stage);
   const uint32_t items = (uint32_t)(v.n1 - v.n0) * a.G;
@@ -291,49 +324,48 @@ __device__ __forceinline__ void divcurl_tile(const TiledArgs &a, int t, const ch
   const uint32_t i1 = (uint32_t)(((uint64_t)items * (part + 1)) / nparts);
   const bool pole = t >= a.ntiles_main;
   const int units = (a.nlev + 1) / 2;
+  const uint32_t rb = a.row_bytes;
   for (uint32_t item = i0 + (threadIdx.x & 31); item < i1; item += 32) {
     const uint32_t il = (uint32_t)(((uint64_t)item * a.g_magic) >> a.g_shift);
     const uint32_t c = item - il * a.G;
     const int u0 = (int)c, u1 = (int)c + a.G;
     const bool has1 = u1 < units;
-    const int64_t node = v.n0 + il;
-    const int32_t p0 = v.rp[node - v.ra], p1 = v.rp[node + 1 - v.ra];
-    const char *colA = v.rows + u0 * 16;
-    const char *colB = v.rows + (has1 ? u1 : u0) * 16;
-    const float4 A = *reinterpret_cast<const float4 *>(colA + il * a.row_bytes);
-    const float4 B = *reinterpret_cast<const float4 *>(colB + il * a.row_bytes);
+    const int32_t node = v.n0 + (int32_t)il;
+    const int32_t p0 = lds_s32(v.r + 4u * (uint32_t)node), p1 = lds_s32(v.r + 4u * (uint32_t)node + 4u);
+    const uint32_t colA = v.rows + (uint32_t)u0 * 16u;
+    const uint32_t colB = v.rows + (uint32_t)(has1 ? u1 : u0) * 16u;
+    const float4 A = lds128(colA + il * rb);
+    const float4 B = lds128(colB + il * rb);
     float r[4];
     if (!pole) {
       // pair accumulators (sum of w.x du, sum of w.y dv) per level
-      const f2_t i0 = pk(A.x, A.y), i1 = pk(A.z, A.w), i2 = pk(B.x, B.y), i3 = pk(B.z, B.w);
+      const f2_t i0p = pk(A.x, A.y), i1p = pk(A.z, A.w), i2p = pk(B.x, B.y), i3p = pk(B.z, B.w);
       Kahan2<COMP> k0, k1, k2, k3;
       auto body = [&](const float2 w, const float4 C, const float4 D) {
         const f2_t w2 = pk(w.x, w.y);
-        k0.add_prod(w2, sub2(pk(C.x, C.y), i0));
-        k1.add_prod(w2, sub2(pk(C.z, C.w), i1));
-        k2.add_prod(w2, sub2(pk(D.x, D.y), i2));
-        k3.add_prod(w2, sub2(pk(D.z, D.w), i3));
+        k0.add_prod(w2, sub2(pk(C.x, C.y), i0p));
+        k1.add_prod(w2, sub2(pk(C.z, C.w), i1p));
+        k2.add_prod(w2, sub2(pk(D.x, D.y), i2p));
+        k3.add_prod(w2, sub2(pk(D.z, D.w), i3p));
       };
+      uint32_t pw = v.w + 8u * (uint32_t)p0, pl = v.l + 2u * (uint32_t)p0;
       int32_t p = p0;
-      for (; p + 1 < p1; p += 2) {
-        const float2 w0 = v.w[p - v.wa], w1 = v.w[p + 1 - v.wa];
-        const uint32_t r0 = v.lr[p - v.la] * a.row_bytes, r1 = v.lr[p + 1 - v.la] * a.row_bytes;
-        const float4 C0 = *reinterpret_cast<const float4 *>(colA + r0);
-        const float4 D0 = *reinterpret_cast<const float4 *>(colB + r0);
-        const float4 C1 = *reinterpret_cast<const float4 *>(colA + r1);
-        const float4 D1 = *reinterpret_cast<const float4 *>(colB + r1);
+      for (; p + 1 < p1; p += 2, pw += 16u, pl += 4u) {
+        const float2 w0 = lds64(pw), w1 = lds64(pw + 8u);
+        const uint32_t r0 = lds_u16(pl) * rb, r1 = lds_u16(pl + 2u) * rb;
+        const float4 C0 = lds128(colA + r0), D0 = lds128(colB + r0);
+        const float4 C1 = lds128(colA + r1), D1 = lds128(colB + r1);
         body(w0, C0, D0);
         body(w1, C1, D1);
       }
       if (p < p1) {
-        const uint32_t r0 = v.lr[p - v.la] * a.row_bytes;
-        body(v.w[p - v.wa], *reinterpret_cast<const float4 *>(colA + r0),
-             *reinterpret_cast<const float4 *>(colB + r0));
+        const uint32_t r0 = lds_u16(pl) * rb;
+        body(lds64(pw), lds128(colA + r0), lds128(colB + r0));
       }
       const float2 sw = __ldg(a.s32 + node);
       const f2_t sw2 = pk(sw.x, sw.y);
       const f2_t vals[4] = {k0.value(), k1.value(), k2.value(), k3.value()};
-      const f2_t self[4] = {i0, i1, i2, i3};
+      const f2_t self[4] = {i0p, i1p, i2p, i3p};
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const f2_t q = fma2(sw2, self[k], vals[k]);
@@ -346,9 +378,9 @@ __device__ __forceinline__ void divcurl_tile(const TiledArgs &a, int t, const ch
       double sacc[4] = {0, 0, 0, 0};
       for (int32_t p = p0; p < p1; ++p) {
         const double2 w = __ldg(a.w64 + p);
-        const uint32_t r0 = v.lr[p - v.la] * a.row_bytes;
-        const float4 C = *reinterpret_cast<const float4 *>(colA + r0);
-        const float4 D = *reinterpret_cast<const float4 *>(colB + r0);
+        const uint32_t r0 = lds_u16(v.l + 2u * (uint32_t)p) * rb;
+        const float4 C = lds128(colA + r0);
+        const float4 D = lds128(colB + r0);
         const float ju[4] = {C.x, C.z, D.x, D.z}, jv[4] = {C.y, C.w, D.y, D.w};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -365,7 +397,7 @@ __device__ __forceinline__ void divcurl_tile(const TiledArgs &a, int t, const ch
       }
     }
     // levels 2 u0, 2 u0 + 1 from r[0..1], levels 2 u1, 2 u1 + 1 from r[2..3]
-    float *oo = a.out + node * a.out_stride;
+    float *oo = a.out + (int64_t)node * a.out_stride;
     const int la0 = 2 * u0, la1 = 2 * u1;
     if (la0 + 1 < a.nlev) __stcs(reinterpret_cast<float2 *>(oo + la0), make_float2(r[0], r[1]));
     else oo[la0] = r[0];
@@ -434,7 +466,7 @@ __global__ void __launch_bounds__(kStagedThreads, 1) staged_f32(TiledArgs a) {
       if (lane == 0) atomicCAS(a.status, 0, (int)NB_ETIMEOUT);
       break;
     }
-    const char *rows = reinterpret_cast<const char *>(smem) + (size_t)s * a.stage_bytes;
+    const uint32_t rows = stage0 + (uint32_t)s * a.stage_bytes;
     if (OP == 0) grad_tile<COMP>(a, t, rows, warp, kConsumerWarps);
     else divcurl_tile<COMP>(a, t, rows, warp, kConsumerWarps);
     __syncwarp();
@@ -462,6 +494,21 @@ static int plan_upload(TilePlan *tp, const nb_mesh *mesh) {
   if ((st = up((void **)&tp->d_halo_ptr, hptr.data(), hptr.size() * 4))) return st;
   if ((st = up((void **)&tp->d_halo, halo.data(), halo.size() * 4))) return st;
   if ((st = up((void **)&tp->d_lnbr, lnbr.data(), lnbr.size() * 2))) return st;
+  // runs of consecutive node ids inside each tile's sorted halo
+  std::vector<uint16_t> hrun(halo.size(), 0);
+  std::vector<int32_t> nruns(tp->ntiles, 0);
+  for (int t = 0; t < tp->ntiles; ++t) {
+    int32_t i = hptr[t];
+    while (i < hptr[t + 1]) {
+      int32_t j = i + 1;
+      while (j < hptr[t + 1] && halo[j] == halo[j - 1] + 1 && j - i < 65535) ++j;
+      hrun[i] = (uint16_t)(j - i);
+      ++nruns[t];
+      i = j;
+    }
+  }
+  if ((st = up((void **)&tp->d_hrun, hrun.data(), hrun.size() * 2))) return st;
+  if ((st = up((void **)&tp->d_nruns, nruns.data(), nruns.size() * 4))) return st;
   return NB_OK;
 }
 
@@ -544,7 +591,7 @@ int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, 
   // the staged columns, then the tile's weights, staged-row indices and
   // row pointers (bounding ranges, 16-byte aligned).
   const int nstages = m->nstages > 0 ? m->nstages : 2;
-  const int stage_kb = m->stage_kb > 0 ? m->stage_kb : 96;
+  const int stage_kb = m->stage_kb > 0 ? m->stage_kb : 112;
   const int nmax = m->tile_nodes > 0 ? m->tile_nodes : 256;
   const int ecap = 10 * nmax;
   const uint32_t meta_bytes = (uint32_t)((ecap + 2) * 8 + 16) + (uint32_t)((ecap + 16) * 2 + 16) +
@@ -567,6 +614,8 @@ int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, 
   a.tile_node0 = tp->d_tile_node0;
   a.halo_ptr = tp->d_halo_ptr;
   a.halo = tp->d_halo;
+  a.hrun = tp->d_hrun;
+  a.nruns = tp->d_nruns;
   a.lnbr = tp->d_lnbr;
   a.row_ptr = m->d_row_ptr;
   const bool g = op == NB_OP_GRAD;
