@@ -204,6 +204,25 @@ int nb_nabla_curl(const nb_method *method, const nb_field *uv, const nb_field *z
 int nb_nabla_laplacian(const nb_method *method, const nb_field *f, const nb_field *lap,
                        const nb_field *scratch, void *stream);
 
+/* Laplacian that allocates nothing.  The paper has no counterpart: this call
+ * serves callers that cannot allocate device memory while they run, such as
+ * a component embedded in a larger model with a device-memory budget fixed at
+ * start-up, or a latency-critical loop in which cudaMalloc/cudaFree (which can
+ * synchronise the whole device) are not allowed.  The intermediate gradient
+ * lives in a fixed array of NB_NOALLOC_SCRATCH_BYTES inside the library, held
+ * on every GPU that loads the library until the process exits; it fits
+ * [V][Lq][2] values of f's dtype with Lq = nlev rounded up to a multiple of 4
+ * (FP32) or 2 (FP64), and larger problems get NB_ESHAPE (use
+ * nb_nabla_laplacian with a scratch field).  The first call on a device looks
+ * up the array's device address, so make that first call before any stream
+ * capture.  All calls share the one array and it keeps the last call's
+ * contents (nothing in it needs to start at zero); calls whose work overlaps
+ * on the GPU, on any stream, race on it, so serialise them.  Same argument
+ * rules and errors as nb_nabla_laplacian. */
+#define NB_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+int nb_nabla_laplacian_noalloc(const nb_method *method, const nb_field *f, const nb_field *lap,
+                               void *stream);
+
 /* Generic entry: op is an nb_op; for NB_OP_LAP scratch may be NULL. */
 int nb_nabla_apply(const nb_method *method, int op, const nb_field *in, const nb_field *out,
                    const nb_field *scratch, void *stream);

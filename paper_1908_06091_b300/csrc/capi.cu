@@ -401,6 +401,12 @@ static int validate(const nb_method *m, int op, const nb_field *in, const nb_fie
   return NB_OK;
 }
 
+// Argument checks shared with the allocation-free entry point.
+int validate_op(const nb_method *m, int op, const nb_field *in, const nb_field *out,
+                const nb_field *scratch) {
+  return validate(m, op, in, out, scratch);
+}
+
 // One of grad, div, curl on the chosen kernel variant.
 static int launch_single(nb_method *m, int op, const nb_field *in, const nb_field *out,
                          cudaStream_t st) {

@@ -86,6 +86,7 @@ SIGNATURES = {
     "nb_nabla_curl": [_P, _FP, _FP, _P],
     "nb_nabla_laplacian": [_P, _FP, _FP, _FP, _P],
     "nb_nabla_apply": [_P, _I, _FP, _FP, _FP, _P],
+    "nb_nabla_laplacian_noalloc": [_P, _FP, _FP, _P],
     "nb_nabla_apply_host": [_P, _I, _P, _P, _FP, _FP, _FP, _P],
     "nb_launch_count": [_I64P],
     "nb_device_status": [_I, ctypes.POINTER(ctypes.c_int32)],
@@ -329,6 +330,18 @@ def curl(method, uv, z, stream=None):
 
 def laplacian(method, f, lap, scratch=None, stream=None):
     return apply(method, OP_LAP, f, lap, scratch=scratch, stream=stream)
+
+
+NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
+
+
+def laplacian_noalloc(method, f, lap, stream=None):
+    """Laplacian whose intermediate gradient lives in the library's fixed
+    scratch array (no device allocation; see nb_nabla_laplacian_noalloc)."""
+    fi, fo = field_view(f, 1), field_view(lap, 1)
+    check(lib().nb_nabla_laplacian_noalloc(method.handle, ctypes.byref(fi), ctypes.byref(fo),
+                                           ctypes.c_void_p(_stream(stream))))
+    return lap
 
 
 def apply_host(method: Method, op, host_in: torch.Tensor, host_out: torch.Tensor,
