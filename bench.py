@@ -125,6 +125,22 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def measured_traffic(op, V, L):
+    """DRAM bytes of one launch of `op` from the ncu capture recorded in
+    profiles/dram_traffic.json (per node-level, scaled to V x L), or None when
+    the staged kernel source has changed since that capture."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as fh:
+            d = json.load(fh)
+        with open(os.path.join(ROOT, d["kernel_source"]), "rb") as fh:
+            if hashlib.sha256(fh.read()).hexdigest() != d["kernel_source_sha256"]:
+                return None
+        return int(d["dram_bytes_per_node_level"][op] * V * L)
+    except Exception:
+        return None
+
+
 def algorithmic_bytes(op, V, E, L, elem):
     """Bytes a launch must move at minimum: each input value read once, each
     output written once, the connectivity and weights read once per node."""
@@ -316,7 +332,8 @@ def bench_ours(a):
         "per_op": per_op,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
                      "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
-                     "peak_kind": peak_kind, "algorithmic_bytes": int(algo), "traffic": None},
+                     "peak_kind": peak_kind, "algorithmic_bytes": int(algo),
+                     "traffic": measured_traffic(dom, V, L) if a.variant != 1 else None},
         "fp64": fp64,
         "e2e": e2e,
         "gpu_launches": int(launches),
