@@ -1,0 +1,617 @@
+// batch.cu -- many nabla operations on fields of different meshes and level
+// counts in one persistent launch, captured in a CUDA graph.
+//
+// Each item (op, method, in, out) is cut into work units of `npw * 8 * rounds`
+// nodes x `lpb` levels.  A persistent grid of 256-thread CTAs takes units from
+// an atomic counter (dynamic load balancing across uneven items); inside a
+// unit, warp w takes `npw` nodes per round and each node's 32 / npw lanes take
+// consecutive levels, so a neighbour's column is read as contiguous words.
+// The per-(node, level) arithmetic is exactly the direct kernels' (same weights,
+// same neighbour order, same compensated accumulation, FP64 for pole-row
+// nodes), so a batched result equals the same operation run alone on the
+// direct kernels bit for bit.  Laplacian items run their gradient pass in
+// phase 1 (into batch-owned scratch) and their divergence pass in phase 2; the
+// counter resets and the two launches form one CUDA graph.  `levels per block`
+// and `nodes per warp` are chosen per item class (op, dtype, grid, levels) by
+// an autotuner that times the candidates on the device.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "kernels_common.cuh"
+
+namespace nb {
+
+struct BItem {
+  int32_t op;     // 0 grad, 1 div, 2 curl (the Laplacian is split into 0 then 1)
+  int32_t f64;
+  int32_t nlev, lpb, npw, rounds;
+  int32_t nchunk_lev;
+  int32_t pad;
+  int64_t V, cap_begin;
+  int64_t unit_begin;  // first unit of this item in its phase
+  const int32_t *row_ptr, *nbr;
+  const void *w32, *w64, *s32, *s64;
+  const void *in;
+  void *out;
+  int64_t in_stride, out_stride;
+};
+
+constexpr int kBatchThreads = 256;
+constexpr int kBatchWarps = kBatchThreads / 32;
+
+// ----------------------------------------------------------- device part
+
+// One (node, level) of grad / div / curl with the direct kernels' arithmetic.
+__device__ __forceinline__ void unit_point_f32(const BItem &it, int64_t i, int l, bool comp) {
+  const int32_t p0 = __ldg(it.row_ptr + i), p1 = __ldg(it.row_ptr + i + 1);
+  if (it.op == 0) {
+    const float *f = static_cast<const float *>(it.in);
+    const float fi = __ldg(f + i * it.in_stride + l);
+    float gx, gy;
+    if (i < it.cap_begin) {
+      const float2 *w = static_cast<const float2 *>(it.w32);
+      KahanAcc ax, ay;
+      PlainAcc px, py;
+      for (int32_t p = p0; p < p1; ++p) {
+        const int32_t j = __ldg(it.nbr + p);
+        const float2 wp = __ldg(w + p);
+        const float d = __fsub_rn(__ldg(f + (int64_t)j * it.in_stride + l), fi);
+        if (comp) {
+          ax.add_prod(wp.x, d);
+          ay.add_prod(wp.y, d);
+        } else {
+          px.add_prod(wp.x, d);
+          py.add_prod(wp.y, d);
+        }
+      }
+      gx = comp ? ax.value() : px.value();
+      gy = comp ? ay.value() : py.value();
+    } else {
+      const double2 *w = static_cast<const double2 *>(it.w64);
+      double sx = 0, sy = 0;
+      for (int32_t p = p0; p < p1; ++p) {
+        const int32_t j = __ldg(it.nbr + p);
+        const double2 wp = __ldg(w + p);
+        const double d = (double)__ldg(f + (int64_t)j * it.in_stride + l) - (double)fi;
+        sx = fma(wp.x, d, sx);
+        sy = fma(wp.y, d, sy);
+      }
+      gx = (float)sx;
+      gy = (float)sy;
+    }
+    float *g = static_cast<float *>(it.out) + i * it.out_stride + 2 * l;
+    g[0] = gx;
+    g[1] = gy;
+  } else {
+    const float *uv = static_cast<const float *>(it.in);
+    const float ui = __ldg(uv + i * it.in_stride + 2 * l), vi = __ldg(uv + i * it.in_stride + 2 * l + 1);
+    float r;
+    if (i < it.cap_begin) {
+      const float2 *w = static_cast<const float2 *>(it.w32);
+      const float2 sw = __ldg(static_cast<const float2 *>(it.s32) + i);
+      KahanAcc acc;
+      PlainAcc pacc;
+      for (int32_t p = p0; p < p1; ++p) {
+        const int32_t j = __ldg(it.nbr + p);
+        const float2 wp = __ldg(w + p);
+        const float *cj = uv + (int64_t)j * it.in_stride + 2 * l;
+        const float du = __fsub_rn(__ldg(cj), ui), dv = __fsub_rn(__ldg(cj + 1), vi);
+        const float term = __fmaf_rn(wp.x, du, __fmul_rn(wp.y, dv));
+        if (comp) acc.add(term);
+        else pacc.add(term);
+      }
+      const float self = __fmaf_rn(sw.x, ui, __fmul_rn(sw.y, vi));
+      if (comp) {
+        acc.add(self);
+        r = acc.value();
+      } else {
+        pacc.add(self);
+        r = pacc.value();
+      }
+    } else {
+      const double2 *w = static_cast<const double2 *>(it.w64);
+      const double2 sw = __ldg(static_cast<const double2 *>(it.s64) + i);
+      double s = 0;
+      for (int32_t p = p0; p < p1; ++p) {
+        const int32_t j = __ldg(it.nbr + p);
+        const double2 wp = __ldg(w + p);
+        const float *cj = uv + (int64_t)j * it.in_stride + 2 * l;
+        s = fma(wp.x, (double)__ldg(cj) - (double)ui, s);
+        s = fma(wp.y, (double)__ldg(cj + 1) - (double)vi, s);
+      }
+      s = fma(sw.x, (double)ui, s);
+      s = fma(sw.y, (double)vi, s);
+      r = (float)s;
+    }
+    static_cast<float *>(it.out)[i * it.out_stride + l] = r;
+  }
+}
+
+__device__ __forceinline__ void unit_point_f64(const BItem &it, int64_t i, int l) {
+  const int32_t p0 = __ldg(it.row_ptr + i), p1 = __ldg(it.row_ptr + i + 1);
+  const double2 *w = static_cast<const double2 *>(it.w64);
+  if (it.op == 0) {
+    const double *f = static_cast<const double *>(it.in);
+    const double fi = __ldg(f + i * it.in_stride + l);
+    double sx = 0, sy = 0;
+    for (int32_t p = p0; p < p1; ++p) {
+      const int32_t j = __ldg(it.nbr + p);
+      const double2 wp = __ldg(w + p);
+      const double d = __ldg(f + (int64_t)j * it.in_stride + l) - fi;
+      sx = fma(wp.x, d, sx);
+      sy = fma(wp.y, d, sy);
+    }
+    double *g = static_cast<double *>(it.out) + i * it.out_stride + 2 * l;
+    g[0] = sx;
+    g[1] = sy;
+  } else {
+    const double *uv = static_cast<const double *>(it.in);
+    const double ui = __ldg(uv + i * it.in_stride + 2 * l), vi = __ldg(uv + i * it.in_stride + 2 * l + 1);
+    const double2 sw = __ldg(static_cast<const double2 *>(it.s64) + i);
+    double s = 0;
+    for (int32_t p = p0; p < p1; ++p) {
+      const int32_t j = __ldg(it.nbr + p);
+      const double2 wp = __ldg(w + p);
+      const double *cj = uv + (int64_t)j * it.in_stride + 2 * l;
+      s = fma(wp.x, __ldg(cj) - ui, s);
+      s = fma(wp.y, __ldg(cj + 1) - vi, s);
+    }
+    s = fma(sw.x, ui, s);
+    s = fma(sw.y, vi, s);
+    static_cast<double *>(it.out)[i * it.out_stride + l] = s;
+  }
+}
+
+// Persistent batch kernel for one phase: CTAs take units from `counter`.
+__global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BItem *__restrict__ items,
+                                                              int nitems, int64_t nunits,
+                                                              unsigned long long *counter, int comp) {
+  __shared__ long long s_unit;
+  __shared__ int s_item;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const long long u = (long long)atomicAdd(counter, 1ull);
+      s_unit = u;
+      int it = -1;
+      if (u < nunits) {  // binary search: last item with unit_begin <= u
+        int lo = 0, hi = nitems - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (items[mid].unit_begin <= u) lo = mid;
+          else hi = mid - 1;
+        }
+        it = lo;
+      }
+      s_item = it;
+    }
+    __syncthreads();
+    const long long u = s_unit;
+    const int ii = s_item;
+    __syncthreads();
+    if (u >= nunits) return;
+    const BItem &it = items[ii];
+    const int64_t k = u - it.unit_begin;
+    const int64_t nchunk = k / it.nchunk_lev, lchunk = k - nchunk * it.nchunk_lev;
+    const int npw = it.npw, sub = 32 / npw;
+    const int l0 = (int)lchunk * it.lpb;
+    const int l1 = min(it.nlev, l0 + it.lpb);
+    const int64_t nodes_per_unit = (int64_t)npw * kBatchWarps * it.rounds;
+    const int64_t n_begin = nchunk * nodes_per_unit;
+    for (int r = 0; r < it.rounds; ++r) {
+      const int64_t i = n_begin + ((int64_t)r * kBatchWarps + warp) * npw + lane / sub;
+      if (i >= it.V) continue;
+      for (int l = l0 + lane % sub; l < l1; l += sub) {
+        if (it.f64) unit_point_f64(it, i, l);
+        else unit_point_f32(it, i, l, comp != 0);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------- host part
+
+struct TuneKey {
+  int op, f64, N, nlev;
+  bool operator<(const TuneKey &o) const {
+    return std::tie(op, f64, N, nlev) < std::tie(o.op, o.f64, o.N, o.nlev);
+  }
+};
+
+static std::mutex g_tune_mu;
+static std::map<std::string, std::map<TuneKey, std::pair<int, int>>> g_tune;  // gpu -> key -> (lpb, npw)
+
+static std::string gpu_name() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp p;
+  if (cudaGetDeviceProperties(&p, dev) != cudaSuccess) return "unknown";
+  return p.name;
+}
+
+// Autotune cache file: NB_TUNE_CACHE (if set), lines "gpu|op|f64|N|nlev|lpb|npw".
+static void load_tune_cache() {
+  const char *path = std::getenv("NB_TUNE_CACHE");
+  if (!path) return;
+  std::ifstream in(path);
+  std::string line;
+  while (std::getline(in, line)) {
+    std::vector<std::string> f;
+    std::stringstream ss(line);
+    std::string tok;
+    while (std::getline(ss, tok, '|')) f.push_back(tok);
+    if (f.size() != 7) continue;
+    try {
+      TuneKey k{std::stoi(f[1]), std::stoi(f[2]), std::stoi(f[3]), std::stoi(f[4])};
+      g_tune[f[0]][k] = {std::stoi(f[5]), std::stoi(f[6])};
+    } catch (...) {
+    }
+  }
+}
+static void save_tune_cache() {
+  const char *path = std::getenv("NB_TUNE_CACHE");
+  if (!path) return;
+  std::ofstream out(path, std::ios::trunc);
+  for (auto &g : g_tune)
+    for (auto &kv : g.second)
+      out << g.first << '|' << kv.first.op << '|' << kv.first.f64 << '|' << kv.first.N << '|'
+          << kv.first.nlev << '|' << kv.second.first << '|' << kv.second.second << '\n';
+}
+
+// Size heuristic when no tuned entry exists: short columns -> many nodes per
+// warp; tall columns -> one node per warp with 32 levels per lane group.
+static std::pair<int, int> default_shape(int nlev) {
+  if (nlev <= 2) return {nlev, 32};
+  if (nlev <= 8) return {8, 4};
+  if (nlev <= 40) return {32, 1};
+  return {64, 1};
+}
+
+}  // namespace nb
+
+struct nb_batch : nb::RefCounted {
+  struct Src {
+    int op;
+    nb_method *method;
+    nb_field in, out;
+  };
+  std::vector<Src> src;
+  std::vector<nb::TuneKey> keys;  // per source item
+  std::vector<std::pair<int, int>> shape;  // per source item (lpb, npw)
+  std::vector<void *> scratch;  // per source item (Laplacian only)
+  nb::BItem *d_items[2] = {nullptr, nullptr};
+  int nitems[2] = {0, 0};
+  int64_t nunits[2] = {0, 0};
+  unsigned long long *d_counter = nullptr;  // 2 counters
+  int64_t node_levels = 0;
+  int comp = 1;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int grid = 0;
+  ~nb_batch() override {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (int ph = 0; ph < 2; ++ph)
+      if (d_items[ph]) cudaFree(d_items[ph]);
+    if (d_counter) cudaFree(d_counter);
+    for (void *p : scratch)
+      if (p) cudaFree(p);
+    for (auto &s : src) nb::release(s.method);
+  }
+};
+
+namespace nb {
+
+int validate_op(const nb_method *m, int op, const nb_field *in, const nb_field *out,
+                const nb_field *scratch);
+
+static BItem make_item(const nb_method *m, int op, const nb_field &in, const nb_field &out,
+                       std::pair<int, int> shp) {
+  BItem b{};
+  b.op = op;
+  b.f64 = in.dtype == NB_F64;
+  b.nlev = in.nlev;
+  b.lpb = std::max(1, std::min(shp.first, in.nlev));
+  b.npw = shp.second;
+  const int sub = 32 / b.npw;
+  // rounds: about 2048 point evaluations per unit
+  const int per_round = b.npw * kBatchWarps * std::min(b.lpb, sub);
+  b.rounds = std::max(1, 2048 / std::max(1, per_round));
+  b.nchunk_lev = (in.nlev + b.lpb - 1) / b.lpb;
+  b.V = m->mesh->V;
+  b.cap_begin = m->mesh->cap_begin;
+  b.row_ptr = m->d_row_ptr;
+  b.nbr = m->d_nbr;
+  b.w32 = op == 0 ? (const void *)m->d_wgrad32 : op == 1 ? (const void *)m->d_wdiv32 : (const void *)m->d_wcurl32;
+  b.w64 = op == 0 ? (const void *)m->d_wgrad64 : op == 1 ? (const void *)m->d_wdiv64 : (const void *)m->d_wcurl64;
+  b.s32 = op == 2 ? (const void *)m->d_scurl32 : (const void *)m->d_sdiv32;
+  b.s64 = op == 2 ? (const void *)m->d_scurl64 : (const void *)m->d_sdiv64;
+  b.in = in.data;
+  b.out = out.data;
+  b.in_stride = in.node_stride;
+  b.out_stride = out.node_stride;
+  return b;
+}
+
+static int64_t item_units(const BItem &b) {
+  const int64_t nodes_per_unit = (int64_t)b.npw * kBatchWarps * b.rounds;
+  return ((b.V + nodes_per_unit - 1) / nodes_per_unit) * b.nchunk_lev;
+}
+
+// (Re)build the device work tables of both phases from the current shapes.
+static int batch_build_tables(nb_batch *bt) {
+  std::vector<BItem> ph[2];
+  for (size_t k = 0; k < bt->src.size(); ++k) {
+    const auto &s = bt->src[k];
+    if (s.op == NB_OP_LAP) {
+      nb_field tmp = s.in;
+      tmp.data = bt->scratch[k];
+      tmp.nvar = 2;
+      const int q = s.in.dtype == NB_F64 ? 2 : 4;
+      tmp.node_stride = 2 * (int64_t)((s.in.nlev + q - 1) / q) * q;
+      tmp.lev_stride = 2;
+      ph[0].push_back(make_item(s.method, 0, s.in, tmp, bt->shape[k]));
+      ph[1].push_back(make_item(s.method, 1, tmp, s.out, bt->shape[k]));
+    } else {
+      ph[0].push_back(make_item(s.method, s.op, s.in, s.out, bt->shape[k]));
+    }
+  }
+  for (int p = 0; p < 2; ++p) {
+    int64_t u = 0;
+    for (auto &b : ph[p]) {
+      b.unit_begin = u;
+      u += item_units(b);
+    }
+    bt->nunits[p] = u;
+    bt->nitems[p] = (int)ph[p].size();
+    if (bt->d_items[p]) {
+      cudaFree(bt->d_items[p]);
+      bt->d_items[p] = nullptr;
+    }
+    if (!ph[p].empty()) {
+      NB_CUDA(cudaMalloc(&bt->d_items[p], ph[p].size() * sizeof(BItem)));
+      NB_CUDA(cudaMemcpy(bt->d_items[p], ph[p].data(), ph[p].size() * sizeof(BItem),
+                         cudaMemcpyHostToDevice));
+    }
+  }
+  return NB_OK;
+}
+
+// Launch the phases directly on a stream (used for capture and for tuning).
+static int batch_launch(nb_batch *bt, cudaStream_t st) {
+  NB_CUDA(cudaMemsetAsync(bt->d_counter, 0, 2 * sizeof(unsigned long long), st));
+  for (int p = 0; p < 2; ++p) {
+    if (bt->nunits[p] == 0) continue;
+    batch_kernel<<<bt->grid, kBatchThreads, 0, st>>>(bt->d_items[p], bt->nitems[p], bt->nunits[p],
+                                                     bt->d_counter + p, bt->comp);
+    count_launch(1);
+    NB_CUDA(cudaGetLastError());
+  }
+  return NB_OK;
+}
+
+static void drop_graph(nb_batch *bt) {
+  if (bt->exec) cudaGraphExecDestroy(bt->exec);
+  if (bt->graph) cudaGraphDestroy(bt->graph);
+  bt->exec = nullptr;
+  bt->graph = nullptr;
+}
+
+static int batch_capture(nb_batch *bt) {
+  drop_graph(bt);
+  cudaStream_t cs;
+  NB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  int rc = NB_OK;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaStreamDestroy(cs);
+    set_error("nb_batch: stream capture failed to start");
+    return NB_ECUDA;
+  }
+  rc = batch_launch(bt, cs);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(cs, &g);
+  cudaStreamDestroy(cs);
+  if (rc != NB_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  bt->graph = g;
+  NB_CUDA(cudaGraphInstantiate(&bt->exec, g, 0));
+  return NB_OK;
+}
+
+}  // namespace nb
+
+extern "C" {
+
+int nb_batch_create(const nb_batch_item *items, int n, nb_batch **out) {
+  if (!out || (!items && n > 0) || n < 0) {
+    nb::set_error("nb_batch_create: NULL argument or negative count");
+    return NB_EINVAL;
+  }
+  try {
+    auto *bt = new nb_batch();
+    std::lock_guard<std::mutex> lk(nb::g_tune_mu);
+    static bool loaded = false;
+    if (!loaded) {
+      nb::load_tune_cache();
+      loaded = true;
+    }
+    const std::string gpu = nb::gpu_name();
+    for (int k = 0; k < n; ++k) {
+      const nb_batch_item &it = items[k];
+      int st = nb::validate_op(it.method, it.op, &it.in, &it.out, nullptr);
+      if (st != NB_OK) {
+        nb::release(bt);
+        return st;
+      }
+      nb_batch::Src s{it.op, nb::retain(const_cast<nb_method *>(it.method)), it.in, it.out};
+      bt->src.push_back(s);
+      nb::TuneKey key{it.op, it.in.dtype == NB_F64, it.method->mesh->grid->N, it.in.nlev};
+      bt->keys.push_back(key);
+      auto g = nb::g_tune.find(gpu);
+      auto hit = (g != nb::g_tune.end()) ? g->second.find(key) : std::map<nb::TuneKey, std::pair<int, int>>::iterator();
+      bt->shape.push_back((g != nb::g_tune.end() && hit != g->second.end()) ? hit->second
+                                                                             : nb::default_shape(it.in.nlev));
+      void *scr = nullptr;
+      if (it.op == NB_OP_LAP) {
+        const int64_t elem = it.in.dtype == NB_F64 ? 8 : 4;
+        const int q = it.in.dtype == NB_F64 ? 2 : 4;
+        const int64_t stride = 2 * (int64_t)((it.in.nlev + q - 1) / q) * q;
+        if (cudaMalloc(&scr, (size_t)(stride * it.in.nnodes * elem)) != cudaSuccess) {
+          nb::release(bt);
+          nb::set_error("nb_batch_create: scratch allocation failed");
+          return NB_EOOM;
+        }
+      }
+      bt->scratch.push_back(scr);
+      bt->node_levels += it.in.nnodes * (int64_t)it.in.nlev;
+    }
+    if (cudaMalloc(&bt->d_counter, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+      nb::release(bt);
+      nb::set_error("nb_batch_create: counter allocation failed");
+      return NB_EOOM;
+    }
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, nb::batch_kernel, nb::kBatchThreads, 0);
+    bt->grid = std::max(1, sms * std::max(1, per_sm));
+    int st = nb::batch_build_tables(bt);
+    if (st != NB_OK) {
+      nb::release(bt);
+      return st;
+    }
+    *out = bt;
+    return NB_OK;
+  } catch (...) {
+    nb::set_error("nb_batch_create: host allocation failed");
+    return NB_EOOM;
+  }
+}
+
+int nb_batch_release(nb_batch *b) {
+  nb::release(b);
+  return NB_OK;
+}
+
+int nb_batch_set_compensated(nb_batch *b, int on) {
+  if (!b) {
+    nb::set_error("nb_batch_set_compensated: NULL batch");
+    return NB_EINVAL;
+  }
+  b->comp = on ? 1 : 0;
+  nb::drop_graph(b);
+  return NB_OK;
+}
+
+int nb_batch_run(nb_batch *b, void *stream) {
+  if (!b) {
+    nb::set_error("nb_batch_run: NULL batch");
+    return NB_EINVAL;
+  }
+  if (!b->exec) {
+    const int st = nb::batch_capture(b);
+    if (st != NB_OK) return st;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const cudaError_t e = cudaGraphLaunch(b->exec, s);
+  if (e != cudaSuccess) return nb::cuda_fail(e, "cudaGraphLaunch");
+  nb::count_launch((b->nunits[0] > 0) + (b->nunits[1] > 0));
+  return NB_OK;
+}
+
+int nb_batch_info(const nb_batch *b, int64_t *units, int64_t *node_levels, int32_t *nodes_per_warp,
+                  int32_t *levels_per_block) {
+  if (!b) {
+    nb::set_error("nb_batch_info: NULL batch");
+    return NB_EINVAL;
+  }
+  if (units) *units = b->nunits[0] + b->nunits[1];
+  if (node_levels) *node_levels = b->node_levels;
+  for (size_t k = 0; k < b->src.size(); ++k) {
+    if (nodes_per_warp) nodes_per_warp[k] = b->shape[k].second;
+    if (levels_per_block) levels_per_block[k] = b->shape[k].first;
+  }
+  return NB_OK;
+}
+
+int nb_batch_tune(nb_batch *b, void *stream) {
+  if (!b) {
+    nb::set_error("nb_batch_tune: NULL batch");
+    return NB_EINVAL;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int lpbs[] = {4, 8, 16, 32, 64};
+  const int npws[] = {1, 2, 4, 8, 16, 32};
+  const std::string gpu = nb::gpu_name();
+  cudaEvent_t e0, e1;
+  NB_CUDA(cudaEventCreate(&e0));
+  NB_CUDA(cudaEventCreate(&e1));
+  // tune each item class once, timing a batch that holds only that item
+  std::map<nb::TuneKey, std::pair<int, int>> best;
+  int rc = NB_OK;
+  for (size_t k = 0; k < b->src.size() && rc == NB_OK; ++k) {
+    if (best.count(b->keys[k])) continue;
+    nb_batch one;
+    one.src.push_back(b->src[k]);
+    nb::retain(b->src[k].method);
+    one.scratch.push_back(b->scratch[k]);
+    one.grid = b->grid;
+    one.comp = b->comp;
+    one.shape.push_back({0, 0});
+    if (cudaMalloc(&one.d_counter, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+      one.scratch[0] = nullptr;
+      rc = NB_EOOM;
+      break;
+    }
+    float best_ms = 1e30f;
+    std::pair<int, int> best_shape = nb::default_shape(b->src[k].in.nlev);
+    for (int lpb : lpbs) {
+      if (lpb > 2 * b->src[k].in.nlev && lpb != 4) continue;
+      for (int npw : npws) {
+        one.shape[0] = {lpb, npw};
+        if ((rc = nb::batch_build_tables(&one)) != NB_OK) break;
+        for (int w = 0; w < 2 && rc == NB_OK; ++w) rc = nb::batch_launch(&one, st);
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 5 && rc == NB_OK; ++r) rc = nb::batch_launch(&one, st);
+        cudaEventRecord(e1, st);
+        if (rc != NB_OK) break;
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+          best_ms = ms;
+          best_shape = {lpb, npw};
+        }
+      }
+      if (rc != NB_OK) break;
+    }
+    one.scratch[0] = nullptr;  // owned by the outer batch
+    best[b->keys[k]] = best_shape;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != NB_OK) return rc;
+  {
+    std::lock_guard<std::mutex> lk(nb::g_tune_mu);
+    for (auto &kv : best) nb::g_tune[gpu][kv.first] = kv.second;
+    nb::save_tune_cache();
+  }
+  for (size_t k = 0; k < b->src.size(); ++k) b->shape[k] = best[b->keys[k]];
+  nb::drop_graph(b);
+  return nb::batch_build_tables(b);
+}
+
+}  // extern "C"

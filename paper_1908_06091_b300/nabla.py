@@ -46,6 +46,11 @@ class nb_field(ctypes.Structure):
                 ("node_stride", ctypes.c_int64), ("lev_stride", ctypes.c_int64)]
 
 
+class nb_batch_item(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("reserved", ctypes.c_int32), ("method", ctypes.c_void_p),
+                ("inp", nb_field), ("out", nb_field)]
+
+
 _lib = None
 
 _P = ctypes.c_void_p
@@ -90,6 +95,12 @@ SIGNATURES = {
     "nb_nabla_apply_host": [_P, _I, _P, _P, _FP, _FP, _FP, _P],
     "nb_launch_count": [_I64P],
     "nb_device_status": [_I, ctypes.POINTER(ctypes.c_int32)],
+    "nb_batch_create": [_P, _I, ctypes.POINTER(_P)],
+    "nb_batch_release": [_P],
+    "nb_batch_tune": [_P, _P],
+    "nb_batch_run": [_P, _P],
+    "nb_batch_set_compensated": [_P, _I],
+    "nb_batch_info": [_P, _I64P, _I64P, _P, _P],
 }
 
 
@@ -330,6 +341,47 @@ def curl(method, uv, z, stream=None):
 
 def laplacian(method, f, lap, scratch=None, stream=None):
     return apply(method, OP_LAP, f, lap, scratch=scratch, stream=stream)
+
+
+class Batch(_Handle):
+    """Many nabla operations in one persistent launch replayed from a CUDA graph.
+
+    items: list of (op, method, in_tensor, out_tensor)."""
+    _release = "nb_batch_release"
+
+    def __init__(self, items):
+        super().__init__()
+        self._keep = items  # the tensors must outlive the batch
+        arr = (nb_batch_item * len(items))()
+        for k, (op, meth, xin, xout) in enumerate(items):
+            code = OPS[op] if isinstance(op, str) else int(op)
+            nin = 2 if code in (OP_DIV, OP_CURL) else 1
+            nout = 2 if code == OP_GRAD else 1
+            arr[k].op = code
+            arr[k].reserved = 0
+            arr[k].method = meth.handle.value
+            arr[k].inp = field_view(xin, nin)
+            arr[k].out = field_view(xout, nout)
+        check(lib().nb_batch_create(arr, len(items), ctypes.byref(self._h)))
+        self.n = len(items)
+
+    def tune(self, stream=None):
+        check(lib().nb_batch_tune(self._h, ctypes.c_void_p(_stream(stream))))
+
+    def run(self, stream=None):
+        check(lib().nb_batch_run(self._h, ctypes.c_void_p(_stream(stream))))
+
+    def set_compensated(self, on: bool):
+        check(lib().nb_batch_set_compensated(self._h, 1 if on else 0))
+
+    def info(self):
+        u, nl = ctypes.c_int64(), ctypes.c_int64()
+        npw = np.zeros(self.n, dtype=np.int32)
+        lpb = np.zeros(self.n, dtype=np.int32)
+        check(lib().nb_batch_info(self._h, ctypes.byref(u), ctypes.byref(nl), npw.ctypes.data,
+                                  lpb.ctypes.data))
+        return {"units": u.value, "node_levels": nl.value, "nodes_per_warp": npw,
+                "levels_per_block": lpb}
 
 
 NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024

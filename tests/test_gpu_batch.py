@@ -1,0 +1,99 @@
+"""Batched persistent launch (CUDA graph) against single-op runs.
+
+Every batched result must equal the same operation run alone on the direct
+kernels bit for bit (same per-point arithmetic), before and after autotuning;
+FP32 results must also meet the oracle gate."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from paper_1908_06091_b300 import nabla
+from gpu_helpers import inputs, oracle_mesh, oracle_op, product, rel_l2, to_device, to_grid
+
+pytestmark = pytest.mark.gpu
+
+
+def _mixed_items(seed=3):
+    rng = np.random.default_rng(seed)
+    items, meta = [], []
+    for N in (16, 24, 32):
+        g, m, meth = product(N)
+        om = oracle_mesh(N)
+        perm = m.permutation()
+        for nlev in (1, 5, 37):
+            for dtype in (torch.float32, torch.float64):
+                f, uv = inputs(om, nlev, 10, dtype, seed=int(rng.integers(1 << 30)))
+                fs = nabla.NodeColumns(meth, nlev, dtype)
+                for op in ("grad", "div", "curl", "lap"):
+                    x = to_device(fs, f if op in ("grad", "lap") else uv, perm, 1 if op in ("grad", "lap") else 2)
+                    out = fs.create_field(nvar=2 if op == "grad" else 1, fill=float("nan"))
+                    items.append((op, meth, x, out))
+                    meta.append((N, nlev, dtype, op, fs, f if op in ("grad", "lap") else uv))
+    return items, meta
+
+
+def _single_direct(meth, fs, op, x):
+    meth.set_kernel(nabla.KERNEL_DIRECT)
+    out = fs.create_field(nvar=2 if op == "grad" else 1, fill=float("nan"))
+    nabla.apply(meth, op, x, out)
+    meth.set_kernel(nabla.KERNEL_AUTO)
+    return out
+
+
+def test_batched_results_equal_single_ops_bitwise_and_meet_gate():
+    items, meta = _mixed_items()
+    b = nabla.Batch(items)
+    b.run()
+    torch.cuda.synchronize()
+    assert nabla.device_status() == 0
+    for (op, meth, x, out), (N, nlev, dtype, _, fs, xh) in zip(items, meta):
+        ref = _single_direct(meth, fs, op, x)
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref), (N, nlev, dtype, op)
+    # spot-check the oracle gate on a few items
+    for k in range(0, len(items), 7):
+        (op, meth, x, out), (N, nlev, dtype, _, fs, xh) = items[k], meta[k]
+        got = to_grid(out, product(N)[1].permutation())
+        ref = oracle_op(oracle_mesh(N), op, xh.astype(np.float64))
+        assert rel_l2(got, ref) <= (1e-5 if dtype == torch.float32 else 1e-12), (N, nlev, dtype, op)
+
+
+def test_graph_replay_is_deterministic_and_tuning_keeps_results(tmp_path, monkeypatch):
+    monkeypatch.setenv("NB_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    items, meta = _mixed_items(seed=5)
+    b = nabla.Batch(items)
+    b.run()
+    torch.cuda.synchronize()
+    first = [o.clone() for (_, _, _, o) in items]
+    for _, _, _, o in items:
+        o.fill_(float("nan"))
+    b.run()
+    torch.cuda.synchronize()
+    assert all(torch.equal(a, o) for a, (_, _, _, o) in zip(first, items))
+    before = b.info()
+    b.tune()
+    after = b.info()
+    for _, _, _, o in items:
+        o.fill_(float("nan"))
+    b.run()
+    torch.cuda.synchronize()
+    assert all(torch.equal(a, o) for a, (_, _, _, o) in zip(first, items))
+    assert after["node_levels"] == before["node_levels"]
+    assert set(after["nodes_per_warp"]) <= {1, 2, 4, 8, 16, 32}
+    assert set(after["levels_per_block"]) <= {4, 8, 16, 32, 64}
+    lines = (tmp_path / "tune.txt").read_text().strip().splitlines()
+    assert len(lines) >= 1 and all(len(ln.split("|")) == 7 for ln in lines)
+
+
+def test_batch_rejects_bad_items():
+    g, m, meth = product(16)
+    fs = nabla.NodeColumns(meth, 4, torch.float32)
+    f = fs.create_field()
+    with pytest.raises((nabla.NablaError, ValueError)):
+        nabla.Batch([("grad", meth, f, fs.create_field())])  # grad output must be a vector
+    g2, m2, meth2 = product(24)
+    fs2 = nabla.NodeColumns(meth2, 4, torch.float32)
+    with pytest.raises(nabla.NablaError):
+        nabla.Batch([("grad", meth, fs2.create_field(), fs2.create_field(nvar=2))])
