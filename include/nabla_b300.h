@@ -64,6 +64,7 @@ typedef struct nb_mesh nb_mesh;
 typedef struct nb_method nb_method;
 typedef struct nb_fs nb_fs;
 typedef struct nb_batch nb_batch;
+typedef struct nb_server nb_server;
 
 /* A non-owning view of a field in device memory (Sec. 4.6, Fig. 32). */
 typedef struct nb_field {
@@ -280,6 +281,73 @@ int nb_batch_set_compensated(nb_batch *batch, int on);
  * chosen nodes-per-warp and levels-per-block (arrays of n, may be NULL). */
 int nb_batch_info(const nb_batch *batch, int64_t *units, int64_t *node_levels,
                   int32_t *nodes_per_warp, int32_t *levels_per_block);
+
+/* ---------------------------------------------------------------- serving
+ * Continuous-batching server for derived-field requests (the serving pattern
+ * named for this hot path; the paper has no server).  Grids are registered
+ * once and stay resident with two spherical-harmonic bases used to
+ * synthesise request inputs on the device.  A worker thread admits arrived
+ * requests in arrival order while the device-memory budget and the in-flight
+ * limit allow, takes the request's field memory from the CUDA memory pool
+ * (stream ordered), synthesises its inputs, runs the operator on the least
+ * loaded of `nstreams` streams and frees everything when the request's
+ * completion event has fired, so requests overlap on the device.  A result is
+ * computed by the same kernels whether the request runs alone or among
+ * others, so it is bitwise the same. */
+typedef struct nb_request {
+  int32_t op;          /* nb_op */
+  int32_t N;           /* Gaussian number of a registered grid */
+  int32_t nlev;        /* levels, 1..4096 */
+  int32_t nfields;     /* fields, 1..64; each gets the operator */
+  int32_t dtype;       /* NB_F32 or NB_F64 */
+  int32_t keep_output; /* copy outputs to the host on completion (tests) */
+  uint64_t seed;       /* input synthesis seed */
+} nb_request;
+
+typedef struct nb_result {
+  uint64_t ticket;
+  int32_t status;      /* NB_OK or the error of this request */
+  int32_t reserved;
+  double arrival_s, admit_s, done_s; /* seconds, server clock (trace: from its start) */
+  int64_t node_levels; /* nfields x V x nlev */
+  int64_t bytes;       /* device memory the request held */
+} nb_result;
+
+/* Server on the current device with a device-memory budget in bytes for
+ * request fields, nstreams streams (1..64) and at most max_inflight requests
+ * on the device at once.  Sets the device's default memory pool to keep freed
+ * memory cached.  Errors: NB_EINVAL, NB_ECUDA, NB_EOOM. */
+int nb_server_create(int64_t hbm_budget, int nstreams, int max_inflight, nb_server **out);
+int nb_server_release(nb_server *server);
+
+/* Make the method's grid resident for requests with N = its Gaussian number.
+ * scalar_basis: host double [V][8]; wind_basis: host double [V][8][2] (east,
+ * north), both in functionspace node order; copied to the device.  Request
+ * inputs are per-level mixtures of these 8 fields with weights drawn from the
+ * request seed (SplitMix64). */
+int nb_server_add_grid(nb_server *server, const nb_method *method, const double *scalar_basis,
+                       const double *wind_basis);
+
+/* Queue a request now; returns its ticket.  Errors: NB_EINVAL (grid not
+ * resident, bad fields), NB_EBUDGET (needs more than the whole budget). */
+int nb_server_submit(nb_server *server, const nb_request *request, uint64_t *ticket);
+
+/* Wait up to timeout_ms for a request; NB_ETIMEOUT if it is still queued or
+ * running, NB_OK with its result otherwise. */
+int nb_server_wait(nb_server *server, uint64_t ticket, double timeout_ms, nb_result *result);
+
+/* Copy a finished request's kept outputs (nfields x [V][Lp][nvar] of its
+ * dtype, Lp the padded level stride) to host memory of exactly `bytes`. */
+int nb_server_output(nb_server *server, uint64_t ticket, void *host_out, int64_t bytes);
+
+/* Budget in use, its peak, queued and in-flight request counts. */
+int nb_server_stats(nb_server *server, int64_t *used, int64_t *peak_used, int32_t *pending,
+                    int32_t *inflight);
+
+/* Replay a trace: submit request k at arrival_s[k] seconds after the call
+ * starts, wait for all, fill results[k] (times relative to the call start). */
+int nb_server_run_trace(nb_server *server, const nb_request *requests, const double *arrival_s,
+                        int n, nb_result *results);
 
 /* ------------------------------------------------------ kernel control */
 

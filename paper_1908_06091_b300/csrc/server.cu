@@ -1,0 +1,477 @@
+// server.cu -- continuous-batching request server for derived fields.
+//
+// A request asks for one nabla operator on 1..8 fields of a resident grid
+// with a given number of levels.  A worker thread admits arriving requests in
+// arrival order while the device-memory budget and the in-flight limit allow,
+// takes stream-ordered memory for the request's fields from the CUDA memory
+// pool, synthesises the input fields on the device from the grid's resident
+// spherical-harmonic bases (per-level mixing weights drawn from the request
+// seed with SplitMix64), launches the operator on one of several streams and
+// records a completion event.  Finished requests (event polled) release their
+// memory and budget immediately, so requests that arrive while others are on
+// the GPU are admitted as memory frees up and their work overlaps on the
+// device.  The same engine with one stream, one request in flight and FP64
+// fields gives the sequential plain-FP64 baseline.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "kernels_common.cuh"
+
+namespace nb {
+
+int validate_op(const nb_method *m, int op, const nb_field *in, const nb_field *out,
+                const nb_field *scratch);
+
+// SplitMix64 (Steele, Lea and Flood, OOPSLA 2014): the output function of a
+// 64-bit counter-based generator.
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+  z += 0x9e3779b97f4a7c15ull;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+// Mixing weight of basis b at level k of field f: uniform in [-1, 1) scaled
+// by 1 + k / nlev.
+__device__ __forceinline__ double mix_weight(uint64_t seed, int f, int k, int b, int nlev) {
+  const uint64_t z = splitmix64(seed ^ ((uint64_t)f << 40) ^ ((uint64_t)k << 8) ^ (uint64_t)b);
+  const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+  return (2.0 * u - 1.0) * (1.0 + (double)k / nlev);
+}
+
+// in[node][k][c] = sum_b w(f, k, b) basis[node][b][c]  (c < nvar)
+template <class T>
+__global__ void __launch_bounds__(256) synth_fields_kernel(const double *__restrict__ basis, int nvar,
+                                                           int64_t V, int nlev, int64_t stride,
+                                                           uint64_t seed, int f, T *out) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= V * nlev) return;
+  const int64_t i = idx / nlev;
+  const int k = (int)(idx - i * nlev);
+  double acc0 = 0, acc1 = 0;
+  for (int b = 0; b < 8; ++b) {
+    const double w = mix_weight(seed, f, k, b, nlev);
+    acc0 = fma(w, basis[(i * 8 + b) * nvar], acc0);
+    if (nvar == 2) acc1 = fma(w, basis[(i * 8 + b) * 2 + 1], acc1);
+  }
+  T *o = out + i * stride + (int64_t)k * nvar;
+  o[0] = (T)acc0;
+  if (nvar == 2) o[1] = (T)acc1;
+}
+
+struct SrvGrid {
+  nb_method *method = nullptr;
+  double *d_scalar = nullptr;  // [V][8]
+  double *d_wind = nullptr;    // [V][8][2]
+};
+
+struct SrvReq {
+  uint64_t ticket = 0;
+  nb_request r{};
+  double arrival = 0, admit = -1, done = -1;
+  int status = NB_OK;
+  int64_t bytes = 0, node_levels = 0;
+  int stream = -1;
+  cudaEvent_t ev = nullptr;
+  std::vector<void *> bufs;
+  std::vector<char> host_out;  // kept outputs (tests)
+};
+
+}  // namespace nb
+
+struct nb_server : nb::RefCounted {
+  int device = 0;
+  int64_t budget = 0;
+  int max_inflight = 0;
+  std::vector<cudaStream_t> streams;
+  std::map<int, nb::SrvGrid> grids;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<nb::SrvReq *> pending;  // arrived, not admitted
+  std::vector<nb::SrvReq *> inflight;
+  std::map<uint64_t, nb::SrvReq *> all;
+  std::atomic<uint64_t> next_ticket{1};
+  int64_t used = 0, peak_used = 0;
+  int rr = 0;
+  bool stop = false;
+  std::thread worker;
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  double now() const {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  ~nb_server() override;
+};
+
+namespace nb {
+
+static int64_t req_bytes(const nb_server *s, const nb_request &r, int64_t V) {
+  const int64_t elem = r.dtype == NB_F64 ? 8 : 4;
+  const int q = r.dtype == NB_F64 ? 2 : 4;
+  const int64_t lp = (int64_t)((r.nlev + q - 1) / q) * q;
+  const int in_var = (r.op == NB_OP_DIV || r.op == NB_OP_CURL) ? 2 : 1;
+  const int out_var = r.op == NB_OP_GRAD ? 2 : 1;
+  const int scr_var = r.op == NB_OP_LAP ? 2 : 0;
+  (void)s;
+  return (int64_t)r.nfields * V * lp * elem * (in_var + out_var + scr_var);
+}
+
+// Enqueue one admitted request on its stream (caller holds no lock).
+static int launch_request(nb_server *s, SrvReq *q) {
+  const nb_request &r = q->r;
+  SrvGrid &g = s->grids[r.N];
+  nb_method *m = g.method;
+  const int64_t V = m->mesh->V;
+  cudaStream_t st = s->streams[q->stream];
+  const int64_t elem = r.dtype == NB_F64 ? 8 : 4;
+  const int qq = r.dtype == NB_F64 ? 2 : 4;
+  const int64_t lp = (int64_t)((r.nlev + qq - 1) / qq) * qq;
+  const int in_var = (r.op == NB_OP_DIV || r.op == NB_OP_CURL) ? 2 : 1;
+  const int out_var = r.op == NB_OP_GRAD ? 2 : 1;
+  for (int f = 0; f < r.nfields; ++f) {
+    void *din = nullptr, *dout = nullptr, *dscr = nullptr;
+    NB_CUDA(cudaMallocAsync(&din, (size_t)(V * lp * in_var * elem), st));
+    q->bufs.push_back(din);
+    NB_CUDA(cudaMallocAsync(&dout, (size_t)(V * lp * out_var * elem), st));
+    q->bufs.push_back(dout);
+    if (r.op == NB_OP_LAP) {
+      NB_CUDA(cudaMallocAsync(&dscr, (size_t)(V * lp * 2 * elem), st));
+      q->bufs.push_back(dscr);
+    }
+    const double *basis = in_var == 2 ? g.d_wind : g.d_scalar;
+    const int64_t pts = V * r.nlev;
+    const unsigned blocks = (unsigned)((pts + 255) / 256);
+    if (r.dtype == NB_F64)
+      synth_fields_kernel<double><<<blocks, 256, 0, st>>>(basis, in_var, V, r.nlev, lp * in_var, r.seed,
+                                                          f, static_cast<double *>(din));
+    else
+      synth_fields_kernel<float><<<blocks, 256, 0, st>>>(basis, in_var, V, r.nlev, lp * in_var, r.seed, f,
+                                                         static_cast<float *>(din));
+    count_launch(1);
+    NB_CUDA(cudaGetLastError());
+    nb_field fi{din, r.dtype, in_var, V, r.nlev, 0, lp * in_var, in_var};
+    nb_field fo{dout, r.dtype, out_var, V, r.nlev, 0, lp * out_var, out_var};
+    nb_field fsc{dscr, r.dtype, 2, V, r.nlev, 0, lp * 2, 2};
+    const int rc = launch_op(m, r.op, &fi, &fo, r.op == NB_OP_LAP ? &fsc : nullptr, st);
+    if (rc != NB_OK) return rc;
+  }
+  NB_CUDA(cudaEventCreateWithFlags(&q->ev, cudaEventDisableTiming));
+  NB_CUDA(cudaEventRecord(q->ev, st));
+  return NB_OK;
+}
+
+static void finish_request(nb_server *s, SrvReq *q) {
+  cudaStream_t st = s->streams[q->stream];
+  if (q->r.keep_output && q->status == NB_OK) {
+    // outputs are the 2nd of every 2 (or 3, Laplacian) buffers
+    const int per = q->r.op == NB_OP_LAP ? 3 : 2;
+    const int64_t V = s->grids[q->r.N].method->mesh->V;
+    const int64_t elem = q->r.dtype == NB_F64 ? 8 : 4;
+    const int qq = q->r.dtype == NB_F64 ? 2 : 4;
+    const int64_t lp = (int64_t)((q->r.nlev + qq - 1) / qq) * qq;
+    const int out_var = q->r.op == NB_OP_GRAD ? 2 : 1;
+    const int64_t one = V * lp * out_var * elem;
+    q->host_out.resize((size_t)(one * q->r.nfields));
+    for (int f = 0; f < q->r.nfields; ++f)
+      cudaMemcpy(q->host_out.data() + f * one, q->bufs[f * per + 1], (size_t)one, cudaMemcpyDeviceToHost);
+  }
+  for (void *p : q->bufs) cudaFreeAsync(p, st);
+  q->bufs.clear();
+  if (q->ev) cudaEventDestroy(q->ev);
+  q->ev = nullptr;
+}
+
+static void worker_loop(nb_server *s) {
+  cudaSetDevice(s->device);
+  std::unique_lock<std::mutex> lk(s->mu);
+  for (;;) {
+    // retire finished requests
+    for (size_t k = 0; k < s->inflight.size();) {
+      SrvReq *q = s->inflight[k];
+      const cudaError_t e = cudaEventQuery(q->ev);
+      if (e == cudaErrorNotReady) {
+        ++k;
+        continue;
+      }
+      if (e != cudaSuccess) q->status = NB_ECUDA;
+      q->done = s->now();
+      lk.unlock();
+      finish_request(s, q);
+      lk.lock();
+      s->used -= q->bytes;
+      s->inflight.erase(s->inflight.begin() + (long)k);
+      s->cv.notify_all();
+    }
+    // admit in arrival order while budget and slots allow
+    while (!s->pending.empty() && (int)s->inflight.size() < s->max_inflight) {
+      SrvReq *q = s->pending.front();
+      if (s->used + q->bytes > s->budget) break;
+      s->pending.pop_front();
+      s->used += q->bytes;
+      s->peak_used = std::max(s->peak_used, s->used);
+      q->admit = s->now();
+      // least-loaded stream: the one with the fewest in-flight requests
+      std::vector<int> load(s->streams.size(), 0);
+      for (SrvReq *o : s->inflight) load[o->stream]++;
+      q->stream = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      s->inflight.push_back(q);
+      lk.unlock();
+      const int rc = launch_request(s, q);
+      lk.lock();
+      if (rc != NB_OK) {
+        q->status = rc;
+        if (!q->ev) {  // nothing to wait for: retire now
+          q->done = s->now();
+          lk.unlock();
+          finish_request(s, q);
+          lk.lock();
+          s->used -= q->bytes;
+          s->inflight.erase(std::find(s->inflight.begin(), s->inflight.end(), q));
+          s->cv.notify_all();
+        }
+      }
+    }
+    if (s->stop && s->pending.empty() && s->inflight.empty()) return;
+    if (s->inflight.empty())
+      s->cv.wait_for(lk, std::chrono::milliseconds(2));
+    else {
+      lk.unlock();
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
+      lk.lock();
+    }
+  }
+}
+
+}  // namespace nb
+
+nb_server::~nb_server() {
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    stop = true;
+  }
+  cv.notify_all();
+  if (worker.joinable()) worker.join();
+  for (auto &kv : all) delete kv.second;
+  for (auto &kv : grids) {
+    if (kv.second.d_scalar) cudaFree(kv.second.d_scalar);
+    if (kv.second.d_wind) cudaFree(kv.second.d_wind);
+    nb::release(kv.second.method);
+  }
+  for (cudaStream_t st : streams) cudaStreamDestroy(st);
+}
+
+extern "C" {
+
+int nb_server_create(int64_t hbm_budget, int nstreams, int max_inflight, nb_server **out) {
+  if (!out || hbm_budget <= 0 || nstreams < 1 || nstreams > 64 || max_inflight < 1) {
+    nb::set_error("nb_server_create: need out, budget > 0, 1 <= nstreams <= 64, max_inflight >= 1");
+    return NB_EINVAL;
+  }
+  try {
+    auto *s = new nb_server();
+    s->budget = hbm_budget;
+    s->max_inflight = max_inflight;
+    if (cudaGetDevice(&s->device) != cudaSuccess) {
+      delete s;
+      nb::set_error("nb_server_create: no CUDA device");
+      return NB_ECUDA;
+    }
+    for (int k = 0; k < nstreams; ++k) {
+      cudaStream_t st;
+      if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+        delete s;
+        nb::set_error("nb_server_create: stream creation failed");
+        return NB_ECUDA;
+      }
+      s->streams.push_back(st);
+    }
+    // keep freed request memory in the pool instead of returning it
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, s->device) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    s->worker = std::thread(nb::worker_loop, s);
+    *out = s;
+    return NB_OK;
+  } catch (...) {
+    nb::set_error("nb_server_create: host allocation failed");
+    return NB_EOOM;
+  }
+}
+
+int nb_server_release(nb_server *s) {
+  nb::release(s);
+  return NB_OK;
+}
+
+int nb_server_add_grid(nb_server *s, const nb_method *m, const double *scalar_basis,
+                       const double *wind_basis) {
+  if (!s || !m || !scalar_basis || !wind_basis) {
+    nb::set_error("nb_server_add_grid: NULL argument");
+    return NB_EINVAL;
+  }
+  const int N = m->mesh->grid->N;
+  const int64_t V = m->mesh->V;
+  nb::SrvGrid g;
+  g.method = nb::retain(const_cast<nb_method *>(m));
+  if (cudaMalloc(&g.d_scalar, (size_t)(V * 8 * 8)) != cudaSuccess ||
+      cudaMalloc(&g.d_wind, (size_t)(V * 16 * 8)) != cudaSuccess ||
+      cudaMemcpy(g.d_scalar, scalar_basis, (size_t)(V * 8 * 8), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(g.d_wind, wind_basis, (size_t)(V * 16 * 8), cudaMemcpyHostToDevice) != cudaSuccess) {
+    if (g.d_scalar) cudaFree(g.d_scalar);
+    if (g.d_wind) cudaFree(g.d_wind);
+    nb::release(g.method);
+    nb::set_error("nb_server_add_grid: device allocation or copy failed");
+    return NB_EOOM;
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->grids.find(N);
+  if (it != s->grids.end()) {
+    cudaFree(it->second.d_scalar);
+    cudaFree(it->second.d_wind);
+    nb::release(it->second.method);
+  }
+  s->grids[N] = g;
+  return NB_OK;
+}
+
+int nb_server_submit(nb_server *s, const nb_request *r, uint64_t *ticket) {
+  if (!s || !r || !ticket) {
+    nb::set_error("nb_server_submit: NULL argument");
+    return NB_EINVAL;
+  }
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto g = s->grids.find(r->N);
+  if (g == s->grids.end()) {
+    nb::set_error("nb_server_submit: grid O" + std::to_string(r->N) + " is not resident");
+    return NB_EINVAL;
+  }
+  if (r->op < NB_OP_GRAD || r->op > NB_OP_LAP || r->nlev < 1 || r->nlev > 4096 || r->nfields < 1 ||
+      r->nfields > 64 || (r->dtype != NB_F32 && r->dtype != NB_F64)) {
+    nb::set_error("nb_server_submit: bad op, nlev, nfields or dtype");
+    return NB_EINVAL;
+  }
+  auto *q = new nb::SrvReq();
+  q->r = *r;
+  q->bytes = nb::req_bytes(s, *r, g->second.method->mesh->V);
+  if (q->bytes > s->budget) {
+    delete q;
+    nb::set_error("nb_server_submit: request needs more memory than the whole budget");
+    return NB_EBUDGET;
+  }
+  q->node_levels = (int64_t)r->nfields * g->second.method->mesh->V * r->nlev;
+  q->ticket = s->next_ticket.fetch_add(1);
+  q->arrival = s->now();
+  s->all[q->ticket] = q;
+  s->pending.push_back(q);
+  *ticket = q->ticket;
+  lk.unlock();
+  s->cv.notify_all();
+  return NB_OK;
+}
+
+// NB_OK with the result when the request has finished; NB_ETIMEOUT if it is
+// still queued or running after waiting up to timeout_ms (0 = just look).
+int nb_server_wait(nb_server *s, uint64_t ticket, double timeout_ms, nb_result *res) {
+  if (!s || !res) {
+    nb::set_error("nb_server_wait: NULL argument");
+    return NB_EINVAL;
+  }
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->all.find(ticket);
+  if (it == s->all.end()) {
+    nb::set_error("nb_server_wait: unknown ticket");
+    return NB_EINVAL;
+  }
+  nb::SrvReq *q = it->second;
+  const auto deadline = std::chrono::steady_clock::now() +
+                        std::chrono::microseconds((int64_t)(timeout_ms * 1000.0));
+  while (q->done < 0) {
+    if (s->cv.wait_until(lk, deadline) == std::cv_status::timeout && q->done < 0) return NB_ETIMEOUT;
+  }
+  res->ticket = q->ticket;
+  res->status = q->status;
+  res->reserved = 0;
+  res->arrival_s = q->arrival;
+  res->admit_s = q->admit;
+  res->done_s = q->done;
+  res->node_levels = q->node_levels;
+  res->bytes = q->bytes;
+  return NB_OK;
+}
+
+int nb_server_output(nb_server *s, uint64_t ticket, void *host_out, int64_t bytes) {
+  if (!s || !host_out) {
+    nb::set_error("nb_server_output: NULL argument");
+    return NB_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->all.find(ticket);
+  if (it == s->all.end() || it->second->done < 0 || !it->second->r.keep_output) {
+    nb::set_error("nb_server_output: unknown, unfinished or output not kept");
+    return NB_EINVAL;
+  }
+  if ((int64_t)it->second->host_out.size() != bytes) {
+    nb::set_error("nb_server_output: size mismatch");
+    return NB_ESHAPE;
+  }
+  std::memcpy(host_out, it->second->host_out.data(), (size_t)bytes);
+  return NB_OK;
+}
+
+int nb_server_stats(nb_server *s, int64_t *used, int64_t *peak_used, int32_t *pending,
+                    int32_t *inflight) {
+  if (!s) {
+    nb::set_error("nb_server_stats: NULL server");
+    return NB_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (used) *used = s->used;
+  if (peak_used) *peak_used = s->peak_used;
+  if (pending) *pending = (int32_t)s->pending.size();
+  if (inflight) *inflight = (int32_t)s->inflight.size();
+  return NB_OK;
+}
+
+// Replay a trace: request k is submitted at arrival_s[k] seconds after the
+// call starts (host clock, sleeping between arrivals), then the call waits
+// for all of them and fills results[k] (times relative to the call start).
+int nb_server_run_trace(nb_server *s, const nb_request *reqs, const double *arrival_s, int n,
+                        nb_result *results) {
+  if (!s || (n > 0 && (!reqs || !arrival_s || !results)) || n < 0) {
+    nb::set_error("nb_server_run_trace: NULL argument");
+    return NB_EINVAL;
+  }
+  std::vector<uint64_t> tickets(n, 0);
+  const double base = s->now();
+  for (int k = 0; k < n; ++k) {
+    for (;;) {
+      const double wait = base + arrival_s[k] - s->now();
+      if (wait <= 0) break;
+      if (wait > 2e-3) std::this_thread::sleep_for(std::chrono::microseconds((int64_t)((wait - 1e-3) * 1e6)));
+    }
+    const int rc = nb_server_submit(s, &reqs[k], &tickets[k]);
+    if (rc != NB_OK) return rc;
+  }
+  for (int k = 0; k < n; ++k) {
+    const int rc = nb_server_wait(s, tickets[k], 3.6e6, &results[k]);
+    if (rc != NB_OK) return rc;
+    results[k].arrival_s -= base;
+    results[k].admit_s -= base;
+    results[k].done_s -= base;
+  }
+  return NB_OK;
+}
+
+}  // extern "C"

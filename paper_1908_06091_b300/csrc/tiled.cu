@@ -581,7 +581,8 @@ int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, 
   if (in->dtype != NB_F32) return NB_OK;
   const bool aligned = (((uintptr_t)in->data | (uintptr_t)out->data) & 15u) == 0 &&
                        in->node_stride % 4 == 0 && out->node_stride % 4 == 0;
-  if (!aligned || in->nlev < 4) return NB_OK;
+  // short columns leave most staged items idle: the direct kernels do better
+  if (!aligned || in->nlev < 16) return NB_OK;
   const uint32_t row_bytes = (uint32_t)(in->node_stride * 4);
   const int G = (in->nlev + 3) / 4;
   const int nvar = in->nvar;

@@ -51,6 +51,18 @@ class nb_batch_item(ctypes.Structure):
                 ("inp", nb_field), ("out", nb_field)]
 
 
+class nb_request(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("N", ctypes.c_int32), ("nlev", ctypes.c_int32),
+                ("nfields", ctypes.c_int32), ("dtype", ctypes.c_int32), ("keep_output", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
+
+
+class nb_result(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("arrival_s", ctypes.c_double), ("admit_s", ctypes.c_double), ("done_s", ctypes.c_double),
+                ("node_levels", ctypes.c_int64), ("bytes", ctypes.c_int64)]
+
+
 _lib = None
 
 _P = ctypes.c_void_p
@@ -101,6 +113,14 @@ SIGNATURES = {
     "nb_batch_run": [_P, _P],
     "nb_batch_set_compensated": [_P, _I],
     "nb_batch_info": [_P, _I64P, _I64P, _P, _P],
+    "nb_server_create": [ctypes.c_int64, _I, _I, ctypes.POINTER(_P)],
+    "nb_server_release": [_P],
+    "nb_server_add_grid": [_P, _P, _P, _P],
+    "nb_server_submit": [_P, ctypes.POINTER(nb_request), ctypes.POINTER(ctypes.c_uint64)],
+    "nb_server_wait": [_P, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(nb_result)],
+    "nb_server_output": [_P, ctypes.c_uint64, _P, ctypes.c_int64],
+    "nb_server_stats": [_P, _I64P, _I64P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)],
+    "nb_server_run_trace": [_P, ctypes.POINTER(nb_request), _P, _I, ctypes.POINTER(nb_result)],
 }
 
 
@@ -382,6 +402,68 @@ class Batch(_Handle):
                                   lpb.ctypes.data))
         return {"units": u.value, "node_levels": nl.value, "nodes_per_warp": npw,
                 "levels_per_block": lpb}
+
+
+class Server(_Handle):
+    """Continuous-batching request server (see nb_server_* in the header)."""
+    _release = "nb_server_release"
+
+    def __init__(self, budget_bytes: int, nstreams: int = 4, max_inflight: int = 16):
+        super().__init__()
+        self.grids = {}
+        check(lib().nb_server_create(int(budget_bytes), int(nstreams), int(max_inflight),
+                                     ctypes.byref(self._h)))
+
+    def add_grid(self, method, scalar_basis: np.ndarray, wind_basis: np.ndarray):
+        sb = np.ascontiguousarray(scalar_basis, dtype=np.float64)
+        wb = np.ascontiguousarray(wind_basis, dtype=np.float64)
+        assert sb.shape == (method.mesh.V, 8) and wb.shape == (method.mesh.V, 8, 2)
+        check(lib().nb_server_add_grid(self._h, method.handle, sb.ctypes.data, wb.ctypes.data))
+        self.grids[method.mesh.grid.N] = method
+
+    @staticmethod
+    def request(op, N, nlev, nfields=1, dtype=NB_F32, seed=0, keep_output=False):
+        r = nb_request()
+        r.op = OPS[op] if isinstance(op, str) else int(op)
+        r.N, r.nlev, r.nfields, r.dtype = int(N), int(nlev), int(nfields), int(dtype)
+        r.keep_output = 1 if keep_output else 0
+        r.seed = int(seed)
+        return r
+
+    def submit(self, req) -> int:
+        t = ctypes.c_uint64()
+        check(lib().nb_server_submit(self._h, ctypes.byref(req), ctypes.byref(t)))
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: float = 60000.0):
+        res = nb_result()
+        check(lib().nb_server_wait(self._h, ticket, float(timeout_ms), ctypes.byref(res)))
+        return res
+
+    def output(self, ticket: int, req) -> np.ndarray:
+        meth = self.grids[req.N]
+        q = 2 if req.dtype == NB_F64 else 4
+        lp = (req.nlev + q - 1) // q * q
+        nvar = 2 if req.op == OP_GRAD else 1
+        dt = np.float64 if req.dtype == NB_F64 else np.float32
+        out = np.zeros((req.nfields, meth.mesh.V, lp, nvar), dtype=dt)
+        check(lib().nb_server_output(self._h, ticket, out.ctypes.data, out.nbytes))
+        return out[:, :, :req.nlev, :] if nvar == 2 else out[:, :, :req.nlev, 0]
+
+    def stats(self):
+        u, p = ctypes.c_int64(), ctypes.c_int64()
+        q, f = ctypes.c_int32(), ctypes.c_int32()
+        check(lib().nb_server_stats(self._h, ctypes.byref(u), ctypes.byref(p), ctypes.byref(q),
+                                    ctypes.byref(f)))
+        return {"used": u.value, "peak_used": p.value, "pending": q.value, "inflight": f.value}
+
+    def run_trace(self, reqs, arrivals):
+        n = len(reqs)
+        arr = (nb_request * n)(*reqs)
+        times = np.ascontiguousarray(arrivals, dtype=np.float64)
+        res = (nb_result * n)()
+        check(lib().nb_server_run_trace(self._h, arr, times.ctypes.data, n, res))
+        return res
 
 
 NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
