@@ -47,7 +47,7 @@ def parse():
     p.add_argument("--variant", type=int, default=0, help="kernel variant (0 auto, 1 direct, 2 tiled)")
     p.add_argument("--tile", type=int, default=0)
     p.add_argument("--batch-fields", type=int, default=64, help="0 skips the batched section")
-    p.add_argument("--serve-seconds", type=float, default=5.0, help="0 skips the serving section")
+    p.add_argument("--serve-seconds", type=float, default=2.0, help="0 skips the serving section")
     p.add_argument("--serve-rate", type=float, default=2000.0)
     p.add_argument("--stages", type=int, default=0)
     p.add_argument("--stage-kb", type=int, default=0)

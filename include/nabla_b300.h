@@ -300,7 +300,8 @@ typedef struct nb_request {
   int32_t nlev;        /* levels, 1..4096 */
   int32_t nfields;     /* fields, 1..64; each gets the operator */
   int32_t dtype;       /* NB_F32 or NB_F64 */
-  int32_t keep_output; /* copy outputs to the host on completion (tests) */
+  int32_t keep_output; /* 1: copy outputs to the host on completion;
+                          2: outputs and inputs (tests) */
   uint64_t seed;       /* input synthesis seed */
 } nb_request;
 
@@ -322,9 +323,10 @@ int nb_server_release(nb_server *server);
 
 /* Make the method's grid resident for requests with N = its Gaussian number.
  * scalar_basis: host double [V][8]; wind_basis: host double [V][8][2] (east,
- * north), both in functionspace node order; copied to the device.  Request
- * inputs are per-level mixtures of these 8 fields with weights drawn from the
- * request seed (SplitMix64). */
+ * north), both in functionspace node order; kept on the device as FP32.
+ * Request inputs are per-level mixtures of these 8 fields, computed in FP32,
+ * with weights drawn from the request seed (SplitMix64), rounded to the
+ * request's dtype. */
 int nb_server_add_grid(nb_server *server, const nb_method *method, const double *scalar_basis,
                        const double *wind_basis);
 
@@ -339,6 +341,10 @@ int nb_server_wait(nb_server *server, uint64_t ticket, double timeout_ms, nb_res
 /* Copy a finished request's kept outputs (nfields x [V][Lp][nvar] of its
  * dtype, Lp the padded level stride) to host memory of exactly `bytes`. */
 int nb_server_output(nb_server *server, uint64_t ticket, void *host_out, int64_t bytes);
+
+/* Copy a finished request's kept inputs (keep_output == 2): nfields x
+ * [V][Lp][nvar_in] of its dtype, to host memory of exactly `bytes`. */
+int nb_server_input(nb_server *server, uint64_t ticket, void *host_in, int64_t bytes);
 
 /* Budget in use, its peak, queued and in-flight request counts. */
 int nb_server_stats(nb_server *server, int64_t *used, int64_t *peak_used, int32_t *pending,

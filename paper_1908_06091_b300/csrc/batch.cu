@@ -34,9 +34,9 @@ namespace nb {
 struct BItem {
   int32_t op;     // 0 grad, 1 div, 2 curl (the Laplacian is split into 0 then 1)
   int32_t f64;
+  int32_t vec;    // FP32 with 16-byte columns: lanes take groups of 4 levels
   int32_t nlev, lpb, npw, rounds;
   int32_t nchunk_lev;
-  int32_t pad;
   int64_t V, cap_begin;
   int64_t unit_begin;  // first unit of this item in its phase
   const int32_t *row_ptr, *nbr;
@@ -137,6 +137,139 @@ __device__ __forceinline__ void unit_point_f32(const BItem &it, int64_t i, int l
   }
 }
 
+// Levels l0 .. l0+3 of one node with the direct kernels' 4-level arithmetic
+// (16-byte loads of the column and of each neighbour's column).
+__device__ __forceinline__ void unit_group4_f32(const BItem &it, int64_t i, int l0, bool comp) {
+  const int32_t p0 = __ldg(it.row_ptr + i), p1 = __ldg(it.row_ptr + i + 1);
+  if (it.op == 0) {
+    const float *f = static_cast<const float *>(it.in);
+    float fi[4], gx[4], gy[4];
+    load_scalar_f32<4>(f + i * it.in_stride, l0, it.nlev, fi);
+    if (i < it.cap_begin) {
+      const float2 *w = static_cast<const float2 *>(it.w32);
+      KahanAcc ax[4], ay[4];
+      PlainAcc px[4], py[4];
+      for (int32_t p = p0; p < p1; ++p) {
+        const int32_t j = __ldg(it.nbr + p);
+        const float2 wp = __ldg(w + p);
+        float fj[4];
+        load_scalar_f32<4>(f + (int64_t)j * it.in_stride, l0, it.nlev, fj);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float d = __fsub_rn(fj[k], fi[k]);
+          if (comp) {
+            ax[k].add_prod(wp.x, d);
+            ay[k].add_prod(wp.y, d);
+          } else {
+            px[k].add_prod(wp.x, d);
+            py[k].add_prod(wp.y, d);
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        gx[k] = comp ? ax[k].value() : px[k].value();
+        gy[k] = comp ? ay[k].value() : py[k].value();
+      }
+    } else {
+      const double2 *w = static_cast<const double2 *>(it.w64);
+      double sx[4] = {0, 0, 0, 0}, sy[4] = {0, 0, 0, 0};
+      for (int32_t p = p0; p < p1; ++p) {
+        const int32_t j = __ldg(it.nbr + p);
+        const double2 wp = __ldg(w + p);
+        float fj[4];
+        load_scalar_f32<4>(f + (int64_t)j * it.in_stride, l0, it.nlev, fj);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const double d = (double)fj[k] - (double)fi[k];
+          sx[k] = fma(wp.x, d, sx[k]);
+          sy[k] = fma(wp.y, d, sy[k]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        gx[k] = (float)sx[k];
+        gy[k] = (float)sy[k];
+      }
+    }
+    float *go = static_cast<float *>(it.out) + i * it.out_stride + 2 * l0;
+    if (l0 + 4 <= it.nlev) {
+      reinterpret_cast<float4 *>(go)[0] = make_float4(gx[0], gy[0], gx[1], gy[1]);
+      reinterpret_cast<float4 *>(go)[1] = make_float4(gx[2], gy[2], gx[3], gy[3]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (l0 + k < it.nlev) {
+          go[2 * k] = gx[k];
+          go[2 * k + 1] = gy[k];
+        }
+    }
+  } else {
+    const float *uv = static_cast<const float *>(it.in);
+    float ui[4], vi[4], r[4];
+    load_vector_f32<4>(uv + i * it.in_stride, l0, it.nlev, ui, vi);
+    if (i < it.cap_begin) {
+      const float2 *w = static_cast<const float2 *>(it.w32);
+      const float2 sw = __ldg(static_cast<const float2 *>(it.s32) + i);
+      KahanAcc acc[4];
+      PlainAcc pacc[4];
+      for (int32_t p = p0; p < p1; ++p) {
+        const int32_t j = __ldg(it.nbr + p);
+        const float2 wp = __ldg(w + p);
+        float uj[4], vj[4];
+        load_vector_f32<4>(uv + (int64_t)j * it.in_stride, l0, it.nlev, uj, vj);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float du = __fsub_rn(uj[k], ui[k]), dv = __fsub_rn(vj[k], vi[k]);
+          const float term = __fmaf_rn(wp.x, du, __fmul_rn(wp.y, dv));
+          if (comp) acc[k].add(term);
+          else pacc[k].add(term);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float self = __fmaf_rn(sw.x, ui[k], __fmul_rn(sw.y, vi[k]));
+        if (comp) {
+          acc[k].add(self);
+          r[k] = acc[k].value();
+        } else {
+          pacc[k].add(self);
+          r[k] = pacc[k].value();
+        }
+      }
+    } else {
+      const double2 *w = static_cast<const double2 *>(it.w64);
+      const double2 sw = __ldg(static_cast<const double2 *>(it.s64) + i);
+      double sacc[4] = {0, 0, 0, 0};
+      for (int32_t p = p0; p < p1; ++p) {
+        const int32_t j = __ldg(it.nbr + p);
+        const double2 wp = __ldg(w + p);
+        float uj[4], vj[4];
+        load_vector_f32<4>(uv + (int64_t)j * it.in_stride, l0, it.nlev, uj, vj);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          sacc[k] = fma(wp.x, (double)uj[k] - (double)ui[k], sacc[k]);
+          sacc[k] = fma(wp.y, (double)vj[k] - (double)vi[k], sacc[k]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        sacc[k] = fma(sw.x, (double)ui[k], sacc[k]);
+        sacc[k] = fma(sw.y, (double)vi[k], sacc[k]);
+        r[k] = (float)sacc[k];
+      }
+    }
+    float *oo = static_cast<float *>(it.out) + i * it.out_stride + l0;
+    if (l0 + 4 <= it.nlev) {
+      *reinterpret_cast<float4 *>(oo) = make_float4(r[0], r[1], r[2], r[3]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (l0 + k < it.nlev) oo[k] = r[k];
+    }
+  }
+}
+
 __device__ __forceinline__ void unit_point_f64(const BItem &it, int64_t i, int l) {
   const int32_t p0 = __ldg(it.row_ptr + i), p1 = __ldg(it.row_ptr + i + 1);
   const double2 *w = static_cast<const double2 *>(it.w64);
@@ -211,9 +344,13 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BItem *__res
     for (int r = 0; r < it.rounds; ++r) {
       const int64_t i = n_begin + ((int64_t)r * kBatchWarps + warp) * npw + lane / sub;
       if (i >= it.V) continue;
-      for (int l = l0 + lane % sub; l < l1; l += sub) {
-        if (it.f64) unit_point_f64(it, i, l);
-        else unit_point_f32(it, i, l, comp != 0);
+      if (it.vec) {
+        for (int l = l0 + 4 * (lane % sub); l < l1; l += 4 * sub) unit_group4_f32(it, i, l, comp != 0);
+      } else {
+        for (int l = l0 + lane % sub; l < l1; l += sub) {
+          if (it.f64) unit_point_f64(it, i, l);
+          else unit_point_f32(it, i, l, comp != 0);
+        }
       }
     }
   }
@@ -320,12 +457,15 @@ static BItem make_item(const nb_method *m, int op, const nb_field &in, const nb_
   BItem b{};
   b.op = op;
   b.f64 = in.dtype == NB_F64;
+  b.vec = !b.f64 && in.nlev >= 4 && ((((uintptr_t)in.data) | ((uintptr_t)out.data)) & 15u) == 0 &&
+          in.node_stride % 4 == 0 && out.node_stride % 4 == 0;
   b.nlev = in.nlev;
   b.lpb = std::max(1, std::min(shp.first, in.nlev));
+  if (b.vec) b.lpb = (b.lpb + 3) / 4 * 4;  // level chunks start on 4-level groups
   b.npw = shp.second;
   const int sub = 32 / b.npw;
   // rounds: about 2048 point evaluations per unit
-  const int per_round = b.npw * kBatchWarps * std::min(b.lpb, sub);
+  const int per_round = b.npw * kBatchWarps * std::min(b.lpb, b.vec ? 4 * sub : sub);
   b.rounds = std::max(1, 2048 / std::max(1, per_round));
   b.nchunk_lev = (in.nlev + b.lpb - 1) / b.lpb;
   b.V = m->mesh->V;

@@ -181,49 +181,6 @@ struct DirectArgs {
   int64_t out_stride;
 };
 
-// Load LPT consecutive values of a scalar column starting at level l0;
-// values at levels >= nlev are returned as 0 and never read past the row.
-template <int LPT>
-__device__ __forceinline__ void load_scalar_f32(const float *col, int l0, int nlev, float (&v)[LPT]) {
-  if constexpr (LPT == 4) {
-    if (l0 < nlev) {
-      const float4 x = __ldg(reinterpret_cast<const float4 *>(col + l0));
-      v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
-    } else {
-      v[0] = v[1] = v[2] = v[3] = 0.f;
-    }
-  } else {
-#pragma unroll
-    for (int k = 0; k < LPT; ++k) v[k] = (l0 + k < nlev) ? __ldg(col + l0 + k) : 0.f;
-  }
-}
-// Load LPT levels of a (u, v) column.
-template <int LPT>
-__device__ __forceinline__ void load_vector_f32(const float *col, int l0, int nlev, float (&u)[LPT],
-                                                float (&v)[LPT]) {
-  if constexpr (LPT == 4) {
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      if (l0 + 2 * h < nlev) {
-        const float4 x = __ldg(reinterpret_cast<const float4 *>(col + 2 * (l0 + 2 * h)));
-        u[2 * h] = x.x; v[2 * h] = x.y; u[2 * h + 1] = x.z; v[2 * h + 1] = x.w;
-      } else {
-        u[2 * h] = v[2 * h] = u[2 * h + 1] = v[2 * h + 1] = 0.f;
-      }
-    }
-  } else {
-#pragma unroll
-    for (int k = 0; k < LPT; ++k) {
-      if (l0 + k < nlev) {
-        u[k] = __ldg(col + 2 * (l0 + k));
-        v[k] = __ldg(col + 2 * (l0 + k) + 1);
-      } else {
-        u[k] = v[k] = 0.f;
-      }
-    }
-  }
-}
-
 // op 0: grad.  FP32 arithmetic, compensated or plain accumulation.
 template <int LPT, class Acc>
 __global__ void __launch_bounds__(256) grad_direct_f32(DirectArgs a) {

@@ -6,7 +6,7 @@
 // takes stream-ordered memory for the request's fields from the CUDA memory
 // pool, synthesises the input fields on the device from the grid's resident
 // spherical-harmonic bases (per-level mixing weights drawn from the request
-// seed with SplitMix64), launches the operator on one of several streams and
+// seed with SplitMix64, mixed in FP32), launches the operator on one of several streams and
 // records a completion event.  Finished requests (event polled) release their
 // memory and budget immediately, so requests that arrive while others are on
 // the GPU are admitted as memory frees up and their work overlaps on the
@@ -50,20 +50,29 @@ __device__ __forceinline__ double mix_weight(uint64_t seed, int f, int k, int b,
   return (2.0 * u - 1.0) * (1.0 + (double)k / nlev);
 }
 
-// in[node][k][c] = sum_b w(f, k, b) basis[node][b][c]  (c < nvar)
+// in[node][k][c] = sum_b w(f, k, b) basis[node][b][c]  (c < nvar), in FP32
+// arithmetic from an FP32 copy of the basis (these are request inputs, not
+// operator arithmetic).  Each block draws the field's nlev x 8 weights once
+// into shared memory; one thread per (node, level).
 template <class T>
-__global__ void __launch_bounds__(256) synth_fields_kernel(const double *__restrict__ basis, int nvar,
+__global__ void __launch_bounds__(256) synth_fields_kernel(const float *__restrict__ basis, int nvar,
                                                            int64_t V, int nlev, int64_t stride,
                                                            uint64_t seed, int f, T *out) {
+  extern __shared__ float s_w[];  // [nlev][8]
+  for (int t = threadIdx.x; t < nlev * 8; t += blockDim.x)
+    s_w[t] = (float)mix_weight(seed, f, t >> 3, t & 7, nlev);
+  __syncthreads();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= V * nlev) return;
   const int64_t i = idx / nlev;
   const int k = (int)(idx - i * nlev);
-  double acc0 = 0, acc1 = 0;
+  const float *w = s_w + 8 * k;
+  const float *bi = basis + i * 8 * nvar;
+  float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll
   for (int b = 0; b < 8; ++b) {
-    const double w = mix_weight(seed, f, k, b, nlev);
-    acc0 = fma(w, basis[(i * 8 + b) * nvar], acc0);
-    if (nvar == 2) acc1 = fma(w, basis[(i * 8 + b) * 2 + 1], acc1);
+    acc0 = __fmaf_rn(w[b], bi[b * nvar], acc0);
+    if (nvar == 2) acc1 = __fmaf_rn(w[b], bi[b * 2 + 1], acc1);
   }
   T *o = out + i * stride + (int64_t)k * nvar;
   o[0] = (T)acc0;
@@ -72,8 +81,8 @@ __global__ void __launch_bounds__(256) synth_fields_kernel(const double *__restr
 
 struct SrvGrid {
   nb_method *method = nullptr;
-  double *d_scalar = nullptr;  // [V][8]
-  double *d_wind = nullptr;    // [V][8][2]
+  float *d_scalar = nullptr;  // [V][8]
+  float *d_wind = nullptr;    // [V][8][2]
 };
 
 struct SrvReq {
@@ -86,6 +95,7 @@ struct SrvReq {
   cudaEvent_t ev = nullptr;
   std::vector<void *> bufs;
   std::vector<char> host_out;  // kept outputs (tests)
+  std::vector<char> host_in;   // kept inputs (keep_output == 2)
 };
 
 }  // namespace nb
@@ -148,15 +158,16 @@ static int launch_request(nb_server *s, SrvReq *q) {
       NB_CUDA(cudaMallocAsync(&dscr, (size_t)(V * lp * 2 * elem), st));
       q->bufs.push_back(dscr);
     }
-    const double *basis = in_var == 2 ? g.d_wind : g.d_scalar;
+    const float *basis = in_var == 2 ? g.d_wind : g.d_scalar;
     const int64_t pts = V * r.nlev;
     const unsigned blocks = (unsigned)((pts + 255) / 256);
+    const size_t wsm = (size_t)r.nlev * 8 * sizeof(float);
     if (r.dtype == NB_F64)
-      synth_fields_kernel<double><<<blocks, 256, 0, st>>>(basis, in_var, V, r.nlev, lp * in_var, r.seed,
-                                                          f, static_cast<double *>(din));
+      synth_fields_kernel<double><<<blocks, 256, wsm, st>>>(basis, in_var, V, r.nlev, lp * in_var,
+                                                            r.seed, f, static_cast<double *>(din));
     else
-      synth_fields_kernel<float><<<blocks, 256, 0, st>>>(basis, in_var, V, r.nlev, lp * in_var, r.seed, f,
-                                                         static_cast<float *>(din));
+      synth_fields_kernel<float><<<blocks, 256, wsm, st>>>(basis, in_var, V, r.nlev, lp * in_var, r.seed,
+                                                           f, static_cast<float *>(din));
     count_launch(1);
     NB_CUDA(cudaGetLastError());
     nb_field fi{din, r.dtype, in_var, V, r.nlev, 0, lp * in_var, in_var};
@@ -184,6 +195,13 @@ static void finish_request(nb_server *s, SrvReq *q) {
     q->host_out.resize((size_t)(one * q->r.nfields));
     for (int f = 0; f < q->r.nfields; ++f)
       cudaMemcpy(q->host_out.data() + f * one, q->bufs[f * per + 1], (size_t)one, cudaMemcpyDeviceToHost);
+    if (q->r.keep_output == 2) {
+      const int in_var = (q->r.op == NB_OP_DIV || q->r.op == NB_OP_CURL) ? 2 : 1;
+      const int64_t ione = V * lp * in_var * elem;
+      q->host_in.resize((size_t)(ione * q->r.nfields));
+      for (int f = 0; f < q->r.nfields; ++f)
+        cudaMemcpy(q->host_in.data() + f * ione, q->bufs[f * per], (size_t)ione, cudaMemcpyDeviceToHost);
+    }
   }
   for (void *p : q->bufs) cudaFreeAsync(p, st);
   q->bufs.clear();
@@ -325,10 +343,13 @@ int nb_server_add_grid(nb_server *s, const nb_method *m, const double *scalar_ba
   const int64_t V = m->mesh->V;
   nb::SrvGrid g;
   g.method = nb::retain(const_cast<nb_method *>(m));
-  if (cudaMalloc(&g.d_scalar, (size_t)(V * 8 * 8)) != cudaSuccess ||
-      cudaMalloc(&g.d_wind, (size_t)(V * 16 * 8)) != cudaSuccess ||
-      cudaMemcpy(g.d_scalar, scalar_basis, (size_t)(V * 8 * 8), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(g.d_wind, wind_basis, (size_t)(V * 16 * 8), cudaMemcpyHostToDevice) != cudaSuccess) {
+  std::vector<float> sb((size_t)(V * 8)), wb((size_t)(V * 16));
+  for (size_t k = 0; k < sb.size(); ++k) sb[k] = (float)scalar_basis[k];
+  for (size_t k = 0; k < wb.size(); ++k) wb[k] = (float)wind_basis[k];
+  if (cudaMalloc(&g.d_scalar, sb.size() * 4) != cudaSuccess ||
+      cudaMalloc(&g.d_wind, wb.size() * 4) != cudaSuccess ||
+      cudaMemcpy(g.d_scalar, sb.data(), sb.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(g.d_wind, wb.data(), wb.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
     if (g.d_scalar) cudaFree(g.d_scalar);
     if (g.d_wind) cudaFree(g.d_wind);
     nb::release(g.method);
@@ -427,6 +448,25 @@ int nb_server_output(nb_server *s, uint64_t ticket, void *host_out, int64_t byte
     return NB_ESHAPE;
   }
   std::memcpy(host_out, it->second->host_out.data(), (size_t)bytes);
+  return NB_OK;
+}
+
+int nb_server_input(nb_server *s, uint64_t ticket, void *host_in, int64_t bytes) {
+  if (!s || !host_in) {
+    nb::set_error("nb_server_input: NULL argument");
+    return NB_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->all.find(ticket);
+  if (it == s->all.end() || it->second->done < 0 || it->second->r.keep_output != 2) {
+    nb::set_error("nb_server_input: unknown, unfinished or inputs not kept");
+    return NB_EINVAL;
+  }
+  if ((int64_t)it->second->host_in.size() != bytes) {
+    nb::set_error("nb_server_input: size mismatch");
+    return NB_ESHAPE;
+  }
+  std::memcpy(host_in, it->second->host_in.data(), (size_t)bytes);
   return NB_OK;
 }
 

@@ -119,6 +119,7 @@ SIGNATURES = {
     "nb_server_submit": [_P, ctypes.POINTER(nb_request), ctypes.POINTER(ctypes.c_uint64)],
     "nb_server_wait": [_P, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(nb_result)],
     "nb_server_output": [_P, ctypes.c_uint64, _P, ctypes.c_int64],
+    "nb_server_input": [_P, ctypes.c_uint64, _P, ctypes.c_int64],
     "nb_server_stats": [_P, _I64P, _I64P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)],
     "nb_server_run_trace": [_P, ctypes.POINTER(nb_request), _P, _I, ctypes.POINTER(nb_result)],
 }
@@ -422,11 +423,11 @@ class Server(_Handle):
         self.grids[method.mesh.grid.N] = method
 
     @staticmethod
-    def request(op, N, nlev, nfields=1, dtype=NB_F32, seed=0, keep_output=False):
+    def request(op, N, nlev, nfields=1, dtype=NB_F32, seed=0, keep_output=False, keep_input=False):
         r = nb_request()
         r.op = OPS[op] if isinstance(op, str) else int(op)
         r.N, r.nlev, r.nfields, r.dtype = int(N), int(nlev), int(nfields), int(dtype)
-        r.keep_output = 1 if keep_output else 0
+        r.keep_output = 2 if keep_input else (1 if keep_output else 0)
         r.seed = int(seed)
         return r
 
@@ -449,6 +450,16 @@ class Server(_Handle):
         out = np.zeros((req.nfields, meth.mesh.V, lp, nvar), dtype=dt)
         check(lib().nb_server_output(self._h, ticket, out.ctypes.data, out.nbytes))
         return out[:, :, :req.nlev, :] if nvar == 2 else out[:, :, :req.nlev, 0]
+
+    def input(self, ticket: int, req) -> np.ndarray:
+        meth = self.grids[req.N]
+        q = 2 if req.dtype == NB_F64 else 4
+        lp = (req.nlev + q - 1) // q * q
+        nvar = 2 if req.op in (OP_DIV, OP_CURL) else 1
+        dt = np.float64 if req.dtype == NB_F64 else np.float32
+        x = np.zeros((req.nfields, meth.mesh.V, lp, nvar), dtype=dt)
+        check(lib().nb_server_input(self._h, ticket, x.ctypes.data, x.nbytes))
+        return x[:, :, :req.nlev, :] if nvar == 2 else x[:, :, :req.nlev, 0]
 
     def stats(self):
         u, p = ctypes.c_int64(), ctypes.c_int64()

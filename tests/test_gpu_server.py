@@ -70,22 +70,33 @@ def test_result_is_the_same_alone_and_in_the_mix(server):
 
 @pytest.mark.parametrize("op", ["grad", "div", "curl", "lap"])
 def test_served_result_meets_the_oracle_gate(server, op):
+    """The server's own inputs (kept) through the oracle vs its outputs."""
     N, nlev, seed = 24, 5, 77
-    req = nabla.Server.request(op, N, nlev, nfields=2, seed=seed, keep_output=True)
-    out = server.output(server.wait(server.submit(req)).ticket, req)
-    meth, sb, wb = _bases(N)
+    req = nabla.Server.request(op, N, nlev, nfields=2, seed=seed, keep_input=True)
+    t = server.wait(server.submit(req)).ticket
+    out, xin = server.output(t, req), server.input(t, req)
     perm = product(N)[1].permutation()
     om = oracle_mesh(N)
     for f in range(2):
-        w = _weights(seed, f, nlev)
-        x = (sb @ w.T) if op in ("grad", "lap") else np.einsum("vbc,kb->vkc", wb, w)
-        x = x.astype(np.float32).astype(np.float64)
-        xg = np.empty_like(x)
-        xg[perm] = x
+        xg = np.empty(xin[f].shape)
+        xg[perm] = xin[f]
         ref = {"grad": oracle.grad, "div": oracle.div, "curl": oracle.curl, "lap": oracle.lap}[op](om, xg)
         got = np.empty(out[f].shape)
         got[perm] = out[f]
         assert rel_l2(got, ref) <= 1e-5, (op, f, rel_l2(got, ref))
+
+
+def test_served_inputs_follow_the_documented_recipe(server):
+    """Inputs are per-level SplitMix64 mixtures of the registered bases."""
+    N, nlev, seed = 16, 3, 5
+    req = nabla.Server.request("grad", N, nlev, nfields=2, seed=seed, keep_input=True)
+    t = server.wait(server.submit(req)).ticket
+    xin = server.input(t, req)
+    meth, sb, wb = _bases(N)
+    for f in range(2):
+        w = _weights(seed, f, nlev).astype(np.float32).astype(np.float64)
+        x = sb.astype(np.float32).astype(np.float64) @ w.T
+        assert np.allclose(xin[f], x, rtol=1e-5, atol=1e-5 * np.abs(x).max())
 
 
 def test_admission_respects_the_budget_and_refuses_oversize():
