@@ -479,17 +479,15 @@ void build_geometry(const nb_mesh *m, double R, std::vector<double> &vol, std::v
 
 // ------------------------------------------------------------- tile plans
 
-// Variable-size tiles of consecutive nodes for the shared-memory staged
-// kernels.  Tiles are grown greedily along the node order while the tile's
-// own nodes plus its halo (neighbours outside the tile) fit `rcap` staged
-// rows, the tile has at most `nmax` nodes and at most `ecap` CSR entries.  Main tiles cover
-// [0, cap_begin), pole tiles [cap_begin, V).  halo[t] lists the sorted halo
-// nodes of tile t; lnbr[p] is the staged row of CSR neighbour p (0..n-1 the
-// tile's own nodes, n + k halo entry k).
-void build_tile_plan_host(const nb_mesh *m, int rcap, int nmax, int ecap, std::vector<int32_t> &node0,
-                          std::vector<int32_t> &halo_ptr, std::vector<int32_t> &halo,
-                          std::vector<uint16_t> &lnbr, int &max_halo, int &max_entries,
-                          int &ntiles_main) {
+// Tiles of consecutive nodes for the shared-memory staged kernels, grown
+// greedily along the node order while fits(n, H) holds for the tile's n own
+// nodes and H halo nodes (neighbours outside it), with at most nmax nodes and
+// ecap CSR entries.  Main tiles cover [0, cap_begin), pole tiles
+// [cap_begin, V).  halo[t] lists the sorted halo nodes of tile t.
+template <class Fits>
+static void plan_tiles(const nb_mesh *m, Fits fits, int nmax, int ecap, std::vector<int32_t> &node0,
+                       std::vector<int32_t> &halo_ptr, std::vector<int32_t> &halo, int &max_halo,
+                       int &max_entries, int &ntiles_main) {
   const int64_t V = m->V;
   std::vector<int32_t> mark(V, -1);
   node0.clear();
@@ -509,7 +507,7 @@ void build_tile_plan_host(const nb_mesh *m, int rcap, int nmax, int ecap, std::v
         }
         const int64_t inhalo = (mark[v] == stamp) ? 1 : 0;
         const int64_t newH = H + add - inhalo;
-        if (n1 > n0 && (n1 - n0 + 1) + newH > rcap) break;
+        if (n1 > n0 && !fits(n1 - n0 + 1, newH)) break;
         for (int64_t p = m->row_ptr[v]; p < m->row_ptr[v + 1]; ++p) {
           const int32_t j = m->nbr[p];
           if (j < n0 || j > v) mark[j] = stamp;
@@ -528,7 +526,6 @@ void build_tile_plan_host(const nb_mesh *m, int rcap, int nmax, int ecap, std::v
   node0.push_back((int32_t)V);
   const int nt = (int)node0.size() - 1;
   std::vector<std::vector<int32_t>> hal(nt);
-  lnbr.assign(m->row_ptr[V], 0);
   std::vector<int> hmax(nt, 0), emax(nt, 0);
 #pragma omp parallel for schedule(dynamic, 64)
   for (int t = 0; t < nt; ++t) {
@@ -540,13 +537,6 @@ void build_tile_plan_host(const nb_mesh *m, int rcap, int nmax, int ecap, std::v
     }
     std::sort(h.begin(), h.end());
     h.erase(std::unique(h.begin(), h.end()), h.end());
-    for (int64_t p = m->row_ptr[a]; p < m->row_ptr[b]; ++p) {
-      const int32_t j = m->nbr[p];
-      int loc;
-      if (j >= a && j < b) loc = j - a;
-      else loc = (b - a) + (int)(std::lower_bound(h.begin(), h.end(), j) - h.begin());
-      lnbr[p] = (uint16_t)loc;
-    }
     hmax[t] = (int)h.size();
     emax[t] = (int)(m->row_ptr[b] - m->row_ptr[a]);
   }
@@ -560,6 +550,58 @@ void build_tile_plan_host(const nb_mesh *m, int rcap, int nmax, int ecap, std::v
   }
   halo.resize(halo_ptr[nt]);
   for (int t = 0; t < nt; ++t) std::copy(hal[t].begin(), hal[t].end(), halo.begin() + halo_ptr[t]);
+}
+
+// Position of CSR neighbour p of a node of tile t among the staged columns:
+// k < n for the tile's own node k, n + h for halo node h.
+template <class Out>
+static void staged_index(const nb_mesh *m, const std::vector<int32_t> &node0,
+                         const std::vector<int32_t> &halo_ptr, const std::vector<int32_t> &halo,
+                         Out out) {
+  const int nt = (int)node0.size() - 1;
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int t = 0; t < nt; ++t) {
+    const int32_t a = node0[t], b = node0[t + 1];
+    const int32_t *h0 = halo.data() + halo_ptr[t], *h1 = halo.data() + halo_ptr[t + 1];
+    for (int64_t p = m->row_ptr[a]; p < m->row_ptr[b]; ++p) {
+      const int32_t j = m->nbr[p];
+      const int64_t k = (j >= a && j < b) ? (j - a) : (b - a) + (std::lower_bound(h0, h1, j) - h0);
+      out(p, t, (int64_t)(b - a), k);
+    }
+  }
+}
+
+// Plan with a staged-row capacity: own nodes + halo nodes <= rcap; lnbr[p]
+// is the staged row of CSR neighbour p.
+void build_tile_plan_host(const nb_mesh *m, int rcap, int nmax, int ecap, std::vector<int32_t> &node0,
+                          std::vector<int32_t> &halo_ptr, std::vector<int32_t> &halo,
+                          std::vector<uint16_t> &lnbr, int &max_halo, int &max_entries,
+                          int &ntiles_main) {
+  plan_tiles(m, [&](int64_t n, int64_t H) { return n + H <= rcap; }, nmax, ecap, node0, halo_ptr, halo,
+             max_halo, max_entries, ntiles_main);
+  lnbr.assign(m->row_ptr[m->V], 0);
+  staged_index(m, node0, halo_ptr, halo,
+               [&](int64_t p, int, int64_t, int64_t k) { lnbr[p] = (uint16_t)k; });
+}
+
+// Plan in bytes for the gather-staged layout: the tile's own columns at
+// `row_bytes` pitch from offset 0, then halo columns in groups of four at
+// `copy_bytes` pitch, each group starting on a 128-byte boundary
+// (group pitch = 4 copy_bytes rounded up to 128).  Tiles grow while the
+// layout fits `area` bytes; loff[p] is the byte offset of CSR neighbour p.
+void build_tile_plan_bytes(const nb_mesh *m, int64_t area, int64_t row_bytes, int64_t copy_bytes,
+                           int nmax, int ecap, std::vector<int32_t> &node0,
+                           std::vector<int32_t> &halo_ptr, std::vector<int32_t> &halo,
+                           std::vector<uint32_t> &loff, int &max_halo, int &max_entries,
+                           int &ntiles_main) {
+  const int64_t gpitch = (4 * copy_bytes + 127) / 128 * 128;
+  auto hbase = [&](int64_t n) { return (n * row_bytes + 127) / 128 * 128; };
+  plan_tiles(m, [&](int64_t n, int64_t H) { return hbase(n) + (H + 3) / 4 * gpitch <= area; }, nmax,
+             ecap, node0, halo_ptr, halo, max_halo, max_entries, ntiles_main);
+  loff.assign(m->row_ptr[m->V], 0);
+  staged_index(m, node0, halo_ptr, halo, [&](int64_t p, int, int64_t n, int64_t k) {
+    loff[p] = (uint32_t)(k < n ? k * row_bytes : hbase(n) + ((k - n) >> 2) * gpitch + ((k - n) & 3) * copy_bytes);
+  });
 }
 
 }  // namespace nb

@@ -64,11 +64,13 @@ struct nb_mesh : nb::RefCounted {
   ~nb_mesh() override { nb::release(grid); }
 };
 
-// Per-tile halo plan of the staged kernels for one staged-row capacity.
+// Per-tile halo plan of the staged kernels for one stage layout.
 struct TilePlan {
-  int rcap = 0;        // staged rows per tile (own nodes + halo)
-  int nmax = 0;        // nodes per tile at most
-  int ecap = 0;        // CSR entries per tile at most
+  int64_t area = 0;      // stage bytes for columns
+  int64_t row_bytes = 0; // column pitch of the tile's own nodes
+  int64_t copy_bytes = 0;// bytes copied per column (halo pitch)
+  int nmax = 0;          // nodes per tile at most
+  int ecap = 0;          // CSR entries per tile at most
   int ntiles = 0;
   int ntiles_main = 0;               // tiles before the pole block
   int max_halo = 0;
@@ -77,10 +79,7 @@ struct TilePlan {
   int32_t *d_tile_node0 = nullptr;   // ntiles+1: tile t = [node0[t], node0[t+1])
   int32_t *d_halo_ptr = nullptr;     // ntiles+1
   int32_t *d_halo = nullptr;         // halo node ids
-  uint16_t *d_lnbr = nullptr;        // 2E: shared-memory row of each CSR neighbour
-  uint16_t *d_hrun = nullptr;        // per halo entry: length of the run of consecutive
-                                     // node ids starting there (0 inside a run)
-  int32_t *d_nruns = nullptr;        // runs per tile
+  uint32_t *d_loff = nullptr;        // 2E (+4): stage byte offset of each CSR neighbour
 };
 
 // fvm::Method: geometry and operator weights resident on one device.
@@ -111,7 +110,7 @@ struct nb_method : nb::RefCounted {
   int stage_kb = 0;     // staged kernels: KB per stage (0 = default)
   int compensated = 1;
   std::mutex plan_mu;
-  std::map<std::tuple<int, int, int>, std::unique_ptr<TilePlan>> plans;  // (rcap, nmax, ecap)
+  std::map<std::tuple<int64_t, int64_t, int64_t, int, int>, std::unique_ptr<TilePlan>> plans;
   ~nb_method() override;
 };
 
@@ -135,6 +134,12 @@ void build_tile_plan_host(const nb_mesh *m, int rcap, int nmax, int ecap, std::v
                           std::vector<int32_t> &halo_ptr, std::vector<int32_t> &halo,
                           std::vector<uint16_t> &lnbr, int &max_halo, int &max_entries,
                           int &ntiles_main);
+
+void build_tile_plan_bytes(const nb_mesh *m, int64_t area, int64_t row_bytes, int64_t copy_bytes,
+                           int nmax, int ecap, std::vector<int32_t> &node0,
+                           std::vector<int32_t> &halo_ptr, std::vector<int32_t> &halo,
+                           std::vector<uint32_t> &loff, int &max_halo, int &max_entries,
+                           int &ntiles_main);
 
 // device side (nabla_kernels.cu)
 int method_upload(nb_method *m);            // returns NB_* status

@@ -149,7 +149,7 @@ void method_free_device(nb_method *m) {
     if (p) cudaFree(p);
   for (auto &kv : m->plans) {
     TilePlan *tp = kv.second.get();
-    void *q[] = {tp->d_tile_node0, tp->d_halo_ptr, tp->d_halo, tp->d_lnbr, tp->d_hrun, tp->d_nruns};
+    void *q[] = {tp->d_tile_node0, tp->d_halo_ptr, tp->d_halo, tp->d_loff};
     for (void *p : q)
       if (p) cudaFree(p);
   }

@@ -50,23 +50,29 @@ __device__ __forceinline__ double mix_weight(uint64_t seed, int f, int k, int b,
   return (2.0 * u - 1.0) * (1.0 + (double)k / nlev);
 }
 
-// in[node][k][c] = sum_b w(f, k, b) basis[node][b][c]  (c < nvar), in FP32
+// Mixing weights of all fields of a request: w[f][k][b], drawn once.
+__global__ void __launch_bounds__(256) synth_weights_kernel(uint64_t seed, int nfields, int nlev,
+                                                            float *w) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nfields * nlev * 8) return;
+  const int f = t / (nlev * 8), r = t - f * nlev * 8;
+  w[t] = (float)mix_weight(seed, f, r >> 3, r & 7, nlev);
+}
+
+// in[node][k][c] = sum_b w[f][k][b] basis[node][b][c]  (c < nvar), in FP32
 // arithmetic from an FP32 copy of the basis (these are request inputs, not
-// operator arithmetic).  Each block draws the field's nlev x 8 weights once
-// into shared memory; one thread per (node, level).
+// operator arithmetic); one thread per (node, level).
 template <class T>
 __global__ void __launch_bounds__(256) synth_fields_kernel(const float *__restrict__ basis, int nvar,
                                                            int64_t V, int nlev, int64_t stride,
-                                                           uint64_t seed, int f, T *out) {
-  extern __shared__ float s_w[];  // [nlev][8]
-  for (int t = threadIdx.x; t < nlev * 8; t += blockDim.x)
-    s_w[t] = (float)mix_weight(seed, f, t >> 3, t & 7, nlev);
-  __syncthreads();
+                                                           const float *__restrict__ wts, T *out) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= V * nlev) return;
   const int64_t i = idx / nlev;
   const int k = (int)(idx - i * nlev);
-  const float *w = s_w + 8 * k;
+  const float4 w0 = __ldg(reinterpret_cast<const float4 *>(wts + 8 * k));
+  const float4 w1 = __ldg(reinterpret_cast<const float4 *>(wts + 8 * k) + 1);
+  const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
   const float *bi = basis + i * 8 * nvar;
   float acc0 = 0.f, acc1 = 0.f;
 #pragma unroll
@@ -94,6 +100,7 @@ struct SrvReq {
   int stream = -1;
   cudaEvent_t ev = nullptr;
   std::vector<void *> bufs;
+  void *wts = nullptr;         // mixing weights of the request's fields
   std::vector<char> host_out;  // kept outputs (tests)
   std::vector<char> host_in;   // kept inputs (keep_output == 2)
 };
@@ -148,6 +155,13 @@ static int launch_request(nb_server *s, SrvReq *q) {
   const int64_t lp = (int64_t)((r.nlev + qq - 1) / qq) * qq;
   const int in_var = (r.op == NB_OP_DIV || r.op == NB_OP_CURL) ? 2 : 1;
   const int out_var = r.op == NB_OP_GRAD ? 2 : 1;
+  float *wts = nullptr;
+  const int nw = r.nfields * r.nlev * 8;
+  NB_CUDA(cudaMallocAsync((void **)&wts, (size_t)nw * sizeof(float), st));
+  q->wts = wts;
+  synth_weights_kernel<<<(nw + 255) / 256, 256, 0, st>>>(r.seed, r.nfields, r.nlev, wts);
+  count_launch(1);
+  NB_CUDA(cudaGetLastError());
   for (int f = 0; f < r.nfields; ++f) {
     void *din = nullptr, *dout = nullptr, *dscr = nullptr;
     NB_CUDA(cudaMallocAsync(&din, (size_t)(V * lp * in_var * elem), st));
@@ -161,13 +175,13 @@ static int launch_request(nb_server *s, SrvReq *q) {
     const float *basis = in_var == 2 ? g.d_wind : g.d_scalar;
     const int64_t pts = V * r.nlev;
     const unsigned blocks = (unsigned)((pts + 255) / 256);
-    const size_t wsm = (size_t)r.nlev * 8 * sizeof(float);
+    const float *wf = wts + (size_t)f * r.nlev * 8;
     if (r.dtype == NB_F64)
-      synth_fields_kernel<double><<<blocks, 256, wsm, st>>>(basis, in_var, V, r.nlev, lp * in_var,
-                                                            r.seed, f, static_cast<double *>(din));
+      synth_fields_kernel<double><<<blocks, 256, 0, st>>>(basis, in_var, V, r.nlev, lp * in_var, wf,
+                                                          static_cast<double *>(din));
     else
-      synth_fields_kernel<float><<<blocks, 256, wsm, st>>>(basis, in_var, V, r.nlev, lp * in_var, r.seed,
-                                                           f, static_cast<float *>(din));
+      synth_fields_kernel<float><<<blocks, 256, 0, st>>>(basis, in_var, V, r.nlev, lp * in_var, wf,
+                                                         static_cast<float *>(din));
     count_launch(1);
     NB_CUDA(cudaGetLastError());
     nb_field fi{din, r.dtype, in_var, V, r.nlev, 0, lp * in_var, in_var};
@@ -205,6 +219,8 @@ static void finish_request(nb_server *s, SrvReq *q) {
   }
   for (void *p : q->bufs) cudaFreeAsync(p, st);
   q->bufs.clear();
+  if (q->wts) cudaFreeAsync(q->wts, st);
+  q->wts = nullptr;
   if (q->ev) cudaEventDestroy(q->ev);
   q->ev = nullptr;
 }

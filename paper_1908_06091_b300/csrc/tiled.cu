@@ -1,18 +1,20 @@
 // tiled.cu -- shared-memory staged nabla kernels for sm_103a.
 //
 // A persistent grid walks the tiles of a TilePlan (consecutive Hilbert-
-// ordered nodes whose own columns plus halo columns fit one stage).  For
-// each tile one warp issues 1-D TMA bulk copies (cp.async.bulk) of the
-// tile's contiguous column block and of every halo column into a
-// shared-memory stage, completing on an mbarrier; two stages alternate, so
-// the copies of tile k+1 run under the arithmetic of tile k.  Threads then
-// take (node, 4-level group) items: the node's own column and its
-// neighbours' columns are read from shared memory with 16-byte loads, the
-// edge weights through L1, and the per-node gather is accumulated with
-// packed FP32x2 Kahan arithmetic.  Pole tiles (the first and last grid
-// rows) are evaluated in FP64.  Every mbarrier wait is bounded: on timeout
-// the kernel records NB_ETIMEOUT in a device status word, waits (bounded)
-// for its own copies and returns.
+// ordered nodes whose own columns plus halo columns fit one stage).  A
+// producer warp fills each stage with TMA copies completing on an mbarrier:
+// one bulk copy (cp.async.bulk) of the tile's contiguous column block, bulk
+// copies of the tile's CSR weights, staged offsets and row pointers, and the
+// halo columns four at a time with tile::gather4 tensor copies (the copy
+// engine's cost is per copy, so scattered halo columns are gathered in
+// fours).  Two stages alternate, so tile k+1 is copied while tile k is
+// computed.  Sixteen consumer warps take (node, 4-level group) items, read
+// the node's and its neighbours' columns from shared memory with 16-byte
+// loads and accumulate with packed FP32x2 compensated sums; pole tiles (the
+// first and last grid rows) run in FP64.  Every mbarrier wait is bounded:
+// on timeout the kernel records NB_ETIMEOUT in a device status word, waits
+// (bounded) for its own copies and returns.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -59,6 +61,16 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
       "l"(src), "r"(bytes), "r"(bar)
       : "memory");
 }
+// Four rows (y0..y3) of a 2-D tensor, one box row each, into consecutive
+// shared memory at `dst` (128-byte aligned).
+__device__ __forceinline__ void gather4_g2s(uint32_t dst, const CUtensorMap *map, int32_t y0, int32_t y1,
+                                           int32_t y2, int32_t y3, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(y0), "r"(y1), "r"(y2), "r"(y3), "r"(bar)
+      : "memory");
+}
 __device__ __forceinline__ uint64_t globaltimer() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -102,8 +114,12 @@ __device__ __forceinline__ f2_t sub2(f2_t a, f2_t b) {
 }
 
 // Kahan accumulation of two independent sums at once.  nc holds the
-// negated running correction, so each term w * d costs one fma2 and three
-// add/sub2: y = w*d + nc; t = s + y; nc = y - (t - s); s = t.
+// negated running correction.  One term w*d costs one fma2 and three
+// add/sub2: y = w*d + nc; t = s + y; nc = y - (t - s); s = t.  A pair of
+// edge terms is summed as one summand, y = w1*d1 + (w0*d0 + nc) by two
+// fma2, then compensated into s: 2.5 operations per term.  (Each product is
+// rounded once without compensation in either form; the compensation keeps
+// the running sum's rounding out of the result.)
 template <bool COMP>
 struct Kahan2 {
   f2_t s = 0ull, nc = 0ull;
@@ -117,6 +133,16 @@ struct Kahan2 {
       s = fma2(w, d, s);
     }
   }
+  __device__ __forceinline__ void add_pair(f2_t w0, f2_t d0, f2_t w1, f2_t d1) {
+    if (COMP) {
+      const f2_t y = fma2(w1, d1, fma2(w0, d0, nc));
+      const f2_t t = add2(s, y);
+      nc = sub2(y, sub2(t, s));
+      s = t;
+    } else {
+      s = fma2(w1, d1, fma2(w0, d0, s));
+    }
+  }
   __device__ __forceinline__ f2_t value() const { return COMP ? add2(s, nc) : s; }
 };
 
@@ -127,16 +153,14 @@ struct TiledArgs {
   const int32_t *tile_node0;
   const int32_t *halo_ptr;
   const int32_t *halo;
-  const uint16_t *hrun;
-  const int32_t *nruns;
-  const uint16_t *lnbr;
+  const uint32_t *loff;
   const int32_t *row_ptr;
   const float2 *w32;
   const double2 *w64;
   const float2 *s32;
   const double2 *s64;
   const char *in;
-  uint32_t row_bytes;  // bytes of one staged column (in_stride * 4)
+  uint32_t row_bytes;  // bytes of one own column (in_stride * 4)
   int64_t in_stride;   // elements
   float *out;
   int64_t out_stride;  // elements
@@ -145,47 +169,42 @@ struct TiledArgs {
   uint64_t g_magic;    // item / G == (item * g_magic) >> g_shift, exact for items < 2^24
   uint32_t g_shift;
   uint32_t copy_bytes; // bytes copied per column: the real data rounded up to 16
-  uint32_t off_w, off_l, off_r;  // stage offsets of the staged weights, rows, row pointers
+  uint32_t gpitch;     // shared-memory pitch of a group of four halo columns
+  uint32_t off_w, off_l, off_r;  // stage offsets of the staged weights, offsets, row pointers
   uint32_t stage_bytes;
   int nstages;
   int *status;
   uint64_t timeout_ns;
 };
 
-// Issue the copies of tile t into the stage at `stage` (one whole warp): the
-// tile's contiguous column block, its halo columns (one bulk copy per run of
-// consecutive node ids), and 16-byte aligned bounding ranges of the tile's
-// CSR weights, staged-row indices and row pointers, all as TMA bulk copies
-// completing on the stage's "full" barrier.  The copy engine's cost is per
-// copy rather than per byte, so copies are kept few and large.
-__device__ __forceinline__ void issue_tile(const TiledArgs &a, int t, uint32_t stage, uint32_t bar,
-                                           int lane) {
+// Issue the copies of tile t into the stage at `stage` (one whole warp).
+__device__ __forceinline__ void issue_tile(const TiledArgs &a, const CUtensorMap *map, int t,
+                                           uint32_t stage, uint32_t bar, int lane) {
   const int32_t n0 = __ldg(a.tile_node0 + t), n1 = __ldg(a.tile_node0 + t + 1);
   const int32_t h0 = __ldg(a.halo_ptr + t), h1 = __ldg(a.halo_ptr + t + 1);
   const int32_t pa = __ldg(a.row_ptr + n0), pb = __ldg(a.row_ptr + n1);
   const uint32_t n = (uint32_t)(n1 - n0), H = (uint32_t)(h1 - h0);
   const int32_t wa = pa & ~1, wb = (pb + 1) & ~1;
-  const int32_t la = pa & ~7, lb = (pb + 7) & ~7;
+  const int32_t la = pa & ~3, lb = (pb + 3) & ~3;
   const int32_t ra = n0 & ~3, rb = (n1 + 4) & ~3;
   const uint32_t body = (n - 1) * a.row_bytes + a.copy_bytes;
-  const uint32_t wbytes = (uint32_t)(wb - wa) * 8u, lbytes = (uint32_t)(lb - la) * 2u,
+  const uint32_t wbytes = (uint32_t)(wb - wa) * 8u, lbytes = (uint32_t)(lb - la) * 4u,
                  rbytes = (uint32_t)(rb - ra) * 4u;
-  // a run of L halo columns is one copy of (L - 1) full columns + one column
-  const uint32_t runs = (uint32_t)__ldg(a.nruns + t);
-  const uint32_t hbytes = H * a.copy_bytes + (H - runs) * (a.row_bytes - a.copy_bytes);
+  const uint32_t groups = (H + 3u) >> 2;
+  const uint32_t hbase = (n * a.row_bytes + 127u) & ~127u;
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  if (lane == 0) mbar_expect_tx(bar, body + hbytes + wbytes + lbytes + rbytes);
+  if (lane == 0) mbar_expect_tx(bar, body + wbytes + lbytes + rbytes + groups * 4u * a.copy_bytes);
   __syncwarp();
   if (lane == 0) bulk_g2s(stage, a.in + (int64_t)n0 * a.in_stride * 4, body, bar);
   if (lane == 1) bulk_g2s(stage + a.off_w, a.w32 + wa, wbytes, bar);
-  if (lane == 2) bulk_g2s(stage + a.off_l, a.lnbr + la, lbytes, bar);
+  if (lane == 2) bulk_g2s(stage + a.off_l, a.loff + la, lbytes, bar);
   if (lane == 3) bulk_g2s(stage + a.off_r, a.row_ptr + ra, rbytes, bar);
-  for (uint32_t h = lane; h < H; h += 32) {
-    const uint32_t L = __ldg(a.hrun + h0 + h);
-    if (L == 0) continue;
-    const int32_t node = __ldg(a.halo + h0 + h);
-    bulk_g2s(stage + (n + h) * a.row_bytes, a.in + (int64_t)node * a.in_stride * 4,
-             (L - 1) * a.row_bytes + a.copy_bytes, bar);
+  for (uint32_t g = lane; g < groups; g += 32) {
+    // a short last group repeats its last node (the copy fills the group's slots)
+    const int32_t *hp = a.halo + h0;
+    const uint32_t k = 4u * g, last = H - 1u;
+    gather4_g2s(stage + hbase + g * a.gpitch, map, __ldg(hp + k), __ldg(hp + min(k + 1u, last)),
+                __ldg(hp + min(k + 2u, last)), __ldg(hp + min(k + 3u, last)), bar);
   }
 }
 
@@ -203,9 +222,9 @@ __device__ __forceinline__ float2 lds64(uint32_t a) {
   asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
   return v;
 }
-__device__ __forceinline__ uint32_t lds_u16(uint32_t a) {
-  uint16_t v;
-  asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(a));
+__device__ __forceinline__ uint32_t lds_u32(uint32_t a) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
   return v;
 }
 __device__ __forceinline__ int32_t lds_s32(uint32_t a) {
@@ -215,7 +234,7 @@ __device__ __forceinline__ int32_t lds_s32(uint32_t a) {
 }
 
 // 32-bit shared addresses of one staged tile: entry p's weight is at
-// w + 8 p, its staged-row index at l + 2 p, node i's row pointer at r + 4 i
+// w + 8 p, its staged byte offset at l + 4 p, node i's row pointer at r + 4 i
 // (wrap-around arithmetic; the sums land inside the stage).
 struct TileView {
   int32_t n0, n1;
@@ -228,7 +247,7 @@ struct TileView {
     r = stage + a.off_r - 4u * (uint32_t)ra;
     const int32_t pa = lds_s32(r + 4u * (uint32_t)n0);
     w = stage + a.off_w - 8u * (uint32_t)(pa & ~1);
-    l = stage + a.off_l - 2u * (uint32_t)(pa & ~7);
+    l = stage + a.off_l - 4u * (uint32_t)(pa & ~3);
   }
 };
 
@@ -262,17 +281,23 @@ __device__ __forceinline__ void grad_tile(const TiledArgs &a, int t, uint32_t st
         ay01.add_prod(wy, d01);
         ay23.add_prod(wy, d23);
       };
-      uint32_t pw = v.w + 8u * (uint32_t)p0, pl = v.l + 2u * (uint32_t)p0;
+      uint32_t pw = v.w + 8u * (uint32_t)p0, pl = v.l + 4u * (uint32_t)p0;
       int32_t p = p0;
-      for (; p + 1 < p1; p += 2, pw += 16u, pl += 4u) {
+      for (; p + 1 < p1; p += 2, pw += 16u, pl += 8u) {
         const float2 w0 = lds64(pw), w1 = lds64(pw + 8u);
-        const uint32_t r0 = lds_u16(pl), r1 = lds_u16(pl + 2u);
-        const float4 f0 = lds128(col + r0 * rb);
-        const float4 f1 = lds128(col + r1 * rb);
-        body(w0, f0);
-        body(w1, f1);
+        const uint32_t r0 = lds_u32(pl), r1 = lds_u32(pl + 4u);
+        const float4 f0 = lds128(col + r0);
+        const float4 f1 = lds128(col + r1);
+        const f2_t a01 = sub2(pk(f0.x, f0.y), fi01), a23 = sub2(pk(f0.z, f0.w), fi23);
+        const f2_t b01 = sub2(pk(f1.x, f1.y), fi01), b23 = sub2(pk(f1.z, f1.w), fi23);
+        const f2_t wx0 = pk(w0.x, w0.x), wy0 = pk(w0.y, w0.y);
+        const f2_t wx1 = pk(w1.x, w1.x), wy1 = pk(w1.y, w1.y);
+        ax01.add_pair(wx0, a01, wx1, b01);
+        ax23.add_pair(wx0, a23, wx1, b23);
+        ay01.add_pair(wy0, a01, wy1, b01);
+        ay23.add_pair(wy0, a23, wy1, b23);
       }
-      if (p < p1) body(lds64(pw), lds128(col + lds_u16(pl) * rb));
+      if (p < p1) body(lds64(pw), lds128(col + lds_u32(pl)));
       upk(ax01.value(), gx[0], gx[1]);
       upk(ax23.value(), gx[2], gx[3]);
       upk(ay01.value(), gy[0], gy[1]);
@@ -282,7 +307,7 @@ __device__ __forceinline__ void grad_tile(const TiledArgs &a, int t, uint32_t st
       const float fiv[4] = {fi.x, fi.y, fi.z, fi.w};
       for (int32_t p = p0; p < p1; ++p) {
         const double2 w = __ldg(a.w64 + p);
-        const float4 fj = lds128(col + lds_u16(v.l + 2u * (uint32_t)p) * rb);
+        const float4 fj = lds128(col + lds_u32(v.l + 4u * (uint32_t)p));
         const float fjv[4] = {fj.x, fj.y, fj.z, fj.w};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -348,18 +373,21 @@ __device__ __forceinline__ void divcurl_tile(const TiledArgs &a, int t, uint32_t
         k2.add_prod(w2, sub2(pk(D.x, D.y), i2p));
         k3.add_prod(w2, sub2(pk(D.z, D.w), i3p));
       };
-      uint32_t pw = v.w + 8u * (uint32_t)p0, pl = v.l + 2u * (uint32_t)p0;
+      uint32_t pw = v.w + 8u * (uint32_t)p0, pl = v.l + 4u * (uint32_t)p0;
       int32_t p = p0;
-      for (; p + 1 < p1; p += 2, pw += 16u, pl += 4u) {
+      for (; p + 1 < p1; p += 2, pw += 16u, pl += 8u) {
         const float2 w0 = lds64(pw), w1 = lds64(pw + 8u);
-        const uint32_t r0 = lds_u16(pl) * rb, r1 = lds_u16(pl + 2u) * rb;
+        const uint32_t r0 = lds_u32(pl), r1 = lds_u32(pl + 4u);
         const float4 C0 = lds128(colA + r0), D0 = lds128(colB + r0);
         const float4 C1 = lds128(colA + r1), D1 = lds128(colB + r1);
-        body(w0, C0, D0);
-        body(w1, C1, D1);
+        const f2_t w20 = pk(w0.x, w0.y), w21 = pk(w1.x, w1.y);
+        k0.add_pair(w20, sub2(pk(C0.x, C0.y), i0p), w21, sub2(pk(C1.x, C1.y), i0p));
+        k1.add_pair(w20, sub2(pk(C0.z, C0.w), i1p), w21, sub2(pk(C1.z, C1.w), i1p));
+        k2.add_pair(w20, sub2(pk(D0.x, D0.y), i2p), w21, sub2(pk(D1.x, D1.y), i2p));
+        k3.add_pair(w20, sub2(pk(D0.z, D0.w), i3p), w21, sub2(pk(D1.z, D1.w), i3p));
       }
       if (p < p1) {
-        const uint32_t r0 = lds_u16(pl) * rb;
+        const uint32_t r0 = lds_u32(pl);
         body(lds64(pw), lds128(colA + r0), lds128(colB + r0));
       }
       const float2 sw = __ldg(a.s32 + node);
@@ -378,7 +406,7 @@ __device__ __forceinline__ void divcurl_tile(const TiledArgs &a, int t, uint32_t
       double sacc[4] = {0, 0, 0, 0};
       for (int32_t p = p0; p < p1; ++p) {
         const double2 w = __ldg(a.w64 + p);
-        const uint32_t r0 = lds_u16(v.l + 2u * (uint32_t)p) * rb;
+        const uint32_t r0 = lds_u32(v.l + 4u * (uint32_t)p);
         const float4 C = lds128(colA + r0);
         const float4 D = lds128(colB + r0);
         const float ju[4] = {C.x, C.z, D.x, D.z}, jv[4] = {C.y, C.w, D.y, D.w};
@@ -422,7 +450,8 @@ constexpr int kStagedThreads = 32 * (kConsumerWarps + 1);
 // Each consumer warp waits for "full", computes its 1/16 share of the
 // tile's items and releases the stage; no block-wide barrier is used.
 template <int OP, bool COMP>
-__global__ void __launch_bounds__(kStagedThreads, 1) staged_f32(TiledArgs a) {
+__global__ void __launch_bounds__(kStagedThreads, 1) staged_f32(const TiledArgs a,
+                                                                 const __grid_constant__ CUtensorMap map) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int NS = a.nstages;
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)NS * a.stage_bytes);
@@ -448,7 +477,7 @@ __global__ void __launch_bounds__(kStagedThreads, 1) staged_f32(TiledArgs a) {
         failed = true;
         break;
       }
-      issue_tile(a, t, stage0 + s * a.stage_bytes, full0 + 8 * s, lane);
+      issue_tile(a, &map, t, stage0 + s * a.stage_bytes, full0 + 8 * s, lane);
     }
     if (failed) {
       if (lane == 0) atomicCAS(a.status, 0, (int)NB_ETIMEOUT);
@@ -478,10 +507,11 @@ __global__ void __launch_bounds__(kStagedThreads, 1) staged_f32(TiledArgs a) {
 
 static int plan_upload(TilePlan *tp, const nb_mesh *mesh) {
   std::vector<int32_t> node0, hptr, halo;
-  std::vector<uint16_t> lnbr;
-  build_tile_plan_host(mesh, tp->rcap, tp->nmax, tp->ecap, node0, hptr, halo, lnbr, tp->max_halo,
-                       tp->max_entries, tp->ntiles_main);
-  lnbr.resize(lnbr.size() + 16, 0);  // slack for 16-byte bounding copies
+  std::vector<uint32_t> loff;
+  build_tile_plan_bytes(mesh, tp->area, tp->row_bytes, tp->copy_bytes, tp->nmax, tp->ecap, node0, hptr,
+                        halo, loff, tp->max_halo, tp->max_entries, tp->ntiles_main);
+  loff.resize(loff.size() + 8, 0);  // slack for 16-byte bounding copies
+  if (halo.empty()) halo.push_back(0);
   tp->ntiles = (int)node0.size() - 1;
   auto up = [&](void **dst, const void *src, size_t bytes) -> int {
     NB_CUDA(cudaMalloc(dst, std::max<size_t>(bytes, 16)));
@@ -493,32 +523,20 @@ static int plan_upload(TilePlan *tp, const nb_mesh *mesh) {
   if ((st = up((void **)&tp->d_tile_node0, node0.data(), node0.size() * 4))) return st;
   if ((st = up((void **)&tp->d_halo_ptr, hptr.data(), hptr.size() * 4))) return st;
   if ((st = up((void **)&tp->d_halo, halo.data(), halo.size() * 4))) return st;
-  if ((st = up((void **)&tp->d_lnbr, lnbr.data(), lnbr.size() * 2))) return st;
-  // runs of consecutive node ids inside each tile's sorted halo
-  std::vector<uint16_t> hrun(halo.size(), 0);
-  std::vector<int32_t> nruns(tp->ntiles, 0);
-  for (int t = 0; t < tp->ntiles; ++t) {
-    int32_t i = hptr[t];
-    while (i < hptr[t + 1]) {
-      int32_t j = i + 1;
-      while (j < hptr[t + 1] && halo[j] == halo[j - 1] + 1 && j - i < 65535) ++j;
-      hrun[i] = (uint16_t)(j - i);
-      ++nruns[t];
-      i = j;
-    }
-  }
-  if ((st = up((void **)&tp->d_hrun, hrun.data(), hrun.size() * 2))) return st;
-  if ((st = up((void **)&tp->d_nruns, nruns.data(), nruns.size() * 4))) return st;
+  if ((st = up((void **)&tp->d_loff, loff.data(), loff.size() * 4))) return st;
   return NB_OK;
 }
 
-static TilePlan *get_plan(nb_method *m, int rcap, int nmax, int ecap, int *status) {
+static TilePlan *get_plan(nb_method *m, int64_t area, int64_t row_bytes, int64_t copy_bytes, int nmax,
+                          int ecap, int *status) {
   std::lock_guard<std::mutex> lk(m->plan_mu);
-  auto key = std::make_tuple(rcap, nmax, ecap);
+  auto key = std::make_tuple(area, row_bytes, copy_bytes, nmax, ecap);
   auto it = m->plans.find(key);
   if (it != m->plans.end()) return it->second.get();
   auto tp = std::make_unique<TilePlan>();
-  tp->rcap = rcap;
+  tp->area = area;
+  tp->row_bytes = row_bytes;
+  tp->copy_bytes = copy_bytes;
   tp->nmax = nmax;
   tp->ecap = ecap;
   *status = plan_upload(tp.get(), m->mesh);
@@ -526,6 +544,25 @@ static TilePlan *get_plan(nb_method *m, int rcap, int nmax, int ecap, int *statu
   TilePlan *raw = tp.get();
   m->plans[key] = std::move(tp);
   return raw;
+}
+
+// cuTensorMapEncodeTiled from the driver, looked up once.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_fn() {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
 }
 
 // Division by a run-time constant d: x / d == (x * m) >> k with k = 32 + s,
@@ -541,7 +578,8 @@ static void magic_div(uint32_t d, uint64_t &magic, uint32_t &shift) {
 }
 
 template <int OP, bool COMP>
-static int launch_staged_t(const TiledArgs &a, int grid, size_t smem, cudaStream_t st) {
+static int launch_staged_t(const TiledArgs &a, const CUtensorMap &map, int grid, size_t smem,
+                           cudaStream_t st) {
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [&] {
@@ -549,7 +587,7 @@ static int launch_staged_t(const TiledArgs &a, int grid, size_t smem, cudaStream
                                     227 * 1024);
   });
   NB_CUDA(attr_err);
-  staged_f32<OP, COMP><<<grid, kStagedThreads, smem, st>>>(a);
+  staged_f32<OP, COMP><<<grid, kStagedThreads, smem, st>>>(a, map);
   count_launch(1);
   NB_CUDA(cudaGetLastError());
   return NB_OK;
@@ -588,26 +626,47 @@ int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, 
   const int nvar = in->nvar;
   // each 4-level group must lie inside the staged column
   if ((uint64_t)G * 16u * nvar > row_bytes) return NB_OK;
-  // nstages stages of stage_kb KB, one 512-thread CTA per SM.  A stage holds
-  // the staged columns, then the tile's weights, staged-row indices and
-  // row pointers (bounding ranges, 16-byte aligned).
+  const uint32_t copy_bytes = (uint32_t)(((int64_t)in->nlev * nvar * 4 + 15) / 16 * 16);
+  // halo columns are gathered as tensor rows of 4-byte (scalar) or 8-byte
+  // (vector) elements; a box row holds at most 256 elements
+  const uint32_t esz = nvar == 2 ? 8u : 4u;
+  if (copy_bytes / esz > 256u || encode_fn() == nullptr) return NB_OK;
+  // nstages stages of stage_kb KB, one CTA per SM.  A stage holds the staged
+  // columns, then the tile's weights, offsets and row pointers (bounding
+  // ranges, 16-byte aligned).
   const int nstages = m->nstages > 0 ? m->nstages : 2;
   const int stage_kb = m->stage_kb > 0 ? m->stage_kb : 112;
   const int nmax = m->tile_nodes > 0 ? m->tile_nodes : 256;
   const int ecap = 10 * nmax;
-  const uint32_t meta_bytes = (uint32_t)((ecap + 2) * 8 + 16) + (uint32_t)((ecap + 16) * 2 + 16) +
-                              (uint32_t)((nmax + 8) * 4 + 16);
+  auto up16 = [](uint32_t x) { return (x + 15u) & ~15u; };
+  const uint32_t wsz = up16((uint32_t)(ecap + 2) * 8u), lsz = up16((uint32_t)(ecap + 8) * 4u),
+                 rsz = up16((uint32_t)(nmax + 8) * 4u);
   const uint32_t stage_target = (uint32_t)stage_kb * 1024u;
-  if (stage_target <= meta_bytes) return NB_OK;
-  const int rcap = (int)((stage_target - meta_bytes) / row_bytes);
-  if (rcap < 24) return NB_OK;  // columns too tall to stage a useful tile
+  if (stage_target <= wsz + lsz + rsz + 4096u) return NB_OK;
+  const uint32_t area = ((stage_target - wsz - lsz - rsz) / 128u) * 128u;
+  if (area < 24u * row_bytes) return NB_OK;  // columns too tall to stage a useful tile
   int status = NB_OK;
-  TilePlan *tp = get_plan(m, rcap, nmax, ecap, &status);
+  TilePlan *tp = get_plan(m, area, row_bytes, copy_bytes, nmax, ecap, &status);
   if (!tp) return status;
   if (g_sm_count == 0) {
     int dev = 0;
     NB_CUDA(cudaGetDevice(&dev));
     NB_CUDA(cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev));
+  }
+  // tensor map over the input columns: rows = nodes (pitch row_bytes), the
+  // first copy_bytes of each row
+  CUtensorMap map;
+  const cuuint64_t gdim[2] = {copy_bytes / esz, (cuuint64_t)in->nnodes};
+  const cuuint64_t gstride[1] = {row_bytes};
+  const cuuint32_t box[2] = {copy_bytes / esz, 1};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult cr = encode_fn()(&map, esz == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                                  2, const_cast<void *>(in->data), gdim, gstride, box, estr,
+                                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) {
+    set_error("staged kernel: cuTensorMapEncodeTiled failed (" + std::to_string((int)cr) + ")");
+    return NB_ECUDA;
   }
   TiledArgs a;
   a.ntiles = tp->ntiles;
@@ -615,9 +674,7 @@ int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, 
   a.tile_node0 = tp->d_tile_node0;
   a.halo_ptr = tp->d_halo_ptr;
   a.halo = tp->d_halo;
-  a.hrun = tp->d_hrun;
-  a.nruns = tp->d_nruns;
-  a.lnbr = tp->d_lnbr;
+  a.loff = tp->d_loff;
   a.row_ptr = m->d_row_ptr;
   const bool g = op == NB_OP_GRAD;
   a.w32 = reinterpret_cast<const float2 *>(g ? m->d_wgrad32 : op == NB_OP_DIV ? m->d_wdiv32 : m->d_wcurl32);
@@ -632,12 +689,12 @@ int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, 
   a.nlev = in->nlev;
   a.G = G;
   magic_div((uint32_t)a.G, a.g_magic, a.g_shift);
-  a.copy_bytes = (uint32_t)(((int64_t)in->nlev * nvar * 4 + 15) / 16 * 16);
-  auto up16 = [](uint32_t x) { return (x + 15u) & ~15u; };
-  a.off_w = up16((uint32_t)rcap * row_bytes);
-  a.off_l = a.off_w + up16((uint32_t)(ecap + 2) * 8u);
-  a.off_r = a.off_l + up16((uint32_t)(ecap + 16) * 2u);
-  a.stage_bytes = (a.off_r + up16((uint32_t)(nmax + 8) * 4u) + 127u) & ~127u;
+  a.copy_bytes = copy_bytes;
+  a.gpitch = (4u * copy_bytes + 127u) & ~127u;
+  a.off_w = area;
+  a.off_l = a.off_w + wsz;
+  a.off_r = a.off_l + lsz;
+  a.stage_bytes = (a.off_r + rsz + 127u) & ~127u;
   a.nstages = nstages;
   a.status = nullptr;
   if (const int rc = status_word(&a.status)) return rc;
@@ -650,8 +707,8 @@ int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, 
   const int grid = std::min(tp->ntiles, g_sm_count);
   *handled = true;
   const bool comp = m->compensated != 0;
-  if (g) return comp ? launch_staged_t<0, true>(a, grid, smem, st) : launch_staged_t<0, false>(a, grid, smem, st);
-  return comp ? launch_staged_t<1, true>(a, grid, smem, st) : launch_staged_t<1, false>(a, grid, smem, st);
+  if (g) return comp ? launch_staged_t<0, true>(a, map, grid, smem, st) : launch_staged_t<0, false>(a, map, grid, smem, st);
+  return comp ? launch_staged_t<1, true>(a, map, grid, smem, st) : launch_staged_t<1, false>(a, map, grid, smem, st);
 }
 
 int device_status(int clear, int *code) {
