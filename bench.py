@@ -63,6 +63,18 @@ def dist_env():
     return rank, world, local
 
 
+def reduce_max(x: float, world: int, device=None) -> float:
+    """Maximum of x over all ranks (identity for one rank).  Works with the
+    gloo (CPU tensors) and nccl (device tensors) backends."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device or "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -244,11 +256,7 @@ def bench_ours(a):
         stream.synchronize()
     barrier()
     launches = nabla.launch_count() - launches0
-    ms_total = start.elapsed_time(stop)
-    t_max = torch.tensor([ms_total], device=device)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    ms_total = float(t_max.item())
+    ms_total = reduce_max(start.elapsed_time(stop), world, device)
     ms_step = ms_total / a.steps
     per_op_ms = {op: statistics.median(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(a.steps))
                  for i, op in enumerate(OPS)}

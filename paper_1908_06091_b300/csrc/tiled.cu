@@ -636,12 +636,17 @@ int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, 
   // ranges, 16-byte aligned).
   const int nstages = m->nstages > 0 ? m->nstages : 2;
   const int stage_kb = m->stage_kb > 0 ? m->stage_kb : 112;
-  const int nmax = m->tile_nodes > 0 ? m->tile_nodes : 256;
-  const int ecap = 10 * nmax;
+  // Metadata reservation: a tile holds at most area / row_bytes own nodes;
+  // the plan caps its CSR entries at 7 per such node (tiles are cut earlier
+  // otherwise), so the reservation follows the columns that fit.
   auto up16 = [](uint32_t x) { return (x + 15u) & ~15u; };
+  const uint32_t stage_target = (uint32_t)stage_kb * 1024u;
+  const int nmax_req = m->tile_nodes > 0 ? m->tile_nodes : 256;
+  const int fit_nodes = (int)(stage_target / row_bytes) + 1;
+  const int nmax = std::max(1, std::min(nmax_req, fit_nodes));
+  const int ecap = 7 * nmax + 16;
   const uint32_t wsz = up16((uint32_t)(ecap + 2) * 8u), lsz = up16((uint32_t)(ecap + 8) * 4u),
                  rsz = up16((uint32_t)(nmax + 8) * 4u);
-  const uint32_t stage_target = (uint32_t)stage_kb * 1024u;
   if (stage_target <= wsz + lsz + rsz + 4096u) return NB_OK;
   const uint32_t area = ((stage_target - wsz - lsz - rsz) / 128u) * 128u;
   if (area < 24u * row_bytes) return NB_OK;  // columns too tall to stage a useful tile
