@@ -84,6 +84,38 @@ const char *nb_version(void);
 /* Message of the last failing call on this thread ("" if none). */
 const char *nb_last_error(void);
 
+/* ------------------------------------------------------ device memory
+ *
+ * Where the device memory the library owns comes from: method geometry and
+ * weights, tile plans, batch tables and batch scratch, and the Laplacian's
+ * intermediate gradient when the caller passes no scratch.  (The paper
+ * leaves memory to its Array/storage layer, Sec. 5.1-5.2; this hook lets a
+ * caller's caching allocator, e.g. torch's, serve these buffers.)
+ *
+ *   alloc(ctx, bytes, stream) returns at least `bytes` bytes of device
+ *     memory on the current device, usable in stream order on `stream`
+ *     (NULL = the legacy default stream; used for buffers that live as long
+ *     as their object), or NULL on failure -- the library call then fails
+ *     with NB_EOOM;
+ *   release(ctx, ptr, bytes, stream) gives a block back, with the size and
+ *     stream it was allocated with.
+ *
+ * Both are called on the thread that called into the library, never from
+ * a library-owned thread.  An object keeps the allocator that was current
+ * when it was created and releases its blocks through it.  The request
+ * server (nb_server_*) always uses its own stream-ordered CUDA pool. */
+typedef struct nb_allocator {
+  void *ctx;
+  void *(*alloc)(void *ctx, int64_t bytes, void *stream);
+  void (*release)(void *ctx, void *ptr, int64_t bytes, void *stream);
+} nb_allocator;
+
+/* Install a copy of *allocator for objects created and calls made from now
+ * on, process-wide.  NULL restores the CUDA runtime (cudaMalloc/cudaFree
+ * for objects, cudaMallocAsync/cudaFreeAsync on the call's stream for the
+ * Laplacian scratch).  Errors: NB_EINVAL if alloc or release is NULL. */
+int nb_set_allocator(const nb_allocator *allocator);
+
 /* ------------------------------------------------------------------ grid */
 
 /* Octahedral reduced Gaussian grid O<N> (Sec. 4.2.3.7, Listing 6): 2N
@@ -338,6 +370,11 @@ int nb_server_submit(nb_server *server, const nb_request *request, uint64_t *tic
  * running, NB_OK with its result otherwise. */
 int nb_server_wait(nb_server *server, uint64_t ticket, double timeout_ms, nb_result *result);
 
+/* Non-blocking query of a request: *done = 1 and *result filled if it has
+ * finished (result->status holds its own error), *done = 0 if it is still
+ * queued or running.  Errors: NB_EINVAL (NULL argument, unknown ticket). */
+int nb_server_poll(nb_server *server, uint64_t ticket, int32_t *done, nb_result *result);
+
 /* Copy a finished request's kept outputs (nfields x [V][Lp][nvar] of its
  * dtype, Lp the padded level stride) to host memory of exactly `bytes`. */
 int nb_server_output(nb_server *server, uint64_t ticket, void *host_out, int64_t bytes);
@@ -366,7 +403,7 @@ enum { NB_KERNEL_AUTO = 0, NB_KERNEL_DIRECT = 1, NB_KERNEL_TILED = 2 };
 int nb_method_set_kernel(nb_method *method, int variant, int tile_nodes);
 
 /* Pipeline shape of the shared-memory staged kernels: nstages stages of
- * stage_kb KB each (nstages * stage_kb <= 224; 0 = defaults 4 x 48 KB).
+ * stage_kb KB each (nstages * stage_kb <= 224; 0 = defaults 2 x 112 KB).
  * Tile plans are sized so that a tile's own columns plus its halo columns
  * fill one stage. */
 int nb_method_set_staging(nb_method *method, int nstages, int stage_kb);

@@ -426,7 +426,10 @@ struct nb_batch : nb::RefCounted {
   std::vector<nb::TuneKey> keys;  // per source item
   std::vector<std::pair<int, int>> shape;  // per source item (lpb, npw)
   std::vector<void *> scratch;  // per source item (Laplacian only)
+  std::vector<size_t> scratch_bytes;
+  nb::DevAlloc alloc;  // allocator current at creation
   nb::BItem *d_items[2] = {nullptr, nullptr};
+  size_t items_bytes[2] = {0, 0};
   int nitems[2] = {0, 0};
   int64_t nunits[2] = {0, 0};
   unsigned long long *d_counter = nullptr;  // 2 counters
@@ -438,11 +441,10 @@ struct nb_batch : nb::RefCounted {
   ~nb_batch() override {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
-    for (int ph = 0; ph < 2; ++ph)
-      if (d_items[ph]) cudaFree(d_items[ph]);
-    if (d_counter) cudaFree(d_counter);
-    for (void *p : scratch)
-      if (p) cudaFree(p);
+    if (d_counter || d_items[0] || d_items[1]) cudaDeviceSynchronize();
+    for (int ph = 0; ph < 2; ++ph) nb::dev_free(alloc, d_items[ph], items_bytes[ph]);
+    nb::dev_free(alloc, d_counter, 2 * sizeof(unsigned long long));
+    for (size_t k = 0; k < scratch.size(); ++k) nb::dev_free(alloc, scratch[k], scratch_bytes[k]);
     for (auto &s : src) nb::release(s.method);
   }
 };
@@ -515,11 +517,16 @@ static int batch_build_tables(nb_batch *bt) {
     bt->nunits[p] = u;
     bt->nitems[p] = (int)ph[p].size();
     if (bt->d_items[p]) {
-      cudaFree(bt->d_items[p]);
+      cudaDeviceSynchronize();
+      dev_free(bt->alloc, bt->d_items[p], bt->items_bytes[p]);
       bt->d_items[p] = nullptr;
+      bt->items_bytes[p] = 0;
     }
     if (!ph[p].empty()) {
-      NB_CUDA(cudaMalloc(&bt->d_items[p], ph[p].size() * sizeof(BItem)));
+      const int st = dev_alloc(bt->alloc, (void **)&bt->d_items[p], ph[p].size() * sizeof(BItem),
+                               "batch work table");
+      if (st != NB_OK) return st;
+      bt->items_bytes[p] = ph[p].size() * sizeof(BItem);
       NB_CUDA(cudaMemcpy(bt->d_items[p], ph[p].data(), ph[p].size() * sizeof(BItem),
                          cudaMemcpyHostToDevice));
     }
@@ -582,6 +589,7 @@ int nb_batch_create(const nb_batch_item *items, int n, nb_batch **out) {
   }
   try {
     auto *bt = new nb_batch();
+    bt->alloc = nb::current_allocator();
     std::lock_guard<std::mutex> lk(nb::g_tune_mu);
     static bool loaded = false;
     if (!loaded) {
@@ -605,23 +613,29 @@ int nb_batch_create(const nb_batch_item *items, int n, nb_batch **out) {
       bt->shape.push_back((g != nb::g_tune.end() && hit != g->second.end()) ? hit->second
                                                                              : nb::default_shape(it.in.nlev));
       void *scr = nullptr;
+      size_t scr_bytes = 0;
       if (it.op == NB_OP_LAP) {
         const int64_t elem = it.in.dtype == NB_F64 ? 8 : 4;
         const int q = it.in.dtype == NB_F64 ? 2 : 4;
         const int64_t stride = 2 * (int64_t)((it.in.nlev + q - 1) / q) * q;
-        if (cudaMalloc(&scr, (size_t)(stride * it.in.nnodes * elem)) != cudaSuccess) {
+        scr_bytes = (size_t)(stride * it.in.nnodes * elem);
+        const int sa = nb::dev_alloc(bt->alloc, &scr, scr_bytes, "nb_batch_create: Laplacian scratch");
+        if (sa != NB_OK) {
           nb::release(bt);
-          nb::set_error("nb_batch_create: scratch allocation failed");
-          return NB_EOOM;
+          return sa;
         }
       }
       bt->scratch.push_back(scr);
+      bt->scratch_bytes.push_back(scr_bytes);
       bt->node_levels += it.in.nnodes * (int64_t)it.in.nlev;
     }
-    if (cudaMalloc(&bt->d_counter, 2 * sizeof(unsigned long long)) != cudaSuccess) {
-      nb::release(bt);
-      nb::set_error("nb_batch_create: counter allocation failed");
-      return NB_EOOM;
+    {
+      const int ca = nb::dev_alloc(bt->alloc, (void **)&bt->d_counter, 2 * sizeof(unsigned long long),
+                                   "nb_batch_create: counters");
+      if (ca != NB_OK) {
+        nb::release(bt);
+        return ca;
+      }
     }
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
@@ -708,12 +722,14 @@ int nb_batch_tune(nb_batch *b, void *stream) {
     one.src.push_back(b->src[k]);
     nb::retain(b->src[k].method);
     one.scratch.push_back(b->scratch[k]);
+    one.scratch_bytes.push_back(b->scratch_bytes[k]);
+    one.alloc = b->alloc;
     one.grid = b->grid;
     one.comp = b->comp;
     one.shape.push_back({0, 0});
-    if (cudaMalloc(&one.d_counter, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+    if ((rc = nb::dev_alloc(one.alloc, (void **)&one.d_counter, 2 * sizeof(unsigned long long),
+                            "nb_batch_tune: counters")) != NB_OK) {
       one.scratch[0] = nullptr;
-      rc = NB_EOOM;
       break;
     }
     float best_ms = 1e30f;

@@ -6,6 +6,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <stdexcept>
 #include <string>
@@ -17,6 +18,67 @@ namespace nb {
 
 static thread_local std::string t_last_error;
 void set_error(const std::string &msg) { t_last_error = msg; }
+
+static std::mutex g_alloc_mu;
+static DevAlloc g_alloc;
+
+DevAlloc current_allocator() {
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  return g_alloc;
+}
+
+int dev_alloc(const DevAlloc &a, void **ptr, size_t bytes, const char *what) {
+  *ptr = nullptr;
+  if (!a.user.alloc) {
+    const cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e == cudaSuccess) return NB_OK;
+    *ptr = nullptr;
+    if (e == cudaErrorMemoryAllocation) {
+      cudaGetLastError();
+      set_error(std::string(what) + ": cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+      return NB_EOOM;
+    }
+    return cuda_fail(e, what);
+  }
+  *ptr = a.user.alloc(a.user.ctx, (int64_t)bytes, nullptr);
+  if (*ptr) return NB_OK;
+  set_error(std::string(what) + ": allocator callback returned NULL for " + std::to_string(bytes) +
+            " bytes");
+  return NB_EOOM;
+}
+
+void dev_free(const DevAlloc &a, void *ptr, size_t bytes) {
+  if (!ptr) return;
+  if (a.user.release)
+    a.user.release(a.user.ctx, ptr, (int64_t)bytes, nullptr);
+  else
+    cudaFree(ptr);
+}
+
+int dev_alloc_async(const DevAlloc &a, void **ptr, size_t bytes, void *stream, const char *what) {
+  *ptr = nullptr;
+  if (!a.user.alloc) {
+    const cudaError_t e = cudaMallocAsync(ptr, bytes, static_cast<cudaStream_t>(stream));
+    if (e == cudaSuccess) return NB_OK;
+    *ptr = nullptr;
+    return cuda_fail(e, what);
+  }
+  *ptr = a.user.alloc(a.user.ctx, (int64_t)bytes, stream);
+  if (*ptr) return NB_OK;
+  set_error(std::string(what) + ": allocator callback returned NULL for " + std::to_string(bytes) +
+            " bytes");
+  return NB_EOOM;
+}
+
+int dev_free_async(const DevAlloc &a, void *ptr, size_t bytes, void *stream) {
+  if (!ptr) return NB_OK;
+  if (a.user.release) {
+    a.user.release(a.user.ctx, ptr, (int64_t)bytes, stream);
+    return NB_OK;
+  }
+  const cudaError_t e = cudaFreeAsync(ptr, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? NB_OK : cuda_fail(e, "cudaFreeAsync");
+}
 
 int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, cudaStream_t st,
                  bool *handled);
@@ -60,6 +122,14 @@ extern "C" {
 const char *nb_version(void) { return "nabla_b300 0.1.0 sm_103a"; }
 
 const char *nb_last_error(void) { return nb::t_last_error.c_str(); }
+
+int nb_set_allocator(const nb_allocator *a) {
+  NB_REQUIRE(!a || (a->alloc && a->release), NB_EINVAL,
+             "nb_set_allocator: alloc and release must both be set");
+  std::lock_guard<std::mutex> lk(nb::g_alloc_mu);
+  nb::g_alloc.user = a ? *a : nb_allocator{};
+  return NB_OK;
+}
 
 int nb_launch_count(int64_t *count) {
   NB_REQUIRE(count, NB_EINVAL, "nb_launch_count: NULL");
@@ -202,6 +272,7 @@ int nb_method_create(const nb_mesh *mesh, double radius_m, nb_method **out) {
   auto *m = new nb_method();
   m->mesh = nb::retain(const_cast<nb_mesh *>(mesh));
   m->R = radius_m > 0 ? radius_m : 6.37122e6;
+  m->alloc = nb::current_allocator();
   nb::build_geometry(mesh, m->R, m->vol, m->S, m->T, m->east, m->north);
   const int st = nb::method_upload(m);
   if (st != NB_OK) {
@@ -426,13 +497,17 @@ int launch_op(nb_method *m, int op, const nb_field *in, const nb_field *out,
   // Laplacian: gradient into scratch, then the divergence of it
   nb_field tmp;
   void *owned = nullptr;
+  size_t owned_bytes = 0;
+  const DevAlloc alloc = current_allocator();
   if (scratch) {
     tmp = *scratch;
   } else {
     const int64_t elem = in->dtype == NB_F64 ? 8 : 4;
     const int q = in->dtype == NB_F64 ? 2 : 4;
     const int64_t stride = 2 * (int64_t)((in->nlev + q - 1) / q) * q;
-    NB_CUDA(cudaMallocAsync(&owned, (size_t)(stride * in->nnodes * elem), st));
+    owned_bytes = (size_t)(stride * in->nnodes * elem);
+    const int ra = dev_alloc_async(alloc, &owned, owned_bytes, stream, "Laplacian scratch");
+    if (ra != NB_OK) return ra;
     tmp = *in;
     tmp.data = owned;
     tmp.nvar = 2;
@@ -442,8 +517,8 @@ int launch_op(nb_method *m, int op, const nb_field *in, const nb_field *out,
   int rc = launch_single(m, NB_OP_GRAD, in, &tmp, st);
   if (rc == NB_OK) rc = launch_single(m, NB_OP_DIV, &tmp, out, st);
   if (owned) {
-    const cudaError_t e = cudaFreeAsync(owned, st);
-    if (rc == NB_OK && e != cudaSuccess) rc = cuda_fail(e, "cudaFreeAsync");
+    const int rf = dev_free_async(alloc, owned, owned_bytes, stream);
+    if (rc == NB_OK) rc = rf;
   }
   return rc;
 }

@@ -17,6 +17,23 @@ namespace nb {
 
 void set_error(const std::string &msg);
 
+// Source of library-owned device memory: the caller's nb_allocator, or the
+// CUDA runtime when user.alloc is NULL (capi.cu).
+struct DevAlloc {
+  nb_allocator user{};
+};
+struct DevBlock {
+  void *ptr;
+  size_t bytes;
+};
+DevAlloc current_allocator();
+// Long-lived blocks (stream NULL): cudaMalloc/cudaFree or the callbacks.
+int dev_alloc(const DevAlloc &a, void **ptr, size_t bytes, const char *what);
+void dev_free(const DevAlloc &a, void *ptr, size_t bytes);
+// Stream-ordered scratch: cudaMallocAsync/cudaFreeAsync or the callbacks.
+int dev_alloc_async(const DevAlloc &a, void **ptr, size_t bytes, void *stream, const char *what);
+int dev_free_async(const DevAlloc &a, void *ptr, size_t bytes, void *stream);
+
 // Intrusive reference count shared by every handle type.
 struct RefCounted {
   std::atomic<int> refs{1};
@@ -103,6 +120,8 @@ struct nb_method : nb::RefCounted {
   float *d_wgrad32 = nullptr, *d_wdiv32 = nullptr, *d_wcurl32 = nullptr;
   float *d_sdiv32 = nullptr, *d_scurl32 = nullptr;
   int64_t device_bytes = 0;
+  nb::DevAlloc alloc;                // allocator current at creation
+  std::vector<nb::DevBlock> blocks;  // every device block of the method and its plans
   // kernel control
   int kernel_variant = 0;  // NB_KERNEL_*
   int tile_nodes = 0;   // staged kernels: nodes per tile at most (0 = 256)

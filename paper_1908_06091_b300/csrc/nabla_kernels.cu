@@ -87,9 +87,11 @@ __global__ void __launch_bounds__(256) setup_weights_kernel(
 }
 
 template <class T>
-static int dev_upload(T **dst, const void *src, size_t n, int64_t &bytes) {
-  NB_CUDA(cudaMalloc((void **)dst, n * sizeof(T)));
-  bytes += (int64_t)(n * sizeof(T));
+static int dev_upload(nb_method *m, T **dst, const void *src, size_t n) {
+  const int st = dev_alloc(m->alloc, (void **)dst, n * sizeof(T), "method upload");
+  if (st != NB_OK) return st;
+  m->blocks.push_back({*dst, n * sizeof(T)});
+  m->device_bytes += (int64_t)(n * sizeof(T));
   if (src) NB_CUDA(cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice));
   return NB_OK;
 }
@@ -98,7 +100,6 @@ int method_upload(nb_method *m) {
   const nb_mesh *mesh = m->mesh;
   const int64_t V = mesh->V, E = mesh->E, P = 2 * E;
   NB_CUDA(cudaGetDevice(&m->device));
-  int64_t &b = m->device_bytes;
   // row_ptr is padded with 8 copies of its last entry so that 16-byte
   // aligned bounding copies of any node range stay inside the allocation
   std::vector<int32_t> rp(V + 1 + 8);
@@ -106,7 +107,7 @@ int method_upload(nb_method *m) {
   for (int64_t i = V + 1; i < V + 9; ++i) rp[i] = (int32_t)mesh->row_ptr[V];
   int st;
 #define UP(dst, src, n) \
-  if ((st = dev_upload(&(dst), (src), (n), b)) != NB_OK) return st;
+  if ((st = dev_upload(m, &(dst), (src), (n))) != NB_OK) return st;
   UP(m->d_row_ptr, rp.data(), V + 9);
   UP(m->d_nbr, mesh->nbr.data(), P);
   UP(m->d_nbr_edge, mesh->nbr_edge.data(), P);
@@ -141,18 +142,11 @@ int method_upload(nb_method *m) {
 }
 
 void method_free_device(nb_method *m) {
-  void *ptrs[] = {m->d_row_ptr, m->d_nbr, m->d_nbr_edge, m->d_vol, m->d_S, m->d_T, m->d_east,
-                  m->d_north, m->d_wgrad64, m->d_wdiv64, m->d_wcurl64, m->d_sdiv64,
-                  m->d_scurl64, m->d_wgrad32, m->d_wdiv32, m->d_wcurl32, m->d_sdiv32,
-                  m->d_scurl32};
-  for (void *p : ptrs)
-    if (p) cudaFree(p);
-  for (auto &kv : m->plans) {
-    TilePlan *tp = kv.second.get();
-    void *q[] = {tp->d_tile_node0, tp->d_halo_ptr, tp->d_halo, tp->d_loff};
-    for (void *p : q)
-      if (p) cudaFree(p);
-  }
+  // every block of the method and of its tile plans, through the allocator
+  // that made it (plans are created under plan_mu and recorded there too)
+  if (!m->blocks.empty()) cudaDeviceSynchronize();
+  for (const DevBlock &b : m->blocks) dev_free(m->alloc, b.ptr, b.bytes);
+  m->blocks.clear();
   m->plans.clear();
 }
 

@@ -448,6 +448,27 @@ int nb_server_wait(nb_server *s, uint64_t ticket, double timeout_ms, nb_result *
   return NB_OK;
 }
 
+int nb_server_poll(nb_server *s, uint64_t ticket, int32_t *done, nb_result *res) {
+  if (!s || !done || !res) {
+    nb::set_error("nb_server_poll: NULL argument");
+    return NB_EINVAL;
+  }
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) {
+      nb::set_error("nb_server_poll: unknown ticket");
+      return NB_EINVAL;
+    }
+    if (it->second->done < 0) {
+      *done = 0;
+      return NB_OK;
+    }
+  }
+  *done = 1;
+  return nb_server_wait(s, ticket, 0.0, res);
+}
+
 int nb_server_output(nb_server *s, uint64_t ticket, void *host_out, int64_t bytes) {
   if (!s || !host_out) {
     nb::set_error("nb_server_output: NULL argument");

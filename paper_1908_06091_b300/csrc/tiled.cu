@@ -505,7 +505,8 @@ __global__ void __launch_bounds__(kStagedThreads, 1) staged_f32(const TiledArgs 
 
 // --------------------------------------------------------------- host
 
-static int plan_upload(TilePlan *tp, const nb_mesh *mesh) {
+static int plan_upload(TilePlan *tp, nb_method *m) {
+  const nb_mesh *mesh = m->mesh;
   std::vector<int32_t> node0, hptr, halo;
   std::vector<uint32_t> loff;
   build_tile_plan_bytes(mesh, tp->area, tp->row_bytes, tp->copy_bytes, tp->nmax, tp->ecap, node0, hptr,
@@ -514,7 +515,10 @@ static int plan_upload(TilePlan *tp, const nb_mesh *mesh) {
   if (halo.empty()) halo.push_back(0);
   tp->ntiles = (int)node0.size() - 1;
   auto up = [&](void **dst, const void *src, size_t bytes) -> int {
-    NB_CUDA(cudaMalloc(dst, std::max<size_t>(bytes, 16)));
+    const size_t nb = std::max<size_t>(bytes, 16);
+    const int st = dev_alloc(m->alloc, dst, nb, "tile plan upload");
+    if (st != NB_OK) return st;
+    m->blocks.push_back({*dst, nb});
     if (bytes) NB_CUDA(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
     tp->bytes += (int64_t)bytes;
     return NB_OK;
@@ -539,7 +543,7 @@ static TilePlan *get_plan(nb_method *m, int64_t area, int64_t row_bytes, int64_t
   tp->copy_bytes = copy_bytes;
   tp->nmax = nmax;
   tp->ecap = ecap;
-  *status = plan_upload(tp.get(), m->mesh);
+  *status = plan_upload(tp.get(), m);
   if (*status != NB_OK) return nullptr;
   TilePlan *raw = tp.get();
   m->plans[key] = std::move(tp);

@@ -57,6 +57,14 @@ class nb_request(ctypes.Structure):
                 ("seed", ctypes.c_uint64)]
 
 
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p)
+_RELEASE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p)
+
+
+class nb_allocator(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("alloc", _ALLOC_FN), ("release", _RELEASE_FN)]
+
+
 class nb_result(ctypes.Structure):
     _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("arrival_s", ctypes.c_double), ("admit_s", ctypes.c_double), ("done_s", ctypes.c_double),
@@ -105,6 +113,7 @@ SIGNATURES = {
     "nb_nabla_apply": [_P, _I, _FP, _FP, _FP, _P],
     "nb_nabla_laplacian_noalloc": [_P, _FP, _FP, _P],
     "nb_nabla_apply_host": [_P, _I, _P, _P, _FP, _FP, _FP, _P],
+    "nb_set_allocator": [ctypes.POINTER(nb_allocator)],
     "nb_launch_count": [_I64P],
     "nb_device_status": [_I, ctypes.POINTER(ctypes.c_int32)],
     "nb_batch_create": [_P, _I, ctypes.POINTER(_P)],
@@ -118,6 +127,7 @@ SIGNATURES = {
     "nb_server_add_grid": [_P, _P, _P, _P],
     "nb_server_submit": [_P, ctypes.POINTER(nb_request), ctypes.POINTER(ctypes.c_uint64)],
     "nb_server_wait": [_P, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(nb_result)],
+    "nb_server_poll": [_P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(nb_result)],
     "nb_server_output": [_P, ctypes.c_uint64, _P, ctypes.c_int64],
     "nb_server_input": [_P, ctypes.c_uint64, _P, ctypes.c_int64],
     "nb_server_stats": [_P, _I64P, _I64P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)],
@@ -163,6 +173,34 @@ def device_status(clear: bool = False) -> int:
     c = ctypes.c_int32()
     check(lib().nb_device_status(1 if clear else 0, ctypes.byref(c)))
     return c.value
+
+
+# callbacks of the installed allocator, kept alive while the library may call them
+_allocator_keep = []
+
+
+def _torch_alloc(ctx, nbytes, stream):
+    try:
+        return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+    except Exception:  # out of memory: the library call fails with NB_EOOM
+        return None
+
+
+def _torch_release(ctx, ptr, nbytes, stream):
+    torch.cuda.caching_allocator_delete(ptr)
+
+
+def use_torch_allocator(on: bool = True) -> None:
+    """Serve the library's own device buffers (method geometry, tile plans,
+    batch tables, Laplacian scratch) from torch's caching allocator, or, with
+    on=False, from the CUDA runtime again.  Objects keep the allocator that
+    was current when they were created."""
+    if on:
+        a = nb_allocator(None, _ALLOC_FN(_torch_alloc), _RELEASE_FN(_torch_release))
+        check(lib().nb_set_allocator(ctypes.byref(a)))
+        _allocator_keep.append(a)
+    else:
+        check(lib().nb_set_allocator(None))
 
 
 class _Handle:
@@ -440,6 +478,12 @@ class Server(_Handle):
         res = nb_result()
         check(lib().nb_server_wait(self._h, ticket, float(timeout_ms), ctypes.byref(res)))
         return res
+
+    def poll(self, ticket: int):
+        """The request's result if it has finished, else None (never blocks)."""
+        res, done = nb_result(), ctypes.c_int32()
+        check(lib().nb_server_poll(self._h, ticket, ctypes.byref(done), ctypes.byref(res)))
+        return res if done.value else None
 
     def output(self, ticket: int, req) -> np.ndarray:
         meth = self.grids[req.N]

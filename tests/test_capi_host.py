@@ -137,3 +137,15 @@ def test_tile_plan_fits_stage_and_maps_every_neighbour(N, rcap, nmax):
     e = m.edges()
     deg = np.bincount(e.ravel(), minlength=m.V)
     assert np.array_equal(np.diff(rp), deg)
+
+
+def test_allocator_and_server_poll_argument_checks():
+    """nb_set_allocator wants both callbacks (NULL restores the CUDA runtime);
+    nb_server_poll rejects NULL arguments before touching any server."""
+    L = nabla.lib()
+    half = nabla.nb_allocator(None, nabla._ALLOC_FN(lambda c, n, s: None), nabla._RELEASE_FN())
+    assert L.nb_set_allocator(ctypes.byref(half)) == nabla.NB_EINVAL
+    assert b"both" in L.nb_last_error()
+    assert L.nb_set_allocator(None) == nabla.NB_OK
+    done, res = ctypes.c_int32(), nabla.nb_result()
+    assert L.nb_server_poll(None, 1, ctypes.byref(done), ctypes.byref(res)) == nabla.NB_EINVAL

@@ -128,3 +128,21 @@ def test_trace_replay_orders_times(server):
         assert res[k].status == nabla.NB_OK
         assert res[k].arrival_s <= res[k].admit_s <= res[k].done_s
         assert res[k].arrival_s >= arrivals[k] - 1e-3
+
+
+def test_poll_reports_pending_then_the_waited_result(server):
+    import time
+    req = nabla.Server.request("lap", 24, 137, nfields=8, seed=9)
+    t = server.submit(req)
+    seen_pending = server.poll(t) is None
+    deadline = time.monotonic() + 60.0
+    res = None
+    while res is None and time.monotonic() < deadline:
+        res = server.poll(t)
+        time.sleep(0.001)
+    assert res is not None and res.status == nabla.NB_OK
+    w = server.wait(t, 0.0)
+    assert (w.ticket, w.done_s, w.node_levels) == (res.ticket, res.done_s, res.node_levels)
+    assert isinstance(seen_pending, bool)
+    with pytest.raises(nabla.NablaError):
+        server.poll(t + 10_000)
