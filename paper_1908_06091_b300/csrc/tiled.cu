@@ -222,6 +222,15 @@ __device__ __forceinline__ float2 lds64(uint32_t a) {
   asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
   return v;
 }
+// 16 bytes as two packed FP32x2 registers, 8 bytes as one (no repacking moves)
+__device__ __forceinline__ void lds2x64(uint32_t a, unsigned long long &lo, unsigned long long &hi) {
+  asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(lo), "=l"(hi) : "r"(a));
+}
+__device__ __forceinline__ unsigned long long lds_b64(uint32_t a) {
+  unsigned long long v;
+  asm volatile("ld.shared.b64 %0, [%1];" : "=l"(v) : "r"(a));
+  return v;
+}
 __device__ __forceinline__ uint32_t lds_u32(uint32_t a) {
   uint32_t v;
   asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
@@ -251,7 +260,125 @@ struct TileView {
   }
 };
 
-// Items [i0, i1) of tile t for the calling warp, one per lane, stride 32.
+// Consumer side.  A warp takes items [i0, i1) of tile t, one per lane,
+// stride 32.  All but a handful of nodes of an octahedral mesh have six
+// neighbours: for them the neighbour loop is fully unrolled, so every
+// accumulator and address stays in fixed registers and no loop bookkeeping
+// is issued; other degrees take a loop over neighbour pairs.  Staged data
+// is loaded straight into packed FP32x2 registers.
+//
+// div / curl.  A staged (u, v) column is a sequence of 16-byte units of two
+// levels each; item c of a node takes units c and c + G, so that every
+// shared-memory load of a warp reads consecutive 16-byte words.
+template <bool COMP>
+__device__ __forceinline__ void divcurl_tile(const TiledArgs &a, int t, uint32_t stage, int part,
+                                             int nparts) {
+  const TileView v(a, t, stage);
+  const uint32_t items = (uint32_t)(v.n1 - v.n0) * a.G;
+  const uint32_t i0 = (uint32_t)(((uint64_t)items * part) / nparts);
+  const uint32_t i1 = (uint32_t)(((uint64_t)items * (part + 1)) / nparts);
+  const bool pole = t >= a.ntiles_main;
+  const int units = (a.nlev + 1) / 2;
+  const uint32_t rb = a.row_bytes;
+  const uint32_t g16 = 16u * (uint32_t)a.G;
+  for (uint32_t item = i0 + (threadIdx.x & 31); item < i1; item += 32) {
+    const uint32_t il = (uint32_t)(((uint64_t)item * a.g_magic) >> a.g_shift);
+    const uint32_t c = item - il * a.G;
+    const int u0 = (int)c, u1 = (int)c + a.G;
+    const bool has1 = u1 < units;
+    const int32_t node = v.n0 + (int32_t)il;
+    const int32_t p0 = lds_s32(v.r + 4u * (uint32_t)node), p1 = lds_s32(v.r + 4u * (uint32_t)node + 4u);
+    const uint32_t colA = v.rows + (uint32_t)u0 * 16u;
+    const uint32_t colB = colA + (has1 ? g16 : 0u);
+    float r[4];
+    if (!pole) {
+      f2_t i0p, i1p, i2p, i3p;
+      lds2x64(colA + il * rb, i0p, i1p);
+      lds2x64(colB + il * rb, i2p, i3p);
+      Kahan2<COMP> k0, k1, k2, k3;
+      const uint32_t pw = v.w + 8u * (uint32_t)p0, pl = v.l + 4u * (uint32_t)p0;
+      auto pair = [&](uint32_t q) {
+        const f2_t w20 = lds_b64(pw + 8u * q), w21 = lds_b64(pw + 8u * q + 8u);
+        const uint32_t r0 = lds_u32(pl + 4u * q), r1 = lds_u32(pl + 4u * q + 4u);
+        f2_t c00, c01, d00, d01, c10, c11, d10, d11;
+        lds2x64(colA + r0, c00, c01);
+        lds2x64(colB + r0, d00, d01);
+        lds2x64(colA + r1, c10, c11);
+        lds2x64(colB + r1, d10, d11);
+        k0.add_pair(w20, sub2(c00, i0p), w21, sub2(c10, i0p));
+        k1.add_pair(w20, sub2(c01, i1p), w21, sub2(c11, i1p));
+        k2.add_pair(w20, sub2(d00, i2p), w21, sub2(d10, i2p));
+        k3.add_pair(w20, sub2(d01, i3p), w21, sub2(d11, i3p));
+      };
+      auto single = [&](uint32_t q) {
+        const f2_t w2 = lds_b64(pw + 8u * q);
+        const uint32_t r0 = lds_u32(pl + 4u * q);
+        f2_t c00, c01, d00, d01;
+        lds2x64(colA + r0, c00, c01);
+        lds2x64(colB + r0, d00, d01);
+        k0.add_prod(w2, sub2(c00, i0p));
+        k1.add_prod(w2, sub2(c01, i1p));
+        k2.add_prod(w2, sub2(d00, i2p));
+        k3.add_prod(w2, sub2(d01, i3p));
+      };
+      const int deg = p1 - p0;
+      if (deg == 6) {
+        pair(0);
+        pair(2);
+        pair(4);
+      } else {
+        int q = 0;
+        for (; q + 1 < deg; q += 2) pair((uint32_t)q);
+        if (q < deg) single((uint32_t)q);
+      }
+      const f2_t sw2 = *reinterpret_cast<const f2_t *>(a.s32 + node);
+      const f2_t vals[4] = {k0.value(), k1.value(), k2.value(), k3.value()};
+      const f2_t self[4] = {i0p, i1p, i2p, i3p};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const f2_t q = fma2(sw2, self[k], vals[k]);
+        float x, y;
+        upk(q, x, y);
+        r[k] = __fadd_rn(x, y);
+      }
+    } else {
+      const float4 A = lds128(colA + il * rb);
+      const float4 B = lds128(colB + il * rb);
+      const float iu[4] = {A.x, A.z, B.x, B.z}, iv[4] = {A.y, A.w, B.y, B.w};
+      double sacc[4] = {0, 0, 0, 0};
+      for (int32_t p = p0; p < p1; ++p) {
+        const double2 w = __ldg(a.w64 + p);
+        const uint32_t r0 = lds_u32(v.l + 4u * (uint32_t)p);
+        const float4 C = lds128(colA + r0);
+        const float4 D = lds128(colB + r0);
+        const float ju[4] = {C.x, C.z, D.x, D.z}, jv[4] = {C.y, C.w, D.y, D.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          sacc[k] = fma(w.x, (double)ju[k] - (double)iu[k], sacc[k]);
+          sacc[k] = fma(w.y, (double)jv[k] - (double)iv[k], sacc[k]);
+        }
+      }
+      const double2 sw = __ldg(a.s64 + node);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        sacc[k] = fma(sw.x, (double)iu[k], sacc[k]);
+        sacc[k] = fma(sw.y, (double)iv[k], sacc[k]);
+        r[k] = (float)sacc[k];
+      }
+    }
+    float *oo = a.out + (int64_t)node * a.out_stride;
+    const int la0 = 2 * u0, la1 = 2 * u1;
+    if (la0 + 1 < a.nlev) __stcs(reinterpret_cast<float2 *>(oo + la0), make_float2(r[0], r[1]));
+    else oo[la0] = r[0];
+    if (has1) {
+      if (la1 + 1 < a.nlev) __stcs(reinterpret_cast<float2 *>(oo + la1), make_float2(r[2], r[3]));
+      else oo[la1] = r[2];
+    }
+  }
+}
+
+// grad.  Item c of a node takes the 4-level unit c of its scalar column;
+// each weight is broadcast to both lanes of a packed register.
 template <bool COMP>
 __device__ __forceinline__ void grad_tile(const TiledArgs &a, int t, uint32_t stage, int part,
                                           int nparts) {
@@ -268,41 +395,54 @@ __device__ __forceinline__ void grad_tile(const TiledArgs &a, int t, uint32_t st
     const int32_t node = v.n0 + (int32_t)il;
     const int32_t p0 = lds_s32(v.r + 4u * (uint32_t)node), p1 = lds_s32(v.r + 4u * (uint32_t)node + 4u);
     const uint32_t col = v.rows + c * 16u;
-    const float4 fi = lds128(col + il * rb);
     float gx[4], gy[4];
     if (!pole) {
-      const f2_t fi01 = pk(fi.x, fi.y), fi23 = pk(fi.z, fi.w);
+      f2_t fi01, fi23;
+      lds2x64(col + il * rb, fi01, fi23);
       Kahan2<COMP> ax01, ax23, ay01, ay23;
-      auto body = [&](const float2 w, const float4 fj) {
-        const f2_t d01 = sub2(pk(fj.x, fj.y), fi01), d23 = sub2(pk(fj.z, fj.w), fi23);
-        const f2_t wx = pk(w.x, w.x), wy = pk(w.y, w.y);
-        ax01.add_prod(wx, d01);
-        ax23.add_prod(wx, d23);
-        ay01.add_prod(wy, d01);
-        ay23.add_prod(wy, d23);
-      };
-      uint32_t pw = v.w + 8u * (uint32_t)p0, pl = v.l + 4u * (uint32_t)p0;
-      int32_t p = p0;
-      for (; p + 1 < p1; p += 2, pw += 16u, pl += 8u) {
-        const float2 w0 = lds64(pw), w1 = lds64(pw + 8u);
-        const uint32_t r0 = lds_u32(pl), r1 = lds_u32(pl + 4u);
-        const float4 f0 = lds128(col + r0);
-        const float4 f1 = lds128(col + r1);
-        const f2_t a01 = sub2(pk(f0.x, f0.y), fi01), a23 = sub2(pk(f0.z, f0.w), fi23);
-        const f2_t b01 = sub2(pk(f1.x, f1.y), fi01), b23 = sub2(pk(f1.z, f1.w), fi23);
+      const uint32_t pw = v.w + 8u * (uint32_t)p0, pl = v.l + 4u * (uint32_t)p0;
+      auto pair = [&](uint32_t q) {
+        const float2 w0 = lds64(pw + 8u * q), w1 = lds64(pw + 8u * q + 8u);
+        const uint32_t r0 = lds_u32(pl + 4u * q), r1 = lds_u32(pl + 4u * q + 4u);
+        f2_t f001, f023, f101, f123;
+        lds2x64(col + r0, f001, f023);
+        lds2x64(col + r1, f101, f123);
+        const f2_t a01 = sub2(f001, fi01), a23 = sub2(f023, fi23);
+        const f2_t b01 = sub2(f101, fi01), b23 = sub2(f123, fi23);
         const f2_t wx0 = pk(w0.x, w0.x), wy0 = pk(w0.y, w0.y);
         const f2_t wx1 = pk(w1.x, w1.x), wy1 = pk(w1.y, w1.y);
         ax01.add_pair(wx0, a01, wx1, b01);
         ax23.add_pair(wx0, a23, wx1, b23);
         ay01.add_pair(wy0, a01, wy1, b01);
         ay23.add_pair(wy0, a23, wy1, b23);
+      };
+      auto single = [&](uint32_t q) {
+        const float2 w = lds64(pw + 8u * q);
+        f2_t f001, f023;
+        lds2x64(col + lds_u32(pl + 4u * q), f001, f023);
+        const f2_t d01 = sub2(f001, fi01), d23 = sub2(f023, fi23);
+        const f2_t wx = pk(w.x, w.x), wy = pk(w.y, w.y);
+        ax01.add_prod(wx, d01);
+        ax23.add_prod(wx, d23);
+        ay01.add_prod(wy, d01);
+        ay23.add_prod(wy, d23);
+      };
+      const int deg = p1 - p0;
+      if (deg == 6) {
+        pair(0);
+        pair(2);
+        pair(4);
+      } else {
+        int q = 0;
+        for (; q + 1 < deg; q += 2) pair((uint32_t)q);
+        if (q < deg) single((uint32_t)q);
       }
-      if (p < p1) body(lds64(pw), lds128(col + lds_u32(pl)));
       upk(ax01.value(), gx[0], gx[1]);
       upk(ax23.value(), gx[2], gx[3]);
       upk(ay01.value(), gy[0], gy[1]);
       upk(ay23.value(), gy[2], gy[3]);
     } else {
+      const float4 fi = lds128(col + il * rb);
       double sx[4] = {0, 0, 0, 0}, sy[4] = {0, 0, 0, 0};
       const float fiv[4] = {fi.x, fi.y, fi.z, fi.w};
       for (int32_t p = p0; p < p1; ++p) {
@@ -333,105 +473,6 @@ __device__ __forceinline__ void grad_tile(const TiledArgs &a, int t, uint32_t st
           go[2 * k] = gx[k];
           go[2 * k + 1] = gy[k];
         }
-    }
-  }
-}
-
-// div / curl.  A staged (u, v) column is a sequence of 16-byte units of two
-// levels each; item c of a node takes units c and c + G, so that every
-// shared-memory load of a warp reads consecutive 16-byte words.
-template <bool COMP>
-__device__ __forceinline__ void divcurl_tile(const TiledArgs &a, int t, uint32_t stage, int part,
-                                             int nparts) {
-  const TileView v(a, t, stage);
-  const uint32_t items = (uint32_t)(v.n1 - v.n0) * a.G;
-  const uint32_t i0 = (uint32_t)(((uint64_t)items * part) / nparts);
-  const uint32_t i1 = (uint32_t)(((uint64_t)items * (part + 1)) / nparts);
-  const bool pole = t >= a.ntiles_main;
-  const int units = (a.nlev + 1) / 2;
-  const uint32_t rb = a.row_bytes;
-  for (uint32_t item = i0 + (threadIdx.x & 31); item < i1; item += 32) {
-    const uint32_t il = (uint32_t)(((uint64_t)item * a.g_magic) >> a.g_shift);
-    const uint32_t c = item - il * a.G;
-    const int u0 = (int)c, u1 = (int)c + a.G;
-    const bool has1 = u1 < units;
-    const int32_t node = v.n0 + (int32_t)il;
-    const int32_t p0 = lds_s32(v.r + 4u * (uint32_t)node), p1 = lds_s32(v.r + 4u * (uint32_t)node + 4u);
-    const uint32_t colA = v.rows + (uint32_t)u0 * 16u;
-    const uint32_t colB = v.rows + (uint32_t)(has1 ? u1 : u0) * 16u;
-    const float4 A = lds128(colA + il * rb);
-    const float4 B = lds128(colB + il * rb);
-    float r[4];
-    if (!pole) {
-      // pair accumulators (sum of w.x du, sum of w.y dv) per level
-      const f2_t i0p = pk(A.x, A.y), i1p = pk(A.z, A.w), i2p = pk(B.x, B.y), i3p = pk(B.z, B.w);
-      Kahan2<COMP> k0, k1, k2, k3;
-      auto body = [&](const float2 w, const float4 C, const float4 D) {
-        const f2_t w2 = pk(w.x, w.y);
-        k0.add_prod(w2, sub2(pk(C.x, C.y), i0p));
-        k1.add_prod(w2, sub2(pk(C.z, C.w), i1p));
-        k2.add_prod(w2, sub2(pk(D.x, D.y), i2p));
-        k3.add_prod(w2, sub2(pk(D.z, D.w), i3p));
-      };
-      uint32_t pw = v.w + 8u * (uint32_t)p0, pl = v.l + 4u * (uint32_t)p0;
-      int32_t p = p0;
-      for (; p + 1 < p1; p += 2, pw += 16u, pl += 8u) {
-        const float2 w0 = lds64(pw), w1 = lds64(pw + 8u);
-        const uint32_t r0 = lds_u32(pl), r1 = lds_u32(pl + 4u);
-        const float4 C0 = lds128(colA + r0), D0 = lds128(colB + r0);
-        const float4 C1 = lds128(colA + r1), D1 = lds128(colB + r1);
-        const f2_t w20 = pk(w0.x, w0.y), w21 = pk(w1.x, w1.y);
-        k0.add_pair(w20, sub2(pk(C0.x, C0.y), i0p), w21, sub2(pk(C1.x, C1.y), i0p));
-        k1.add_pair(w20, sub2(pk(C0.z, C0.w), i1p), w21, sub2(pk(C1.z, C1.w), i1p));
-        k2.add_pair(w20, sub2(pk(D0.x, D0.y), i2p), w21, sub2(pk(D1.x, D1.y), i2p));
-        k3.add_pair(w20, sub2(pk(D0.z, D0.w), i3p), w21, sub2(pk(D1.z, D1.w), i3p));
-      }
-      if (p < p1) {
-        const uint32_t r0 = lds_u32(pl);
-        body(lds64(pw), lds128(colA + r0), lds128(colB + r0));
-      }
-      const float2 sw = __ldg(a.s32 + node);
-      const f2_t sw2 = pk(sw.x, sw.y);
-      const f2_t vals[4] = {k0.value(), k1.value(), k2.value(), k3.value()};
-      const f2_t self[4] = {i0p, i1p, i2p, i3p};
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const f2_t q = fma2(sw2, self[k], vals[k]);
-        float x, y;
-        upk(q, x, y);
-        r[k] = __fadd_rn(x, y);
-      }
-    } else {
-      const float iu[4] = {A.x, A.z, B.x, B.z}, iv[4] = {A.y, A.w, B.y, B.w};
-      double sacc[4] = {0, 0, 0, 0};
-      for (int32_t p = p0; p < p1; ++p) {
-        const double2 w = __ldg(a.w64 + p);
-        const uint32_t r0 = lds_u32(v.l + 4u * (uint32_t)p);
-        const float4 C = lds128(colA + r0);
-        const float4 D = lds128(colB + r0);
-        const float ju[4] = {C.x, C.z, D.x, D.z}, jv[4] = {C.y, C.w, D.y, D.w};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          sacc[k] = fma(w.x, (double)ju[k] - (double)iu[k], sacc[k]);
-          sacc[k] = fma(w.y, (double)jv[k] - (double)iv[k], sacc[k]);
-        }
-      }
-      const double2 sw = __ldg(a.s64 + node);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        sacc[k] = fma(sw.x, (double)iu[k], sacc[k]);
-        sacc[k] = fma(sw.y, (double)iv[k], sacc[k]);
-        r[k] = (float)sacc[k];
-      }
-    }
-    // levels 2 u0, 2 u0 + 1 from r[0..1], levels 2 u1, 2 u1 + 1 from r[2..3]
-    float *oo = a.out + (int64_t)node * a.out_stride;
-    const int la0 = 2 * u0, la1 = 2 * u1;
-    if (la0 + 1 < a.nlev) __stcs(reinterpret_cast<float2 *>(oo + la0), make_float2(r[0], r[1]));
-    else oo[la0] = r[0];
-    if (has1) {
-      if (la1 + 1 < a.nlev) __stcs(reinterpret_cast<float2 *>(oo + la1), make_float2(r[2], r[3]));
-      else oo[la1] = r[2];
     }
   }
 }
