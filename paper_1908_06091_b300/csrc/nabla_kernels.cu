@@ -124,8 +124,9 @@ int method_upload(nb_method *m) {
   UP(m->d_wgrad32, nullptr, 2 * P);
   UP(m->d_wdiv32, nullptr, 2 * P);
   UP(m->d_wcurl32, nullptr, 2 * P);
-  UP(m->d_sdiv32, nullptr, 2 * V);
-  UP(m->d_scurl32, nullptr, 2 * V);
+  // self weights are staged in even-aligned node pairs: one spare node
+  UP(m->d_sdiv32, nullptr, 2 * V + 4);
+  UP(m->d_scurl32, nullptr, 2 * V + 4);
 #undef UP
   const int threads = 256;
   const int64_t blocks = (V + threads - 1) / threads;

@@ -171,6 +171,8 @@ struct TiledArgs {
   uint32_t copy_bytes; // bytes copied per column: the real data rounded up to 16
   uint32_t gpitch;     // shared-memory pitch of a group of four halo columns
   uint32_t off_w, off_l, off_r;  // stage offsets of the staged weights, offsets, row pointers
+  uint32_t off_s;      // stage offset of the tile's self weights (div / curl; 0 = not staged)
+  uint32_t off_h;      // stage offset of the tile header: first and end node
   uint32_t stage_bytes;
   int nstages;
   int *status;
@@ -192,13 +194,20 @@ __device__ __forceinline__ void issue_tile(const TiledArgs &a, const CUtensorMap
                  rbytes = (uint32_t)(rb - ra) * 4u;
   const uint32_t groups = (H + 3u) >> 2;
   const uint32_t hbase = (n * a.row_bytes + 127u) & ~127u;
+  const int32_t sa = n0 & ~1, sb = (n1 + 1) & ~1;
+  const uint32_t sbytes = a.off_s ? (uint32_t)(sb - sa) * 8u : 0u;
+  if (lane == 0) {
+    // header for the consumers, published by the arrive below
+    asm volatile("st.shared.v2.s32 [%0], {%1, %2};" ::"r"(stage + a.off_h), "r"(n0), "r"(n1) : "memory");
+  }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  if (lane == 0) mbar_expect_tx(bar, body + wbytes + lbytes + rbytes + groups * 4u * a.copy_bytes);
+  if (lane == 0) mbar_expect_tx(bar, body + wbytes + lbytes + rbytes + sbytes + groups * 4u * a.copy_bytes);
   __syncwarp();
   if (lane == 0) bulk_g2s(stage, a.in + (int64_t)n0 * a.in_stride * 4, body, bar);
   if (lane == 1) bulk_g2s(stage + a.off_w, a.w32 + wa, wbytes, bar);
   if (lane == 2) bulk_g2s(stage + a.off_l, a.loff + la, lbytes, bar);
   if (lane == 3) bulk_g2s(stage + a.off_r, a.row_ptr + ra, rbytes, bar);
+  if (lane == 4 && sbytes) bulk_g2s(stage + a.off_s, a.s32 + sa, sbytes, bar);
   for (uint32_t g = lane; g < groups; g += 32) {
     // a short last group repeats its last node (the copy fills the group's slots)
     const int32_t *hp = a.halo + h0;
@@ -247,11 +256,12 @@ __device__ __forceinline__ int32_t lds_s32(uint32_t a) {
 // (wrap-around arithmetic; the sums land inside the stage).
 struct TileView {
   int32_t n0, n1;
-  uint32_t rows, w, l, r;
+  uint32_t rows, w, l, r, s;
   __device__ __forceinline__ TileView(const TiledArgs &a, int t, uint32_t stage) {
-    n0 = __ldg(a.tile_node0 + t);
-    n1 = __ldg(a.tile_node0 + t + 1);
+    n0 = lds_s32(stage + a.off_h);
+    n1 = lds_s32(stage + a.off_h + 4u);
     rows = stage;
+    s = stage + a.off_s - 8u * (uint32_t)(n0 & ~1);
     const int32_t ra = n0 & ~3;
     r = stage + a.off_r - 4u * (uint32_t)ra;
     const int32_t pa = lds_s32(r + 4u * (uint32_t)n0);
@@ -331,7 +341,7 @@ __device__ __forceinline__ void divcurl_tile(const TiledArgs &a, int t, uint32_t
         for (; q + 1 < deg; q += 2) pair((uint32_t)q);
         if (q < deg) single((uint32_t)q);
       }
-      const f2_t sw2 = *reinterpret_cast<const f2_t *>(a.s32 + node);
+      const f2_t sw2 = lds_b64(v.s + 8u * (uint32_t)node);
       const f2_t vals[4] = {k0.value(), k1.value(), k2.value(), k3.value()};
       const f2_t self[4] = {i0p, i1p, i2p, i3p};
 #pragma unroll
@@ -692,8 +702,10 @@ int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, 
   const int ecap = 7 * nmax + 16;
   const uint32_t wsz = up16((uint32_t)(ecap + 2) * 8u), lsz = up16((uint32_t)(ecap + 8) * 4u),
                  rsz = up16((uint32_t)(nmax + 8) * 4u);
-  if (stage_target <= wsz + lsz + rsz + 4096u) return NB_OK;
-  const uint32_t area = ((stage_target - wsz - lsz - rsz) / 128u) * 128u;
+  const uint32_t ssz = op == NB_OP_GRAD ? 0u : up16((uint32_t)(nmax + 2) * 8u), hsz = 16u;
+  const uint32_t meta = wsz + lsz + rsz + ssz + hsz;
+  if (stage_target <= meta + 4096u) return NB_OK;
+  const uint32_t area = ((stage_target - meta) / 128u) * 128u;
   if (area < 24u * row_bytes) return NB_OK;  // columns too tall to stage a useful tile
   int status = NB_OK;
   TilePlan *tp = get_plan(m, area, row_bytes, copy_bytes, nmax, ecap, &status);
@@ -744,7 +756,9 @@ int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, 
   a.off_w = area;
   a.off_l = a.off_w + wsz;
   a.off_r = a.off_l + lsz;
-  a.stage_bytes = (a.off_r + rsz + 127u) & ~127u;
+  a.off_s = ssz ? a.off_r + rsz : 0u;
+  a.off_h = a.off_r + rsz + ssz;
+  a.stage_bytes = (a.off_h + hsz + 127u) & ~127u;
   a.nstages = nstages;
   a.status = nullptr;
   if (const int rc = status_word(&a.status)) return rc;
