@@ -231,6 +231,16 @@ int nb_nabla_divergence(const nb_method *method, const nb_field *uv, const nb_fi
  * uv [V][L][2] -> z [V][L]. */
 int nb_nabla_curl(const nb_method *method, const nb_field *uv, const nb_field *z, void *stream);
 
+/* Divergence and curl of the same wind in one pass: uv [V][L][2] -> d [V][L]
+ * and z [V][L] (Fig. 33 puts both in the one Nabla operator of a Method).
+ * Each output equals, bit for bit, what nb_nabla_divergence and
+ * nb_nabla_curl write for the same input; the fused FP32 pass reads the wind
+ * and the neighbour structure once for both.  d and z must have the same
+ * layout.  Errors as for nb_nabla_divergence, plus NB_ESHAPE if d and z
+ * differ in layout or overlap the wind. */
+int nb_nabla_divcurl(const nb_method *method, const nb_field *uv, const nb_field *d,
+                     const nb_field *z, void *stream);
+
 /* Laplacian = divergence of the gradient: f [V][L] -> lap [V][L].
  * scratch: a [V][L][2] field of f's dtype receiving the intermediate
  * gradient, or NULL to let the library take stream-ordered memory from the

@@ -80,8 +80,8 @@ int dev_free_async(const DevAlloc &a, void *ptr, size_t bytes, void *stream) {
   return e == cudaSuccess ? NB_OK : cuda_fail(e, "cudaFreeAsync");
 }
 
-int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, cudaStream_t st,
-                 bool *handled);
+int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, const nb_field *out2,
+                 cudaStream_t st, bool *handled);
 int device_status(int clear, int *code);
 
 }  // namespace nb
@@ -483,7 +483,7 @@ static int launch_single(nb_method *m, int op, const nb_field *in, const nb_fiel
                          cudaStream_t st) {
   if (m->kernel_variant != NB_KERNEL_DIRECT) {
     bool handled = false;
-    const int rc = launch_tiled(m, op, in, out, st, &handled);
+    const int rc = launch_tiled(m, op, in, out, nullptr, st, &handled);
     if (handled || rc != NB_OK) return rc;
   }
   return launch_direct(m, op, in, out, st);
@@ -546,6 +546,35 @@ int nb_nabla_divergence(const nb_method *m, const nb_field *uv, const nb_field *
 
 int nb_nabla_curl(const nb_method *m, const nb_field *uv, const nb_field *z, void *stream) {
   return nb_nabla_apply(m, NB_OP_CURL, uv, z, nullptr, stream);
+}
+
+int nb_nabla_divcurl(const nb_method *m, const nb_field *uv, const nb_field *d, const nb_field *z,
+                     void *stream) {
+  int st = nb::validate(m, NB_OP_DIV, uv, d, nullptr);
+  if (st != NB_OK) return st;
+  if ((st = nb::validate(m, NB_OP_CURL, uv, z, nullptr)) != NB_OK) return st;
+  NB_REQUIRE(d->node_stride == z->node_stride && d->lev_stride == z->lev_stride, NB_ESHAPE,
+             "nb_nabla_divcurl: d and z must have the same layout");
+  {
+    const int64_t elem = d->dtype == NB_F64 ? 8 : 4;
+    const char *d0 = static_cast<const char *>(d->data), *z0 = static_cast<const char *>(z->data);
+    const int64_t span = (d->nnodes - 1) * d->node_stride * elem + (int64_t)d->nlev * elem;
+    NB_REQUIRE(d->nnodes == 0 || d0 + span <= z0 || z0 + span <= d0, NB_ESHAPE,
+               "nb_nabla_divcurl: d and z overlap");
+  }
+  NB_GUARD_BEGIN
+  nb_method *mm = const_cast<nb_method *>(m);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (mm->mesh->V == 0) return NB_OK;
+  if (mm->kernel_variant != NB_KERNEL_DIRECT) {
+    bool handled = false;
+    const int rc = nb::launch_tiled(mm, NB_OP_DIV, uv, d, z, s, &handled);
+    if (handled || rc != NB_OK) return rc;
+  }
+  st = nb::launch_op(mm, NB_OP_DIV, uv, d, nullptr, stream);
+  if (st == NB_OK) st = nb::launch_op(mm, NB_OP_CURL, uv, z, nullptr, stream);
+  return st;
+  NB_GUARD_END
 }
 
 int nb_nabla_laplacian(const nb_method *m, const nb_field *f, const nb_field *lap,

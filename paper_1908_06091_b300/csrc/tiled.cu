@@ -29,8 +29,8 @@ namespace nb {
 // device status word: 0 = ok, otherwise an NB_* code (first error wins)
 __device__ int g_device_status = 0;
 
-int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, cudaStream_t st,
-                 bool *handled);
+int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, const nb_field *out2,
+                 cudaStream_t st, bool *handled);
 
 // ------------------------------------------------------------ PTX helpers
 
@@ -143,6 +143,17 @@ struct Kahan2 {
       s = fma2(w1, d1, fma2(w0, d0, s));
     }
   }
+  // three edge terms as one summand (the six-neighbour path: two per node)
+  __device__ __forceinline__ void add_triple(f2_t w0, f2_t d0, f2_t w1, f2_t d1, f2_t w2, f2_t d2) {
+    if (COMP) {
+      const f2_t y = fma2(w2, d2, fma2(w1, d1, fma2(w0, d0, nc)));
+      const f2_t t = add2(s, y);
+      nc = sub2(y, sub2(t, s));
+      s = t;
+    } else {
+      s = fma2(w2, d2, fma2(w1, d1, fma2(w0, d0, s)));
+    }
+  }
   __device__ __forceinline__ f2_t value() const { return COMP ? add2(s, nc) : s; }
 };
 
@@ -159,6 +170,11 @@ struct TiledArgs {
   const double2 *w64;
   const float2 *s32;
   const double2 *s64;
+  const float2 *w32b;   // fused div+curl: the curl weights (else unused)
+  const double2 *w64b;
+  const float2 *s32b;
+  const double2 *s64b;
+  float *out2;          // fused div+curl: the curl output (same strides as out)
   const char *in;
   uint32_t row_bytes;  // bytes of one own column (in_stride * 4)
   int64_t in_stride;   // elements
@@ -172,6 +188,7 @@ struct TiledArgs {
   uint32_t gpitch;     // shared-memory pitch of a group of four halo columns
   uint32_t off_w, off_l, off_r;  // stage offsets of the staged weights, offsets, row pointers
   uint32_t off_s;      // stage offset of the tile's self weights (div / curl; 0 = not staged)
+  uint32_t off_w2, off_s2;  // fused div+curl: stage offsets of the curl weights (0 = not staged)
   uint32_t off_h;      // stage offset of the tile header: first and end node
   uint32_t stage_bytes;
   int nstages;
@@ -196,18 +213,22 @@ __device__ __forceinline__ void issue_tile(const TiledArgs &a, const CUtensorMap
   const uint32_t hbase = (n * a.row_bytes + 127u) & ~127u;
   const int32_t sa = n0 & ~1, sb = (n1 + 1) & ~1;
   const uint32_t sbytes = a.off_s ? (uint32_t)(sb - sa) * 8u : 0u;
+  const uint32_t w2bytes = a.off_w2 ? wbytes : 0u, s2bytes = a.off_w2 ? sbytes : 0u;
   if (lane == 0) {
     // header for the consumers, published by the arrive below
     asm volatile("st.shared.v2.s32 [%0], {%1, %2};" ::"r"(stage + a.off_h), "r"(n0), "r"(n1) : "memory");
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  if (lane == 0) mbar_expect_tx(bar, body + wbytes + lbytes + rbytes + sbytes + groups * 4u * a.copy_bytes);
+  if (lane == 0)
+    mbar_expect_tx(bar, body + wbytes + lbytes + rbytes + sbytes + w2bytes + s2bytes + groups * 4u * a.copy_bytes);
   __syncwarp();
   if (lane == 0) bulk_g2s(stage, a.in + (int64_t)n0 * a.in_stride * 4, body, bar);
   if (lane == 1) bulk_g2s(stage + a.off_w, a.w32 + wa, wbytes, bar);
   if (lane == 2) bulk_g2s(stage + a.off_l, a.loff + la, lbytes, bar);
   if (lane == 3) bulk_g2s(stage + a.off_r, a.row_ptr + ra, rbytes, bar);
   if (lane == 4 && sbytes) bulk_g2s(stage + a.off_s, a.s32 + sa, sbytes, bar);
+  if (lane == 5 && w2bytes) bulk_g2s(stage + a.off_w2, a.w32b + wa, w2bytes, bar);
+  if (lane == 6 && s2bytes) bulk_g2s(stage + a.off_s2, a.s32b + sa, s2bytes, bar);
   for (uint32_t g = lane; g < groups; g += 32) {
     // a short last group repeats its last node (the copy fills the group's slots)
     const int32_t *hp = a.halo + h0;
@@ -264,10 +285,11 @@ struct TileView {
     s = stage + a.off_s - 8u * (uint32_t)(n0 & ~1);
     const int32_t ra = n0 & ~3;
     r = stage + a.off_r - 4u * (uint32_t)ra;
-    const int32_t pa = lds_s32(r + 4u * (uint32_t)n0);
+    pa = lds_s32(r + 4u * (uint32_t)n0);
     w = stage + a.off_w - 8u * (uint32_t)(pa & ~1);
     l = stage + a.off_l - 4u * (uint32_t)(pa & ~3);
   }
+  int32_t pa;  // CSR index of the tile's first entry
 };
 
 // Consumer side.  A warp takes items [i0, i1) of tile t, one per lane,
@@ -279,8 +301,12 @@ struct TileView {
 //
 // div / curl.  A staged (u, v) column is a sequence of 16-byte units of two
 // levels each; item c of a node takes units c and c + G, so that every
-// shared-memory load of a warp reads consecutive 16-byte words.
-template <bool COMP>
+// shared-memory load of a warp reads consecutive 16-byte words.  FUSED
+// evaluates div and curl of the same wind in one pass: the staged columns,
+// offsets and differences are shared, each operator keeps its own weights
+// and accumulators, and each output gets exactly the arithmetic of its
+// single-operator pass.
+template <bool COMP, bool FUSED>
 __device__ __forceinline__ void divcurl_tile(const TiledArgs &a, int t, uint32_t stage, int part,
                                              int nparts) {
   const TileView v(a, t, stage);
@@ -291,6 +317,9 @@ __device__ __forceinline__ void divcurl_tile(const TiledArgs &a, int t, uint32_t
   const int units = (a.nlev + 1) / 2;
   const uint32_t rb = a.row_bytes;
   const uint32_t g16 = 16u * (uint32_t)a.G;
+  // second weight set and self weights (curl of the fused pass)
+  const uint32_t w2base = stage + a.off_w2 - 8u * (uint32_t)(v.pa & ~1);
+  const uint32_t s2base = stage + a.off_s2 - 8u * (uint32_t)(v.n0 & ~1);
   for (uint32_t item = i0 + (threadIdx.x & 31); item < i1; item += 32) {
     const uint32_t il = (uint32_t)(((uint64_t)item * a.g_magic) >> a.g_shift);
     const uint32_t c = item - il * a.G;
@@ -300,90 +329,145 @@ __device__ __forceinline__ void divcurl_tile(const TiledArgs &a, int t, uint32_t
     const int32_t p0 = lds_s32(v.r + 4u * (uint32_t)node), p1 = lds_s32(v.r + 4u * (uint32_t)node + 4u);
     const uint32_t colA = v.rows + (uint32_t)u0 * 16u;
     const uint32_t colB = colA + (has1 ? g16 : 0u);
-    float r[4];
+    float r[4], z[4];
     if (!pole) {
       f2_t i0p, i1p, i2p, i3p;
       lds2x64(colA + il * rb, i0p, i1p);
       lds2x64(colB + il * rb, i2p, i3p);
-      Kahan2<COMP> k0, k1, k2, k3;
-      const uint32_t pw = v.w + 8u * (uint32_t)p0, pl = v.l + 4u * (uint32_t)p0;
-      auto pair = [&](uint32_t q) {
-        const f2_t w20 = lds_b64(pw + 8u * q), w21 = lds_b64(pw + 8u * q + 8u);
-        const uint32_t r0 = lds_u32(pl + 4u * q), r1 = lds_u32(pl + 4u * q + 4u);
-        f2_t c00, c01, d00, d01, c10, c11, d10, d11;
-        lds2x64(colA + r0, c00, c01);
-        lds2x64(colB + r0, d00, d01);
-        lds2x64(colA + r1, c10, c11);
-        lds2x64(colB + r1, d10, d11);
-        k0.add_pair(w20, sub2(c00, i0p), w21, sub2(c10, i0p));
-        k1.add_pair(w20, sub2(c01, i1p), w21, sub2(c11, i1p));
-        k2.add_pair(w20, sub2(d00, i2p), w21, sub2(d10, i2p));
-        k3.add_pair(w20, sub2(d01, i3p), w21, sub2(d11, i3p));
+      Kahan2<COMP> k0, k1, k2, k3, q0, q1, q2, q3;
+      const uint32_t pw = v.w + 8u * (uint32_t)p0, pw2 = w2base + 8u * (uint32_t)p0;
+      const uint32_t pl = v.l + 4u * (uint32_t)p0;
+      // differences of neighbour entry e: units (c, c + G) minus the node's own
+      auto diffs = [&](uint32_t e, f2_t (&d)[4]) {
+        const uint32_t off = lds_u32(pl + 4u * e);
+        f2_t x0, x1, y0, y1;
+        lds2x64(colA + off, x0, x1);
+        lds2x64(colB + off, y0, y1);
+        d[0] = sub2(x0, i0p);
+        d[1] = sub2(x1, i1p);
+        d[2] = sub2(y0, i2p);
+        d[3] = sub2(y1, i3p);
       };
-      auto single = [&](uint32_t q) {
-        const f2_t w2 = lds_b64(pw + 8u * q);
-        const uint32_t r0 = lds_u32(pl + 4u * q);
-        f2_t c00, c01, d00, d01;
-        lds2x64(colA + r0, c00, c01);
-        lds2x64(colB + r0, d00, d01);
-        k0.add_prod(w2, sub2(c00, i0p));
-        k1.add_prod(w2, sub2(c01, i1p));
-        k2.add_prod(w2, sub2(d00, i2p));
-        k3.add_prod(w2, sub2(d01, i3p));
+      auto triple = [&](uint32_t e) {
+        f2_t d0[4], d1[4], d2[4];
+        diffs(e, d0);
+        diffs(e + 1u, d1);
+        diffs(e + 2u, d2);
+        const f2_t w0 = lds_b64(pw + 8u * e), w1 = lds_b64(pw + 8u * e + 8u), w2 = lds_b64(pw + 8u * e + 16u);
+        k0.add_triple(w0, d0[0], w1, d1[0], w2, d2[0]);
+        k1.add_triple(w0, d0[1], w1, d1[1], w2, d2[1]);
+        k2.add_triple(w0, d0[2], w1, d1[2], w2, d2[2]);
+        k3.add_triple(w0, d0[3], w1, d1[3], w2, d2[3]);
+        if (FUSED) {
+          const f2_t x0 = lds_b64(pw2 + 8u * e), x1 = lds_b64(pw2 + 8u * e + 8u), x2 = lds_b64(pw2 + 8u * e + 16u);
+          q0.add_triple(x0, d0[0], x1, d1[0], x2, d2[0]);
+          q1.add_triple(x0, d0[1], x1, d1[1], x2, d2[1]);
+          q2.add_triple(x0, d0[2], x1, d1[2], x2, d2[2]);
+          q3.add_triple(x0, d0[3], x1, d1[3], x2, d2[3]);
+        }
+      };
+      auto pair = [&](uint32_t e) {
+        f2_t d0[4], d1[4];
+        diffs(e, d0);
+        diffs(e + 1u, d1);
+        const f2_t w0 = lds_b64(pw + 8u * e), w1 = lds_b64(pw + 8u * e + 8u);
+        k0.add_pair(w0, d0[0], w1, d1[0]);
+        k1.add_pair(w0, d0[1], w1, d1[1]);
+        k2.add_pair(w0, d0[2], w1, d1[2]);
+        k3.add_pair(w0, d0[3], w1, d1[3]);
+        if (FUSED) {
+          const f2_t x0 = lds_b64(pw2 + 8u * e), x1 = lds_b64(pw2 + 8u * e + 8u);
+          q0.add_pair(x0, d0[0], x1, d1[0]);
+          q1.add_pair(x0, d0[1], x1, d1[1]);
+          q2.add_pair(x0, d0[2], x1, d1[2]);
+          q3.add_pair(x0, d0[3], x1, d1[3]);
+        }
+      };
+      auto single = [&](uint32_t e) {
+        f2_t d0[4];
+        diffs(e, d0);
+        const f2_t w0 = lds_b64(pw + 8u * e);
+        k0.add_prod(w0, d0[0]);
+        k1.add_prod(w0, d0[1]);
+        k2.add_prod(w0, d0[2]);
+        k3.add_prod(w0, d0[3]);
+        if (FUSED) {
+          const f2_t x0 = lds_b64(pw2 + 8u * e);
+          q0.add_prod(x0, d0[0]);
+          q1.add_prod(x0, d0[1]);
+          q2.add_prod(x0, d0[2]);
+          q3.add_prod(x0, d0[3]);
+        }
       };
       const int deg = p1 - p0;
       if (deg == 6) {
-        pair(0);
-        pair(2);
-        pair(4);
+        triple(0);
+        triple(3);
       } else {
-        int q = 0;
-        for (; q + 1 < deg; q += 2) pair((uint32_t)q);
-        if (q < deg) single((uint32_t)q);
+        int e = 0;
+        for (; e + 1 < deg; e += 2) pair((uint32_t)e);
+        if (e < deg) single((uint32_t)e);
       }
-      const f2_t sw2 = lds_b64(v.s + 8u * (uint32_t)node);
-      const f2_t vals[4] = {k0.value(), k1.value(), k2.value(), k3.value()};
       const f2_t self[4] = {i0p, i1p, i2p, i3p};
+      {
+        const f2_t sw = lds_b64(v.s + 8u * (uint32_t)node);
+        const f2_t vals[4] = {k0.value(), k1.value(), k2.value(), k3.value()};
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const f2_t q = fma2(sw2, self[k], vals[k]);
-        float x, y;
-        upk(q, x, y);
-        r[k] = __fadd_rn(x, y);
+        for (int k = 0; k < 4; ++k) {
+          float x, y;
+          upk(fma2(sw, self[k], vals[k]), x, y);
+          r[k] = __fadd_rn(x, y);
+        }
+      }
+      if (FUSED) {
+        const f2_t sw = lds_b64(s2base + 8u * (uint32_t)node);
+        const f2_t vals[4] = {q0.value(), q1.value(), q2.value(), q3.value()};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          float x, y;
+          upk(fma2(sw, self[k], vals[k]), x, y);
+          z[k] = __fadd_rn(x, y);
+        }
       }
     } else {
       const float4 A = lds128(colA + il * rb);
       const float4 B = lds128(colB + il * rb);
       const float iu[4] = {A.x, A.z, B.x, B.z}, iv[4] = {A.y, A.w, B.y, B.w};
-      double sacc[4] = {0, 0, 0, 0};
+      double sacc[4] = {0, 0, 0, 0}, zacc[4] = {0, 0, 0, 0};
       for (int32_t p = p0; p < p1; ++p) {
         const double2 w = __ldg(a.w64 + p);
+        const double2 x = FUSED ? __ldg(a.w64b + p) : w;
         const uint32_t r0 = lds_u32(v.l + 4u * (uint32_t)p);
         const float4 C = lds128(colA + r0);
         const float4 D = lds128(colB + r0);
         const float ju[4] = {C.x, C.z, D.x, D.z}, jv[4] = {C.y, C.w, D.y, D.w};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          sacc[k] = fma(w.x, (double)ju[k] - (double)iu[k], sacc[k]);
-          sacc[k] = fma(w.y, (double)jv[k] - (double)iv[k], sacc[k]);
+          const double du = (double)ju[k] - (double)iu[k], dv = (double)jv[k] - (double)iv[k];
+          sacc[k] = fma(w.y, dv, fma(w.x, du, sacc[k]));
+          if (FUSED) zacc[k] = fma(x.y, dv, fma(x.x, du, zacc[k]));
         }
       }
       const double2 sw = __ldg(a.s64 + node);
+      const double2 sx = FUSED ? __ldg(a.s64b + node) : sw;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        sacc[k] = fma(sw.x, (double)iu[k], sacc[k]);
-        sacc[k] = fma(sw.y, (double)iv[k], sacc[k]);
-        r[k] = (float)sacc[k];
+        r[k] = (float)fma(sw.y, (double)iv[k], fma(sw.x, (double)iu[k], sacc[k]));
+        if (FUSED) z[k] = (float)fma(sx.y, (double)iv[k], fma(sx.x, (double)iu[k], zacc[k]));
       }
     }
-    float *oo = a.out + (int64_t)node * a.out_stride;
-    const int la0 = 2 * u0, la1 = 2 * u1;
-    if (la0 + 1 < a.nlev) __stcs(reinterpret_cast<float2 *>(oo + la0), make_float2(r[0], r[1]));
-    else oo[la0] = r[0];
-    if (has1) {
-      if (la1 + 1 < a.nlev) __stcs(reinterpret_cast<float2 *>(oo + la1), make_float2(r[2], r[3]));
-      else oo[la1] = r[2];
-    }
+    // levels 2 u0, 2 u0 + 1 from r[0..1], levels 2 u1, 2 u1 + 1 from r[2..3]
+    auto put = [&](float *oo, const float (&o)[4]) {
+      const int la0 = 2 * u0, la1 = 2 * u1;
+      if (la0 + 1 < a.nlev) __stcs(reinterpret_cast<float2 *>(oo + la0), make_float2(o[0], o[1]));
+      else oo[la0] = o[0];
+      if (has1) {
+        if (la1 + 1 < a.nlev) __stcs(reinterpret_cast<float2 *>(oo + la1), make_float2(o[2], o[3]));
+        else oo[la1] = o[2];
+      }
+    };
+    put(a.out + (int64_t)node * a.out_stride, r);
+    if (FUSED) put(a.out2 + (int64_t)node * a.out_stride, z);
   }
 }
 
@@ -426,6 +510,24 @@ __device__ __forceinline__ void grad_tile(const TiledArgs &a, int t, uint32_t st
         ay01.add_pair(wy0, a01, wy1, b01);
         ay23.add_pair(wy0, a23, wy1, b23);
       };
+      auto triple = [&](uint32_t q) {
+        const float2 w0 = lds64(pw + 8u * q), w1 = lds64(pw + 8u * q + 8u), w2 = lds64(pw + 8u * q + 16u);
+        const uint32_t r0 = lds_u32(pl + 4u * q), r1 = lds_u32(pl + 4u * q + 4u), r2 = lds_u32(pl + 4u * q + 8u);
+        f2_t f001, f023, f101, f123, f201, f223;
+        lds2x64(col + r0, f001, f023);
+        lds2x64(col + r1, f101, f123);
+        lds2x64(col + r2, f201, f223);
+        const f2_t a01 = sub2(f001, fi01), a23 = sub2(f023, fi23);
+        const f2_t b01 = sub2(f101, fi01), b23 = sub2(f123, fi23);
+        const f2_t e01 = sub2(f201, fi01), e23 = sub2(f223, fi23);
+        const f2_t wx0 = pk(w0.x, w0.x), wy0 = pk(w0.y, w0.y);
+        const f2_t wx1 = pk(w1.x, w1.x), wy1 = pk(w1.y, w1.y);
+        const f2_t wx2 = pk(w2.x, w2.x), wy2 = pk(w2.y, w2.y);
+        ax01.add_triple(wx0, a01, wx1, b01, wx2, e01);
+        ax23.add_triple(wx0, a23, wx1, b23, wx2, e23);
+        ay01.add_triple(wy0, a01, wy1, b01, wy2, e01);
+        ay23.add_triple(wy0, a23, wy1, b23, wy2, e23);
+      };
       auto single = [&](uint32_t q) {
         const float2 w = lds64(pw + 8u * q);
         f2_t f001, f023;
@@ -439,9 +541,8 @@ __device__ __forceinline__ void grad_tile(const TiledArgs &a, int t, uint32_t st
       };
       const int deg = p1 - p0;
       if (deg == 6) {
-        pair(0);
-        pair(2);
-        pair(4);
+        triple(0);
+        triple(3);
       } else {
         int q = 0;
         for (; q + 1 < deg; q += 2) pair((uint32_t)q);
@@ -548,7 +649,8 @@ __global__ void __launch_bounds__(kStagedThreads, 1) staged_f32(const TiledArgs 
     }
     const uint32_t rows = stage0 + (uint32_t)s * a.stage_bytes;
     if (OP == 0) grad_tile<COMP>(a, t, rows, warp, kConsumerWarps);
-    else divcurl_tile<COMP>(a, t, rows, warp, kConsumerWarps);
+    else if (OP == 1) divcurl_tile<COMP, false>(a, t, rows, warp, kConsumerWarps);
+    else divcurl_tile<COMP, true>(a, t, rows, warp, kConsumerWarps);
     __syncwarp();
     if (lane == 0) mbar_arrive(empty0 + 8 * s);
   }
@@ -668,12 +770,17 @@ static int status_word(int **out) {
   return NB_OK;
 }
 
-int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, cudaStream_t st,
-                 bool *handled) {
+// out2 != nullptr (op == NB_OP_DIV): fused pass writing div to out and curl
+// to out2.
+int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, const nb_field *out2,
+                 cudaStream_t st, bool *handled) {
   *handled = false;
   if (in->dtype != NB_F32) return NB_OK;
-  const bool aligned = (((uintptr_t)in->data | (uintptr_t)out->data) & 15u) == 0 &&
-                       in->node_stride % 4 == 0 && out->node_stride % 4 == 0;
+  const bool fused = out2 != nullptr;
+  if (fused && (op != NB_OP_DIV || out2->node_stride != out->node_stride || out2->dtype != NB_F32))
+    return NB_OK;
+  const uintptr_t addr_bits = (uintptr_t)in->data | (uintptr_t)out->data | (fused ? (uintptr_t)out2->data : 0u);
+  const bool aligned = (addr_bits & 15u) == 0 && in->node_stride % 4 == 0 && out->node_stride % 4 == 0;
   // short columns leave most staged items idle: the direct kernels do better
   if (!aligned || in->nlev < 16) return NB_OK;
   const uint32_t row_bytes = (uint32_t)(in->node_stride * 4);
@@ -703,7 +810,8 @@ int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, 
   const uint32_t wsz = up16((uint32_t)(ecap + 2) * 8u), lsz = up16((uint32_t)(ecap + 8) * 4u),
                  rsz = up16((uint32_t)(nmax + 8) * 4u);
   const uint32_t ssz = op == NB_OP_GRAD ? 0u : up16((uint32_t)(nmax + 2) * 8u), hsz = 16u;
-  const uint32_t meta = wsz + lsz + rsz + ssz + hsz;
+  const uint32_t w2sz = fused ? wsz : 0u, s2sz = fused ? ssz : 0u;
+  const uint32_t meta = wsz + lsz + rsz + ssz + w2sz + s2sz + hsz;
   if (stage_target <= meta + 4096u) return NB_OK;
   const uint32_t area = ((stage_target - meta) / 128u) * 128u;
   if (area < 24u * row_bytes) return NB_OK;  // columns too tall to stage a useful tile
@@ -743,6 +851,11 @@ int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, 
   a.w64 = reinterpret_cast<const double2 *>(g ? m->d_wgrad64 : op == NB_OP_DIV ? m->d_wdiv64 : m->d_wcurl64);
   a.s32 = reinterpret_cast<const float2 *>(op == NB_OP_CURL ? m->d_scurl32 : m->d_sdiv32);
   a.s64 = reinterpret_cast<const double2 *>(op == NB_OP_CURL ? m->d_scurl64 : m->d_sdiv64);
+  a.w32b = fused ? reinterpret_cast<const float2 *>(m->d_wcurl32) : nullptr;
+  a.w64b = fused ? reinterpret_cast<const double2 *>(m->d_wcurl64) : nullptr;
+  a.s32b = fused ? reinterpret_cast<const float2 *>(m->d_scurl32) : nullptr;
+  a.s64b = fused ? reinterpret_cast<const double2 *>(m->d_scurl64) : nullptr;
+  a.out2 = fused ? static_cast<float *>(out2->data) : nullptr;
   a.in = static_cast<const char *>(in->data);
   a.row_bytes = row_bytes;
   a.in_stride = in->node_stride;
@@ -757,7 +870,9 @@ int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, 
   a.off_l = a.off_w + wsz;
   a.off_r = a.off_l + lsz;
   a.off_s = ssz ? a.off_r + rsz : 0u;
-  a.off_h = a.off_r + rsz + ssz;
+  a.off_w2 = fused ? a.off_r + rsz + ssz : 0u;
+  a.off_s2 = fused ? a.off_w2 + w2sz : 0u;
+  a.off_h = a.off_r + rsz + ssz + w2sz + s2sz;
   a.stage_bytes = (a.off_h + hsz + 127u) & ~127u;
   a.nstages = nstages;
   a.status = nullptr;
@@ -772,6 +887,8 @@ int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, 
   *handled = true;
   const bool comp = m->compensated != 0;
   if (g) return comp ? launch_staged_t<0, true>(a, map, grid, smem, st) : launch_staged_t<0, false>(a, map, grid, smem, st);
+  if (fused)
+    return comp ? launch_staged_t<2, true>(a, map, grid, smem, st) : launch_staged_t<2, false>(a, map, grid, smem, st);
   return comp ? launch_staged_t<1, true>(a, map, grid, smem, st) : launch_staged_t<1, false>(a, map, grid, smem, st);
 }
 

@@ -110,6 +110,7 @@ SIGNATURES = {
     "nb_nabla_divergence": [_P, _FP, _FP, _P],
     "nb_nabla_curl": [_P, _FP, _FP, _P],
     "nb_nabla_laplacian": [_P, _FP, _FP, _FP, _P],
+    "nb_nabla_divcurl": [_P, _FP, _FP, _FP, _P],
     "nb_nabla_apply": [_P, _I, _FP, _FP, _FP, _P],
     "nb_nabla_laplacian_noalloc": [_P, _FP, _FP, _P],
     "nb_nabla_apply_host": [_P, _I, _P, _P, _FP, _FP, _FP, _P],
@@ -400,6 +401,13 @@ def curl(method, uv, z, stream=None):
 
 def laplacian(method, f, lap, scratch=None, stream=None):
     return apply(method, OP_LAP, f, lap, scratch=scratch, stream=stream)
+
+
+def divcurl(method, uv, d, z, stream=None):
+    """Divergence into d and curl into z of one wind, in one pass."""
+    fi, fd, fz = field_view(uv, 2), field_view(d, 1), field_view(z, 1)
+    check(lib().nb_nabla_divcurl(method.handle, ctypes.byref(fi), ctypes.byref(fd), ctypes.byref(fz),
+                                 ctypes.c_void_p(_stream(stream))))
 
 
 class Batch(_Handle):

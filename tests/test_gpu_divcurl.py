@@ -1,0 +1,75 @@
+"""Fused divergence + curl (nb_nabla_divcurl): each output equals the
+single-operator pass bit for bit, and therefore meets the oracle gate; the
+call checks d and z before any launch."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from paper_1908_06091_b300 import nabla
+from gpu_helpers import inputs, oracle_mesh, oracle_op, product, rel_l2, run_op, to_device, to_grid
+
+pytestmark = pytest.mark.gpu
+
+TOL = {torch.float64: 1e-12, torch.float32: 1e-5}
+
+
+def _fused(meth, fs, uvd):
+    d = fs.create_field(fill=float("nan"))
+    z = fs.create_field(fill=float("nan"))
+    nabla.divcurl(meth, uvd, d, z)
+    torch.cuda.synchronize()
+    assert nabla.device_status() == 0
+    return d, z
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64], ids=["f32", "f64"])
+@pytest.mark.parametrize("N,nlev", [(32, 137), (32, 7), (48, 37), (16, 16), (16, 21)])
+def test_fused_outputs_equal_single_operator_passes(N, nlev, dtype):
+    g, m, meth = product(N)
+    om = oracle_mesh(N)
+    _, uv = inputs(om, nlev, 10, dtype)
+    fs = nabla.NodeColumns(meth, nlev, dtype)
+    uvd = to_device(fs, uv, m.permutation(), 2)
+    d, z = _fused(meth, fs, uvd)
+    d1, z1 = run_op(meth, fs, "div", uvd), run_op(meth, fs, "curl", uvd)
+    lv = slice(0, nlev)
+    assert torch.equal(d[:, lv], d1[:, lv]) and torch.equal(z[:, lv], z1[:, lv])
+    perm = m.permutation()
+    for out, op in ((d, "div"), (z, "curl")):
+        ref = oracle_op(om, op, uv.astype(np.float64))
+        assert rel_l2(to_grid(out, perm), ref) <= TOL[dtype], op
+
+
+def test_fused_o640_137_levels_meets_the_gate():
+    N, nlev = 640, 137
+    g, m, meth = product(N)
+    om = oracle_mesh(N)
+    _, uv = inputs(om, nlev, 40, torch.float32)
+    fs = nabla.NodeColumns(meth, nlev, torch.float32)
+    perm = m.permutation()
+    d, z = _fused(meth, fs, to_device(fs, uv, perm, 2))
+    for out, op in ((d, "div"), (z, "curl")):
+        ref = oracle_op(om, op, uv.astype(np.float64))
+        assert rel_l2(to_grid(out, perm), ref) <= TOL[torch.float32], op
+
+
+def test_fused_call_checks_outputs_before_any_launch():
+    g, m, meth = product(16)
+    fs = nabla.NodeColumns(meth, 20, torch.float32)
+    uv = fs.create_field(nvar=2, fill=1.0)
+    d = fs.create_field(fill=0.0)
+    L = nabla.lib()
+    before = nabla.launch_count()
+    fu, fd = nabla.field_view(uv, 2), nabla.field_view(d, 1)
+    # z = d: outputs overlap
+    assert L.nb_nabla_divcurl(meth.handle, ctypes.byref(fu), ctypes.byref(fd), ctypes.byref(fd),
+                              None) == nabla.NB_ESHAPE
+    # z with another node stride
+    z = torch.zeros((m.V, 24), dtype=torch.float32, device="cuda")
+    fz = nabla.field_view(z[:, :20], 1)
+    assert L.nb_nabla_divcurl(meth.handle, ctypes.byref(fu), ctypes.byref(fd), ctypes.byref(fz),
+                              None) == nabla.NB_ESHAPE
+    assert nabla.launch_count() == before
+    assert torch.count_nonzero(d).item() == 0
