@@ -435,6 +435,8 @@ def bench_batched(a, nabla, synth, stream):
     t_graph = ev[0].elapsed_time(ev[1]) / reps
 
     def single_sum(items):
+        """Sum of the single operations' own kernel times, and the time of
+        the whole sequence of single calls on the stream (launch gaps in)."""
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in items]
         with torch.cuda.stream(stream):
             for (op, meth, xin, out) in items:  # warm
@@ -444,16 +446,21 @@ def bench_batched(a, nabla, synth, stream):
                 nabla.apply(meth, op, xin, out, stream=stream)
                 e1.record(stream)
         stream.synchronize()
-        return sum(e0.elapsed_time(e1) for e0, e1 in evs)
+        return sum(e0.elapsed_time(e1) for e0, e1 in evs), evs[0][0].elapsed_time(evs[-1][1])
 
-    t_single = single_sum(items32)
-    t_f64 = single_sum(items64)
+    t_single, t_seq = single_sum(items32)
+    t_f64, _ = single_sum(items64)
     info = b.info()
+    staged = sum(1 for v in info["levels_per_block"] if v == 0)
     return {"workload": f"{a.batch_fields} fields, grids O48/O96/O200/O400, levels {{1,37,91,137}}, "
-                        "ops uniform, SH degree<=30, FP32, one persistent launch per phase in a CUDA graph",
+                        "ops uniform, SH degree<=30, FP32; one CUDA graph: persistent launches for "
+                        "small items, staged launches for large ones (tuned routes)",
             "node_levels": int(nl), "graph_ms": round(t_graph, 4),
             "value": round(nl / (t_graph * 1e-3) / 1e9, 2), "unit": "Gnode-levels/s",
+            "staged_route_items": staged,
             "single_op_sum_ms": round(t_single, 4),
+            "single_op_sequence_ms": round(t_seq, 4),
+            "speedup_vs_single_op_sequence": round(t_seq / t_graph, 3),
             "single_op_value": round(nl / (t_single * 1e-3) / 1e9, 2),
             "fp64_single_op_sum_ms": round(t_f64, 4),
             "fp64_value": round(nl / (t_f64 * 1e-3) / 1e9, 2),

@@ -281,15 +281,21 @@ int nb_nabla_apply_host(const nb_method *method, int op, const void *host_in, vo
 
 /* --------------------------------------------------------------- batching
  * Many operations on fields of different grids and level counts in one
- * persistent launch, captured once in a CUDA graph and replayed (the batching
- * pattern named for this hot path; the paper groups all operators in one
- * Nabla, Sec. 4.7 Fig. 33).  Each item is cut into work units of
- * (nodes per warp x 8 warps x rounds) nodes by (levels per block) levels;
- * the grid takes units from an atomic counter.  The per-(node, level)
- * arithmetic equals the direct kernels', so a batched result is bitwise equal
- * to the same operation run alone with nb_method_set_kernel(m,
- * NB_KERNEL_DIRECT, 0).  Laplacian items use batch-owned scratch and a second
- * phase.  Field memory stays caller-owned and must outlive the batch. */
+ * CUDA graph, captured once and replayed (the batching pattern named for
+ * this hot path; the paper groups all operators in one Nabla, Sec. 4.7
+ * Fig. 33).  Each item takes one of two routes:
+ *   - the persistent kernel: the item is cut into work units of (nodes per
+ *     warp x 8 warps x rounds) nodes by (levels per block) levels and one
+ *     persistent launch per phase takes units of all such items from an
+ *     atomic counter.  Its per-(node, level) arithmetic equals the direct
+ *     kernels', so the result is bitwise equal to the operation run alone
+ *     with nb_method_set_kernel(m, NB_KERNEL_DIRECT, 0);
+ *   - the staged route (FP32, 16-byte aligned columns of >= 16 levels): the
+ *     item gets its own shared-memory staged launch(es) inside the graph, so
+ *     the result is bitwise equal to the operation run alone with the default
+ *     kernel choice.
+ * Laplacian items use batch-owned scratch (a second phase on the persistent
+ * route).  Field memory stays caller-owned and must outlive the batch. */
 typedef struct nb_batch_item {
   int32_t op;              /* nb_op */
   int32_t reserved;        /* zero */
@@ -299,17 +305,20 @@ typedef struct nb_batch_item {
 } nb_batch_item;
 
 /* Validate the items (same rules as nb_nabla_apply), allocate the work tables
- * and Laplacian scratch on the current device, take levels-per-block and
- * nodes-per-warp from the tuned table (else a size heuristic).
+ * and Laplacian scratch on the current device, take each item's route and
+ * shape from the tuned table, else a size heuristic (the staged route for
+ * candidates of 2^21 node-levels and more).
  * Errors: NB_EINVAL, NB_ESHAPE, NB_EDTYPE, NB_EOOM. */
 int nb_batch_create(const nb_batch_item *items, int n, nb_batch **out);
 int nb_batch_release(nb_batch *batch);
 
-/* Autotune levels-per-block in {4,8,16,32,64} x nodes-per-warp in
- * {1,2,4,8,16,32} per item class (op, dtype, N, levels) by timing single-item
- * launches on `stream`; results are kept per GPU name for later batches and,
+/* Autotune per item class (op, dtype, N, levels) by timing single-item
+ * launches on `stream`: the staged route (where possible) against the
+ * persistent kernel with levels-per-block in {4,8,16,32,64} x nodes-per-warp
+ * in {1,2,4,8,16,32}.  Results are kept per GPU name for later batches and,
  * if the environment variable NB_TUNE_CACHE names a file, saved there
- * ("gpu|op|f64|N|nlev|lpb|npw" lines) and read back by later processes. */
+ * ("gpu|op|f64|N|nlev|lpb|npw" lines, lpb = npw = 0 for the staged route)
+ * and read back by later processes. */
 int nb_batch_tune(nb_batch *batch, void *stream);
 
 /* Run the batch: the first call (and the first after tuning) captures the
@@ -319,8 +328,9 @@ int nb_batch_run(nb_batch *batch, void *stream);
 /* Compensated (1, default) or plain (0) FP32 accumulation for the batch. */
 int nb_batch_set_compensated(nb_batch *batch, int on);
 
-/* Work units, node-levels (sum over items of V x nlev), and per item the
- * chosen nodes-per-warp and levels-per-block (arrays of n, may be NULL). */
+/* Work units of the persistent route, node-levels (sum over items of
+ * V x nlev), and per item the chosen nodes-per-warp and levels-per-block
+ * (arrays of n, may be NULL; both 0 for an item on the staged route). */
 int nb_batch_info(const nb_batch *batch, int64_t *units, int64_t *node_levels,
                   int32_t *nodes_per_warp, int32_t *levels_per_block);
 

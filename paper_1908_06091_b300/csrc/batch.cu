@@ -10,10 +10,13 @@
 // same neighbour order, same compensated accumulation, FP64 for pole-row
 // nodes), so a batched result equals the same operation run alone on the
 // direct kernels bit for bit.  Laplacian items run their gradient pass in
-// phase 1 (into batch-owned scratch) and their divergence pass in phase 2; the
-// counter resets and the two launches form one CUDA graph.  `levels per block`
-// and `nodes per warp` are chosen per item class (op, dtype, grid, levels) by
-// an autotuner that times the candidates on the device.
+// phase 1 (into batch-owned scratch) and their divergence pass in phase 2.
+// Large FP32 items instead take the shared-memory staged kernels (one launch,
+// two for a Laplacian), exactly as when run alone.  The counter resets, the
+// two persistent launches and the staged launches form one CUDA graph.  The
+// route and, for the persistent kernel, `levels per block` and `nodes per
+// warp` are chosen per item class (op, dtype, grid, levels) by an autotuner
+// that times the candidates on the device.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -414,6 +417,26 @@ static std::pair<int, int> default_shape(int nlev) {
   return {64, 1};
 }
 
+// Shape {0, 0} routes an item to the staged kernels.
+static const std::pair<int, int> kStagedRoute{0, 0};
+static bool staged_route(const std::pair<int, int> &shp) { return shp.first == 0; }
+
+// FP32 items with 16-byte aligned columns of at least 16 levels can take the
+// staged kernels (which still fall back to the direct ones when a column does
+// not fit a stage).
+static bool staged_candidate(const nb_field &in, const nb_field &out) {
+  return in.dtype == NB_F32 && in.nlev >= 16 &&
+         ((((uintptr_t)in.data) | ((uintptr_t)out.data)) & 15u) == 0 && in.node_stride % 4 == 0 &&
+         out.node_stride % 4 == 0;
+}
+
+// Default route: the staged kernels for large candidates (about two million
+// node-levels and up), the persistent kernel otherwise.
+static std::pair<int, int> default_route(const nb_field &in, const nb_field &out) {
+  if (staged_candidate(in, out) && in.nnodes * (int64_t)in.nlev >= (int64_t)1 << 21) return kStagedRoute;
+  return default_shape(in.nlev);
+}
+
 }  // namespace nb
 
 struct nb_batch : nb::RefCounted {
@@ -434,6 +457,7 @@ struct nb_batch : nb::RefCounted {
   int64_t nunits[2] = {0, 0};
   unsigned long long *d_counter = nullptr;  // 2 counters
   int64_t node_levels = 0;
+  int staged_launches = 0;  // launches of the staged route per run
   int comp = 1;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -493,8 +517,13 @@ static int64_t item_units(const BItem &b) {
 // (Re)build the device work tables of both phases from the current shapes.
 static int batch_build_tables(nb_batch *bt) {
   std::vector<BItem> ph[2];
+  bt->staged_launches = 0;
   for (size_t k = 0; k < bt->src.size(); ++k) {
     const auto &s = bt->src[k];
+    if (staged_route(bt->shape[k])) {
+      bt->staged_launches += s.op == NB_OP_LAP ? 2 : 1;
+      continue;
+    }
     if (s.op == NB_OP_LAP) {
       nb_field tmp = s.in;
       tmp.data = bt->scratch[k];
@@ -534,6 +563,19 @@ static int batch_build_tables(nb_batch *bt) {
   return NB_OK;
 }
 
+int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, const nb_field *out2,
+                 cudaStream_t st, bool *handled, int comp);
+
+// One operation of a staged-route item: the staged kernel, or the direct one
+// where a column does not fit a stage.
+static int staged_or_direct(nb_method *m, int op, const nb_field &in, const nb_field &out, int comp,
+                            cudaStream_t st) {
+  bool handled = false;
+  const int rc = launch_tiled(m, op, &in, &out, nullptr, st, &handled, comp);
+  if (handled || rc != NB_OK) return rc;
+  return launch_direct(m, op, &in, &out, st);
+}
+
 // Launch the phases directly on a stream (used for capture and for tuning).
 static int batch_launch(nb_batch *bt, cudaStream_t st) {
   NB_CUDA(cudaMemsetAsync(bt->d_counter, 0, 2 * sizeof(unsigned long long), st));
@@ -543,6 +585,23 @@ static int batch_launch(nb_batch *bt, cudaStream_t st) {
                                                      bt->d_counter + p, bt->comp);
     count_launch(1);
     NB_CUDA(cudaGetLastError());
+  }
+  for (size_t k = 0; k < bt->src.size(); ++k) {
+    if (!staged_route(bt->shape[k])) continue;
+    const auto &s = bt->src[k];
+    int rc;
+    if (s.op == NB_OP_LAP) {
+      nb_field tmp = s.in;
+      tmp.data = bt->scratch[k];
+      tmp.nvar = 2;
+      tmp.node_stride = 2 * (int64_t)((s.in.nlev + 3) / 4) * 4;
+      tmp.lev_stride = 2;
+      rc = staged_or_direct(s.method, NB_OP_GRAD, s.in, tmp, bt->comp, st);
+      if (rc == NB_OK) rc = staged_or_direct(s.method, NB_OP_DIV, tmp, s.out, bt->comp, st);
+    } else {
+      rc = staged_or_direct(s.method, s.op, s.in, s.out, bt->comp, st);
+    }
+    if (rc != NB_OK) return rc;
   }
   return NB_OK;
 }
@@ -558,7 +617,14 @@ static int batch_capture(nb_batch *bt) {
   drop_graph(bt);
   cudaStream_t cs;
   NB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-  int rc = NB_OK;
+  // one eager run first: staged launches build their tile plans (host and
+  // device allocations) on first use, which a capture must not contain
+  int rc = batch_launch(bt, cs);
+  if (rc == NB_OK && cudaStreamSynchronize(cs) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "batch warm-up");
+  if (rc != NB_OK) {
+    cudaStreamDestroy(cs);
+    return rc;
+  }
   if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     cudaStreamDestroy(cs);
     set_error("nb_batch: stream capture failed to start");
@@ -610,8 +676,10 @@ int nb_batch_create(const nb_batch_item *items, int n, nb_batch **out) {
       bt->keys.push_back(key);
       auto g = nb::g_tune.find(gpu);
       auto hit = (g != nb::g_tune.end()) ? g->second.find(key) : std::map<nb::TuneKey, std::pair<int, int>>::iterator();
-      bt->shape.push_back((g != nb::g_tune.end() && hit != g->second.end()) ? hit->second
-                                                                             : nb::default_shape(it.in.nlev));
+      auto shp = (g != nb::g_tune.end() && hit != g->second.end()) ? hit->second
+                                                                   : nb::default_route(it.in, it.out);
+      if (nb::staged_route(shp) && !nb::staged_candidate(it.in, it.out)) shp = nb::default_shape(it.in.nlev);
+      bt->shape.push_back(shp);
       void *scr = nullptr;
       size_t scr_bytes = 0;
       if (it.op == NB_OP_LAP) {
@@ -682,7 +750,7 @@ int nb_batch_run(nb_batch *b, void *stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const cudaError_t e = cudaGraphLaunch(b->exec, s);
   if (e != cudaSuccess) return nb::cuda_fail(e, "cudaGraphLaunch");
-  nb::count_launch((b->nunits[0] > 0) + (b->nunits[1] > 0));
+  nb::count_launch((b->nunits[0] > 0) + (b->nunits[1] > 0) + b->staged_launches);
   return NB_OK;
 }
 
@@ -734,6 +802,20 @@ int nb_batch_tune(nb_batch *b, void *stream) {
     }
     float best_ms = 1e30f;
     std::pair<int, int> best_shape = nb::default_shape(b->src[k].in.nlev);
+    if (nb::staged_candidate(b->src[k].in, b->src[k].out)) {
+      one.shape[0] = nb::kStagedRoute;
+      if ((rc = nb::batch_build_tables(&one)) != NB_OK) break;
+      for (int w = 0; w < 2 && rc == NB_OK; ++w) rc = nb::batch_launch(&one, st);
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < 5 && rc == NB_OK; ++r) rc = nb::batch_launch(&one, st);
+      cudaEventRecord(e1, st);
+      if (rc != NB_OK) break;
+      cudaEventSynchronize(e1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      best_ms = ms;
+      best_shape = nb::kStagedRoute;
+    }
     for (int lpb : lpbs) {
       if (lpb > 2 * b->src[k].in.nlev && lpb != 4) continue;
       for (int npw : npws) {

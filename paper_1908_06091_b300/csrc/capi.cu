@@ -81,7 +81,7 @@ int dev_free_async(const DevAlloc &a, void *ptr, size_t bytes, void *stream) {
 }
 
 int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, const nb_field *out2,
-                 cudaStream_t st, bool *handled);
+                 cudaStream_t st, bool *handled, int comp = -1);
 int device_status(int clear, int *code);
 
 }  // namespace nb

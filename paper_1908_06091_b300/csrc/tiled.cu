@@ -30,7 +30,7 @@ namespace nb {
 __device__ int g_device_status = 0;
 
 int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, const nb_field *out2,
-                 cudaStream_t st, bool *handled);
+                 cudaStream_t st, bool *handled, int comp = -1);
 
 // ------------------------------------------------------------ PTX helpers
 
@@ -771,9 +771,10 @@ static int status_word(int **out) {
 }
 
 // out2 != nullptr (op == NB_OP_DIV): fused pass writing div to out and curl
-// to out2.
+// to out2.  comp: compensated accumulation (1), plain (0), or the method's
+// setting (-1).
 int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, const nb_field *out2,
-                 cudaStream_t st, bool *handled) {
+                 cudaStream_t st, bool *handled, int comp_mode) {
   *handled = false;
   if (in->dtype != NB_F32) return NB_OK;
   const bool fused = out2 != nullptr;
@@ -885,7 +886,7 @@ int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, 
   }
   const int grid = std::min(tp->ntiles, g_sm_count);
   *handled = true;
-  const bool comp = m->compensated != 0;
+  const bool comp = comp_mode < 0 ? m->compensated != 0 : comp_mode != 0;
   if (g) return comp ? launch_staged_t<0, true>(a, map, grid, smem, st) : launch_staged_t<0, false>(a, map, grid, smem, st);
   if (fused)
     return comp ? launch_staged_t<2, true>(a, map, grid, smem, st) : launch_staged_t<2, false>(a, map, grid, smem, st);

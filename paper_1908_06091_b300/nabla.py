@@ -447,8 +447,8 @@ class Batch(_Handle):
         lpb = np.zeros(self.n, dtype=np.int32)
         check(lib().nb_batch_info(self._h, ctypes.byref(u), ctypes.byref(nl), npw.ctypes.data,
                                   lpb.ctypes.data))
-        return {"units": u.value, "node_levels": nl.value, "nodes_per_warp": npw,
-                "levels_per_block": lpb}
+        return {"units": u.value, "node_levels": nl.value, "nodes_per_warp": npw.tolist(),
+                "levels_per_block": lpb.tolist()}
 
 
 class Server(_Handle):
