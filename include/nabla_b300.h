@@ -342,7 +342,9 @@ int nb_batch_info(const nb_batch *batch, int64_t *units, int64_t *node_levels,
  * requests in arrival order while the device-memory budget and the in-flight
  * limit allow, takes the request's field memory from the CUDA memory pool
  * (stream ordered), synthesises its inputs, runs the operator on the least
- * loaded of `nstreams` streams and frees everything when the request's
+ * loaded of `nstreams` streams (a request's fields packed side by side
+ * along the level axis into column blocks of at most 144 levels, one launch
+ * per operator pass and block) and frees everything when the request's
  * completion event has fired, so requests overlap on the device.  A result is
  * computed by the same kernels whether the request runs alone or among
  * others, so it is bitwise the same. */

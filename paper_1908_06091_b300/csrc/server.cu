@@ -1,7 +1,12 @@
 // server.cu -- continuous-batching request server for derived fields.
 //
 // A request asks for one nabla operator on 1..8 fields of a resident grid
-// with a given number of levels.  A worker thread admits arriving requests in
+// with a given number of levels.  A request's fields are packed side by
+// side along the level axis into column blocks ([node][field][level]) of at
+// most kBlockLevels levels, so one synthesis launch and one operator launch
+// (two for a Laplacian) serve all fields of a block; the operators act on
+// each level independently, so every field's result is the one it gets
+// alone.  A worker thread admits arriving requests in
 // arrival order while the device-memory budget and the in-flight limit allow,
 // takes stream-ordered memory for the request's fields from the CUDA memory
 // pool, synthesises the input fields on the device from the grid's resident
@@ -132,15 +137,28 @@ struct nb_server : nb::RefCounted {
 
 namespace nb {
 
+// Column blocks: fields per block, and the level stride of a block of nf
+// fields (padded so that columns start on 16 bytes).  Blocks stay within the
+// column heights the staged kernels handle well.
+constexpr int kBlockLevels = 144;
+static int fields_per_block(const nb_request &r) {
+  return std::max(1, std::min(r.nfields, kBlockLevels / std::max(1, r.nlev)));
+}
+static int64_t block_stride(const nb_request &r, int nf) {
+  const int q = r.dtype == NB_F64 ? 2 : 4;
+  return ((int64_t)nf * r.nlev + q - 1) / q * q;
+}
+
 static int64_t req_bytes(const nb_server *s, const nb_request &r, int64_t V) {
   const int64_t elem = r.dtype == NB_F64 ? 8 : 4;
-  const int q = r.dtype == NB_F64 ? 2 : 4;
-  const int64_t lp = (int64_t)((r.nlev + q - 1) / q) * q;
   const int in_var = (r.op == NB_OP_DIV || r.op == NB_OP_CURL) ? 2 : 1;
   const int out_var = r.op == NB_OP_GRAD ? 2 : 1;
   const int scr_var = r.op == NB_OP_LAP ? 2 : 0;
   (void)s;
-  return (int64_t)r.nfields * V * lp * elem * (in_var + out_var + scr_var);
+  const int fpb = fields_per_block(r);
+  int64_t levels = 0;
+  for (int f0 = 0; f0 < r.nfields; f0 += fpb) levels += block_stride(r, std::min(fpb, r.nfields - f0));
+  return V * levels * elem * (in_var + out_var + scr_var);
 }
 
 // Enqueue one admitted request on its stream (caller holds no lock).
@@ -151,8 +169,6 @@ static int launch_request(nb_server *s, SrvReq *q) {
   const int64_t V = m->mesh->V;
   cudaStream_t st = s->streams[q->stream];
   const int64_t elem = r.dtype == NB_F64 ? 8 : 4;
-  const int qq = r.dtype == NB_F64 ? 2 : 4;
-  const int64_t lp = (int64_t)((r.nlev + qq - 1) / qq) * qq;
   const int in_var = (r.op == NB_OP_DIV || r.op == NB_OP_CURL) ? 2 : 1;
   const int out_var = r.op == NB_OP_GRAD ? 2 : 1;
   float *wts = nullptr;
@@ -162,31 +178,35 @@ static int launch_request(nb_server *s, SrvReq *q) {
   synth_weights_kernel<<<(nw + 255) / 256, 256, 0, st>>>(r.seed, r.nfields, r.nlev, wts);
   count_launch(1);
   NB_CUDA(cudaGetLastError());
-  for (int f = 0; f < r.nfields; ++f) {
+  const float *basis = in_var == 2 ? g.d_wind : g.d_scalar;
+  const int fpb = fields_per_block(r);
+  for (int f0 = 0; f0 < r.nfields; f0 += fpb) {
+    const int nf = std::min(fpb, r.nfields - f0);
+    const int nl = nf * r.nlev;  // levels of the block in use
+    const int64_t lb = block_stride(r, nf);
     void *din = nullptr, *dout = nullptr, *dscr = nullptr;
-    NB_CUDA(cudaMallocAsync(&din, (size_t)(V * lp * in_var * elem), st));
+    NB_CUDA(cudaMallocAsync(&din, (size_t)(V * lb * in_var * elem), st));
     q->bufs.push_back(din);
-    NB_CUDA(cudaMallocAsync(&dout, (size_t)(V * lp * out_var * elem), st));
+    NB_CUDA(cudaMallocAsync(&dout, (size_t)(V * lb * out_var * elem), st));
     q->bufs.push_back(dout);
     if (r.op == NB_OP_LAP) {
-      NB_CUDA(cudaMallocAsync(&dscr, (size_t)(V * lp * 2 * elem), st));
+      NB_CUDA(cudaMallocAsync(&dscr, (size_t)(V * lb * 2 * elem), st));
       q->bufs.push_back(dscr);
     }
-    const float *basis = in_var == 2 ? g.d_wind : g.d_scalar;
-    const int64_t pts = V * r.nlev;
-    const unsigned blocks = (unsigned)((pts + 255) / 256);
-    const float *wf = wts + (size_t)f * r.nlev * 8;
+    // weights are [field][level][basis]: the block's are contiguous
+    const float *wb = wts + (size_t)f0 * r.nlev * 8;
+    const unsigned blocks = (unsigned)((V * nl + 255) / 256);
     if (r.dtype == NB_F64)
-      synth_fields_kernel<double><<<blocks, 256, 0, st>>>(basis, in_var, V, r.nlev, lp * in_var, wf,
+      synth_fields_kernel<double><<<blocks, 256, 0, st>>>(basis, in_var, V, nl, lb * in_var, wb,
                                                           static_cast<double *>(din));
     else
-      synth_fields_kernel<float><<<blocks, 256, 0, st>>>(basis, in_var, V, r.nlev, lp * in_var, wf,
+      synth_fields_kernel<float><<<blocks, 256, 0, st>>>(basis, in_var, V, nl, lb * in_var, wb,
                                                          static_cast<float *>(din));
     count_launch(1);
     NB_CUDA(cudaGetLastError());
-    nb_field fi{din, r.dtype, in_var, V, r.nlev, 0, lp * in_var, in_var};
-    nb_field fo{dout, r.dtype, out_var, V, r.nlev, 0, lp * out_var, out_var};
-    nb_field fsc{dscr, r.dtype, 2, V, r.nlev, 0, lp * 2, 2};
+    nb_field fi{din, r.dtype, in_var, V, nl, 0, lb * in_var, in_var};
+    nb_field fo{dout, r.dtype, out_var, V, nl, 0, lb * out_var, out_var};
+    nb_field fsc{dscr, r.dtype, 2, V, nl, 0, lb * 2, 2};
     const int rc = launch_op(m, r.op, &fi, &fo, r.op == NB_OP_LAP ? &fsc : nullptr, st);
     if (rc != NB_OK) return rc;
   }
@@ -195,26 +215,37 @@ static int launch_request(nb_server *s, SrvReq *q) {
   return NB_OK;
 }
 
+// Copy field j of a column block (level stride lb) to host memory laid out
+// as [V][lp][nvar] at `host` (padding levels left as they are).
+static void copy_field_out(char *host, const void *dev, int64_t V, int64_t lb, int64_t lp, int nlev,
+                           int nvar, int64_t elem, int j) {
+  const size_t dpitch = (size_t)(lp * nvar * elem), spitch = (size_t)(lb * nvar * elem);
+  cudaMemcpy2D(host, dpitch, static_cast<const char *>(dev) + (size_t)j * nlev * nvar * elem, spitch,
+               (size_t)(nlev * nvar * elem), (size_t)V, cudaMemcpyDeviceToHost);
+}
+
 static void finish_request(nb_server *s, SrvReq *q) {
   cudaStream_t st = s->streams[q->stream];
   if (q->r.keep_output && q->status == NB_OK) {
-    // outputs are the 2nd of every 2 (or 3, Laplacian) buffers
-    const int per = q->r.op == NB_OP_LAP ? 3 : 2;
-    const int64_t V = s->grids[q->r.N].method->mesh->V;
-    const int64_t elem = q->r.dtype == NB_F64 ? 8 : 4;
-    const int qq = q->r.dtype == NB_F64 ? 2 : 4;
-    const int64_t lp = (int64_t)((q->r.nlev + qq - 1) / qq) * qq;
-    const int out_var = q->r.op == NB_OP_GRAD ? 2 : 1;
-    const int64_t one = V * lp * out_var * elem;
-    q->host_out.resize((size_t)(one * q->r.nfields));
-    for (int f = 0; f < q->r.nfields; ++f)
-      cudaMemcpy(q->host_out.data() + f * one, q->bufs[f * per + 1], (size_t)one, cudaMemcpyDeviceToHost);
-    if (q->r.keep_output == 2) {
-      const int in_var = (q->r.op == NB_OP_DIV || q->r.op == NB_OP_CURL) ? 2 : 1;
-      const int64_t ione = V * lp * in_var * elem;
-      q->host_in.resize((size_t)(ione * q->r.nfields));
-      for (int f = 0; f < q->r.nfields; ++f)
-        cudaMemcpy(q->host_in.data() + f * ione, q->bufs[f * per], (size_t)ione, cudaMemcpyDeviceToHost);
+    // per block: the input block, the output block (and the Laplacian scratch)
+    const nb_request &r = q->r;
+    const int per = r.op == NB_OP_LAP ? 3 : 2;
+    const int64_t V = s->grids[r.N].method->mesh->V;
+    const int64_t elem = r.dtype == NB_F64 ? 8 : 4;
+    const int qq = r.dtype == NB_F64 ? 2 : 4;
+    const int64_t lp = (int64_t)((r.nlev + qq - 1) / qq) * qq;
+    const int in_var = (r.op == NB_OP_DIV || r.op == NB_OP_CURL) ? 2 : 1;
+    const int out_var = r.op == NB_OP_GRAD ? 2 : 1;
+    const int64_t one = V * lp * out_var * elem, ione = V * lp * in_var * elem;
+    q->host_out.assign((size_t)(one * r.nfields), 0);
+    if (r.keep_output == 2) q->host_in.assign((size_t)(ione * r.nfields), 0);
+    const int fpb = fields_per_block(r);
+    for (int f = 0; f < r.nfields; ++f) {
+      const int blk = f / fpb, j = f - blk * fpb;
+      const int64_t lb = block_stride(r, std::min(fpb, r.nfields - blk * fpb));
+      copy_field_out(q->host_out.data() + f * one, q->bufs[blk * per + 1], V, lb, lp, r.nlev, out_var, elem, j);
+      if (r.keep_output == 2)
+        copy_field_out(q->host_in.data() + f * ione, q->bufs[blk * per], V, lb, lp, r.nlev, in_var, elem, j);
     }
   }
   for (void *p : q->bufs) cudaFreeAsync(p, st);
@@ -238,10 +269,12 @@ static void worker_loop(nb_server *s) {
         continue;
       }
       if (e != cudaSuccess) q->status = NB_ECUDA;
-      q->done = s->now();
+      // the result is published (done >= 0) only once its outputs are kept
+      const double t_done = s->now();
       lk.unlock();
       finish_request(s, q);
       lk.lock();
+      q->done = t_done;
       s->used -= q->bytes;
       s->inflight.erase(s->inflight.begin() + (long)k);
       s->cv.notify_all();
@@ -265,10 +298,11 @@ static void worker_loop(nb_server *s) {
       if (rc != NB_OK) {
         q->status = rc;
         if (!q->ev) {  // nothing to wait for: retire now
-          q->done = s->now();
+          const double t_done = s->now();
           lk.unlock();
           finish_request(s, q);
           lk.lock();
+          q->done = t_done;
           s->used -= q->bytes;
           s->inflight.erase(std::find(s->inflight.begin(), s->inflight.end(), q));
           s->cv.notify_all();
