@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--cpu-levels", type=int, default=64,
                    help="levels of the oracle's bounded CPU sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--single-op-reps", type=int, default=3,
+                   help="timed single-operator div and curl passes after the timed region (0 = none)")
     p.add_argument("--variant", type=int, default=0, help="kernel variant (0 auto, 1 direct, 2 tiled)")
     p.add_argument("--tile", type=int, default=0)
     p.add_argument("--batch-fields", type=int, default=64, help="0 skips the batched section")
@@ -286,15 +288,15 @@ def bench_ours(a):
     # the single-operator passes, outside the timed region (for reference)
     single = {}
     with torch.cuda.stream(stream):
-        for op, xin, o in (("div", uv, outs[1]), ("curl", uv, outs[2])):
+        for op, xin, o in (("div", uv, outs[1]), ("curl", uv, outs[2])) if a.single_op_reps > 0 else ():
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             nabla.apply(method, op, xin, o, stream=stream)
             e0.record(stream)
-            for _ in range(3):
+            for _ in range(a.single_op_reps):
                 nabla.apply(method, op, xin, o, stream=stream)
             e1.record(stream)
             stream.synchronize()
-            single[op] = round(e0.elapsed_time(e1) / 3, 4)
+            single[op] = round(e0.elapsed_time(e1) / a.single_op_reps, 4)
 
     # FP64 GPU path on the same workload (the plain reference GPU path)
     fp64 = None
