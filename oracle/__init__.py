@@ -67,6 +67,10 @@ def _declare(L: ctypes.CDLL) -> None:
     L.or_gaussian_rows.argtypes = [ctypes.c_int, _P, _P]
     L.or_grid_lonlat.argtypes = [ctypes.c_int, _P, _P]
     L.or_triangulate.argtypes = [ctypes.c_int, _P]
+    L.or_num_nodes_pl.restype = _L
+    L.or_num_nodes_pl.argtypes = [ctypes.c_int, _P]
+    L.or_grid_lonlat_pl.argtypes = [ctypes.c_int, _P, _P, _P]
+    L.or_triangulate_pl.argtypes = [ctypes.c_int, _P, _P]
     L.or_edges.restype = _L
     L.or_edges.argtypes = [_L, _L, _P, _P, _P]
     L.or_node_edges.argtypes = [_L, _L, _P, _P, _P]
@@ -104,6 +108,21 @@ def row_nx(N: int) -> np.ndarray:
     return nx
 
 
+def regular_nx(N: int) -> np.ndarray:
+    """Points per parallel of the regular Gaussian grid F<N>: 4N on each of
+    the 2N parallels (Sec. 4.2.3.6)."""
+    return np.full(2 * N, 4 * N, dtype=np.int32)
+
+
+def _pl_array(pl) -> np.ndarray:
+    """A reduced Gaussian grid's PL array (points per parallel, north to
+    south, Sec. 4.2.3.7): an even number of rows, at least 3 points each."""
+    nx = np.ascontiguousarray(pl, dtype=np.int32)
+    if nx.ndim != 1 or nx.size < 2 or nx.size % 2 or (nx < 3).any():
+        raise ValueError("PL array: an even number of parallels, each with at least 3 points")
+    return nx
+
+
 def gaussian_rows(N: int):
     """Roots of P_2N north to south and Gauss weights (Sec. 4.2.3.5)."""
     mu = np.zeros(2 * N)
@@ -112,22 +131,38 @@ def gaussian_rows(N: int):
     return mu, w
 
 
-def grid_lonlat(N: int):
-    """(lat, lon) in radians per node, original order (Sec. 4.2, 4.2.3.5)."""
-    V = num_nodes(N)
+def grid_lonlat(N: int, pl=None):
+    """(lat, lon) in radians per node, original order (Sec. 4.2, 4.2.3.5);
+    pl: the PL array of another reduced Gaussian grid with 2N parallels
+    (default: the octahedral O<N>)."""
+    if pl is None:
+        V = num_nodes(N)
+        lat = np.zeros(V)
+        lon = np.zeros(V)
+        lib().or_grid_lonlat(N, _ptr(lat), _ptr(lon))
+        return lat, lon
+    nx = _pl_array(pl)
+    V = int(lib().or_num_nodes_pl(nx.size, _ptr(nx)))
     lat = np.zeros(V)
     lon = np.zeros(V)
-    lib().or_grid_lonlat(N, _ptr(lat), _ptr(lon))
+    lib().or_grid_lonlat_pl(nx.size, _ptr(nx), _ptr(lat), _ptr(lon))
     return lat, lon
 
 
 # ------------------------------------------------------------------- mesh
 
-def triangulate(N: int) -> np.ndarray:
-    """[F][3] counter-clockwise triangles (reading of Sec. 4.3, Fig. 25b)."""
-    F = int(lib().or_num_triangles(N))
+def triangulate(N: int, pl=None) -> np.ndarray:
+    """[F][3] counter-clockwise triangles (reading of Sec. 4.3, Fig. 25b);
+    pl as for grid_lonlat."""
+    if pl is None:
+        F = int(lib().or_num_triangles(N))
+        tri = np.zeros((F, 3), dtype=np.int32)
+        lib().or_triangulate(N, _ptr(tri))
+        return tri
+    nx = _pl_array(pl)
+    F = 2 * int(nx.sum()) - 4
     tri = np.zeros((F, 3), dtype=np.int32)
-    lib().or_triangulate(N, _ptr(tri))
+    lib().or_triangulate_pl(nx.size, _ptr(nx), _ptr(tri))
     return tri
 
 
@@ -182,12 +217,14 @@ class Mesh:
         return self.tri.shape[0]
 
 
-def build_mesh(N: int, R: float = EARTH_RADIUS_M) -> Mesh:
-    """Grid -> mesh -> median-dual geometry (Sec. 4.2, 4.3, 4.7)."""
+def build_mesh(N: int, R: float = EARTH_RADIUS_M, pl=None) -> Mesh:
+    """Grid -> mesh -> median-dual geometry (Sec. 4.2, 4.3, 4.7).  pl: the
+    PL array of a reduced Gaussian grid with 2N parallels (Sec. 4.2.3.7;
+    default: octahedral O<N>)."""
     L = lib()
-    lat, lon = grid_lonlat(N)
+    lat, lon = grid_lonlat(N, pl)
     V = lat.shape[0]
-    tri = triangulate(N)
+    tri = triangulate(N, pl)
     edge, etri = edges(V, tri)
     nptr, nlist = node_edges(V, edge)
     east = np.zeros((V, 3))

@@ -63,6 +63,16 @@ void or_row_nx(int N, int *nx) {
   for (int j = 0; j < 2 * N; ++j) nx[j] = row_nx(N, j);
 }
 
+/* Any reduced Gaussian grid is given by its points per parallel, the "PL"
+ * array nx[0..rows) from north to south (Sec. 4.2.3.7); the regular F<N>
+ * grid has nx = 4N on all 2N rows (Sec. 4.2.3.6), the octahedral O<N> grid
+ * the row lengths above.  The _pl functions take such an array. */
+long or_num_nodes_pl(int rows, const int *nx) {
+  long v = 0;
+  for (int j = 0; j < rows; ++j) v += nx[j];
+  return v;
+}
+
 /* Legendre polynomial P_n(x) and its derivative, from the three-term
  * recurrence (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1}, in extended
  * precision (long double). */
@@ -106,22 +116,29 @@ void or_gaussian_rows(int N, double *mu, double *weight) {
 /* Latitude and longitude (radians) of every node, original order.  The first
  * point of each row is at longitude 0 and the points of a row are equispaced
  * (Sec. 4.2, Sec. 4.2.3.5). */
-void or_grid_lonlat(int N, double *lat, double *lon) {
+void or_grid_lonlat_pl(int rows, const int *nx, double *lat, double *lon) {
+  int N = rows / 2;
   double *mu = (double *)malloc(sizeof(double) * 2 * N);
   double *w = (double *)malloc(sizeof(double) * 2 * N);
   or_gaussian_rows(N, mu, w);
   long id = 0;
   for (int j = 0; j < 2 * N; ++j) {
-    int nx = row_nx(N, j);
     double phi = asin(mu[j]);
-    for (int i = 0; i < nx; ++i) {
+    for (int i = 0; i < nx[j]; ++i) {
       lat[id] = phi;
-      lon[id] = 2.0 * OR_PI * (double)i / (double)nx;
+      lon[id] = 2.0 * OR_PI * (double)i / (double)nx[j];
       ++id;
     }
   }
   free(mu);
   free(w);
+}
+
+void or_grid_lonlat(int N, double *lat, double *lon) {
+  int *nx = (int *)malloc(sizeof(int) * 2 * N);
+  or_row_nx(N, nx);
+  or_grid_lonlat_pl(2 * N, nx, lat, lon);
+  free(nx);
 }
 
 /* ---------------------------------------------------------- triangulation */
@@ -141,21 +158,23 @@ long or_num_triangles(int N) { return 2 * or_num_nodes(N) - 4; }
  *
  * Pole caps: the polygon of the first (last) row is closed with no extra
  * node by the parallel chords (k, n-1-k); the quad (k, k+1, n-2-k, n-1-k) is
- * split along (k+1, n-1-k).  n - 2 triangles per cap, so F = 2V - 4.
+ * split along (k+1, n-1-k).  An odd ring leaves the triangle
+ * (m, m+1, n-1-m), m = n/2 - 1 (integer division), after the last quad.
+ * n - 2 triangles per cap, so F = 2V - 4.
  *
  * Output order: north cap, strips north to south, south cap. */
-void or_triangulate(int N, int32_t *tri) {
-  int rows = 2 * N;
+void or_triangulate_pl(int rows, const int *nx, int32_t *tri) {
   long *off = (long *)malloc(sizeof(long) * (rows + 1));
   off[0] = 0;
-  for (int j = 0; j < rows; ++j) off[j + 1] = off[j] + row_nx(N, j);
+  for (int j = 0; j < rows; ++j) off[j + 1] = off[j] + nx[j];
   long t = 0;
 
   /* north cap: ring increases counter-clockwise seen from above the pole */
   {
-    int n = row_nx(N, 0);
+    int n = nx[0];
     long b = off[0];
-    for (int k = 0; k + 1 < n / 2; ++k) {
+    int k = 0;
+    for (; k + 1 < n / 2; ++k) {
       tri[3 * t + 0] = (int32_t)(b + k);
       tri[3 * t + 1] = (int32_t)(b + k + 1);
       tri[3 * t + 2] = (int32_t)(b + n - 1 - k);
@@ -165,10 +184,16 @@ void or_triangulate(int N, int32_t *tri) {
       tri[3 * t + 2] = (int32_t)(b + n - 1 - k);
       ++t;
     }
+    if (n % 2 == 1) {
+      tri[3 * t + 0] = (int32_t)(b + k);
+      tri[3 * t + 1] = (int32_t)(b + k + 1);
+      tri[3 * t + 2] = (int32_t)(b + n - 1 - k);
+      ++t;
+    }
   }
 
   for (int j = 0; j + 1 < rows; ++j) {
-    long n = row_nx(N, j), n2 = row_nx(N, j + 1);
+    long n = nx[j], n2 = nx[j + 1];
     long a0 = off[j], b0 = off[j + 1];
     long a = 0, b = 0;
     while (a < n || b < n2) {
@@ -199,9 +224,10 @@ void or_triangulate(int N, int32_t *tri) {
   /* south cap: the same chords, reversed so that the triangles are
    * counter-clockwise seen from below the south pole */
   {
-    int n = row_nx(N, rows - 1);
+    int n = nx[rows - 1];
     long b = off[rows - 1];
-    for (int k = 0; k + 1 < n / 2; ++k) {
+    int k = 0;
+    for (; k + 1 < n / 2; ++k) {
       tri[3 * t + 0] = (int32_t)(b + k);
       tri[3 * t + 1] = (int32_t)(b + n - 1 - k);
       tri[3 * t + 2] = (int32_t)(b + k + 1);
@@ -211,8 +237,21 @@ void or_triangulate(int N, int32_t *tri) {
       tri[3 * t + 2] = (int32_t)(b + n - 2 - k);
       ++t;
     }
+    if (n % 2 == 1) {
+      tri[3 * t + 0] = (int32_t)(b + k);
+      tri[3 * t + 1] = (int32_t)(b + n - 1 - k);
+      tri[3 * t + 2] = (int32_t)(b + k + 1);
+      ++t;
+    }
   }
   free(off);
+}
+
+void or_triangulate(int N, int32_t *tri) {
+  int *nx = (int *)malloc(sizeof(int) * 2 * N);
+  or_row_nx(N, nx);
+  or_triangulate_pl(2 * N, nx, tri);
+  free(nx);
 }
 
 /* ------------------------------------------------------------------ edges */
