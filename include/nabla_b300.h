@@ -124,10 +124,30 @@ int nb_set_allocator(const nb_allocator *allocator);
  * the first point of every row at longitude 0.  N in [1, 8000].
  * Errors: NB_EINVAL (N out of range or out == NULL), NB_EOOM. */
 int nb_grid_create_octahedral(int N, nb_grid **out);
+
+/* Regular Gaussian grid F<N> (Sec. 4.2.3.6): 4N points on each of the 2N
+ * Gaussian latitude rows.  N in [1, 8000].  Errors as above. */
+int nb_grid_create_regular(int N, nb_grid **out);
+
+/* Reduced Gaussian grid from its PL array (Sec. 4.2.3.7): pl[j] points on
+ * Gaussian row j (north to south) of nrows = 2N rows.  nrows even and >= 2,
+ * every pl[j] >= 3 (a pole ring needs a triangle), at most 2^31 - 1 points in
+ * all.  Classic N<N> grids are built this way from their tabulated PL arrays.
+ * pl: caller-owned host array, copied.  Errors: NB_EINVAL, NB_EOOM. */
+int nb_grid_create_reduced(int nrows, const int32_t *pl, nb_grid **out);
+
+/* Grid by name (Sec. 4.2.3): "O<N>" octahedral, "F<N>" regular.  "N<N>"
+ * (classic) needs the tabulated PL array: use nb_grid_create_reduced.
+ * Errors: NB_EINVAL (unknown or unsupported name), NB_EOOM. */
+int nb_grid_create_named(const char *name, nb_grid **out);
 int nb_grid_release(nb_grid *grid);
 
-/* Number of grid points V = 4N^2 + 36N. */
+/* Number of grid points V (4N^2 + 36N for O<N>, 8N^2 for F<N>, the sum of
+ * the PL array otherwise). */
 int nb_grid_size(const nb_grid *grid, int64_t *nodes);
+
+/* The grid's PL array: points per row, north to south (host int32[2N]). */
+int nb_grid_pl(const nb_grid *grid, int32_t *pl);
 
 /* Gaussian number N of the grid. */
 int nb_grid_gaussian_number(const nb_grid *grid, int *N);
@@ -141,7 +161,8 @@ int nb_grid_lonlat(const nb_grid *grid, double *lonlat);
 
 /* Triangulate the grid (structured mesh generator, Sec. 4.3, Listing 7,
  * Fig. 25b): row strips joined by an exact integer longitude merge, pole
- * caps closed with no extra node, so F = 2V - 4 and E = 3V - 6.
+ * caps closed with no extra node (an odd ring by one last triangle), so
+ * F = 2V - 4 and E = 3V - 6.
  * reorder: 0 keeps grid order, 1 renumbers nodes along a 3-D Hilbert curve
  * for memory locality; in both the nodes of the first and last row come
  * last (see nb_mesh_cap_begin).  Runs on the host, multi-threaded.
@@ -312,12 +333,12 @@ typedef struct nb_batch_item {
 int nb_batch_create(const nb_batch_item *items, int n, nb_batch **out);
 int nb_batch_release(nb_batch *batch);
 
-/* Autotune per item class (op, dtype, N, levels) by timing single-item
+/* Autotune per item class (op, dtype, grid nodes V, levels) by timing single-item
  * launches on `stream`: the staged route (where possible) against the
  * persistent kernel with levels-per-block in {4,8,16,32,64} x nodes-per-warp
  * in {1,2,4,8,16,32}.  Results are kept per GPU name for later batches and,
  * if the environment variable NB_TUNE_CACHE names a file, saved there
- * ("gpu|op|f64|N|nlev|lpb|npw" lines, lpb = npw = 0 for the staged route)
+ * ("gpu|op|f64|V|nlev|lpb|npw" lines, lpb = npw = 0 for the staged route)
  * and read back by later processes. */
 int nb_batch_tune(nb_batch *batch, void *stream);
 

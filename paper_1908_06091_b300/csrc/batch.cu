@@ -361,10 +361,13 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BItem *__res
 
 // ------------------------------------------------------------- host part
 
+// Item class: op, dtype, grid size (nodes) and levels.
 struct TuneKey {
-  int op, f64, N, nlev;
+  int op, f64;
+  int64_t V;
+  int nlev;
   bool operator<(const TuneKey &o) const {
-    return std::tie(op, f64, N, nlev) < std::tie(o.op, o.f64, o.N, o.nlev);
+    return std::tie(op, f64, V, nlev) < std::tie(o.op, o.f64, o.V, o.nlev);
   }
 };
 
@@ -379,7 +382,7 @@ static std::string gpu_name() {
   return p.name;
 }
 
-// Autotune cache file: NB_TUNE_CACHE (if set), lines "gpu|op|f64|N|nlev|lpb|npw".
+// Autotune cache file: NB_TUNE_CACHE (if set), lines "gpu|op|f64|V|nlev|lpb|npw".
 static void load_tune_cache() {
   const char *path = std::getenv("NB_TUNE_CACHE");
   if (!path) return;
@@ -392,7 +395,7 @@ static void load_tune_cache() {
     while (std::getline(ss, tok, '|')) f.push_back(tok);
     if (f.size() != 7) continue;
     try {
-      TuneKey k{std::stoi(f[1]), std::stoi(f[2]), std::stoi(f[3]), std::stoi(f[4])};
+      TuneKey k{std::stoi(f[1]), std::stoi(f[2]), (int64_t)std::stoll(f[3]), std::stoi(f[4])};
       g_tune[f[0]][k] = {std::stoi(f[5]), std::stoi(f[6])};
     } catch (...) {
     }
@@ -404,7 +407,7 @@ static void save_tune_cache() {
   std::ofstream out(path, std::ios::trunc);
   for (auto &g : g_tune)
     for (auto &kv : g.second)
-      out << g.first << '|' << kv.first.op << '|' << kv.first.f64 << '|' << kv.first.N << '|'
+      out << g.first << '|' << kv.first.op << '|' << kv.first.f64 << '|' << kv.first.V << '|'
           << kv.first.nlev << '|' << kv.second.first << '|' << kv.second.second << '\n';
 }
 
@@ -672,7 +675,7 @@ int nb_batch_create(const nb_batch_item *items, int n, nb_batch **out) {
       }
       nb_batch::Src s{it.op, nb::retain(const_cast<nb_method *>(it.method)), it.in, it.out};
       bt->src.push_back(s);
-      nb::TuneKey key{it.op, it.in.dtype == NB_F64, it.method->mesh->grid->N, it.in.nlev};
+      nb::TuneKey key{it.op, it.in.dtype == NB_F64, it.method->mesh->V, it.in.nlev};
       bt->keys.push_back(key);
       auto g = nb::g_tune.find(gpu);
       auto hit = (g != nb::g_tune.end()) ? g->second.find(key) : std::map<nb::TuneKey, std::pair<int, int>>::iterator();

@@ -4,7 +4,10 @@
 // this file's functions.
 #include <cuda_runtime.h>
 
+#include <climits>
 #include <cmath>
+#include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -156,8 +159,56 @@ int nb_grid_create_octahedral(int N, nb_grid **out) {
   NB_GUARD_END
 }
 
+int nb_grid_create_regular(int N, nb_grid **out) {
+  NB_REQUIRE(out, NB_EINVAL, "nb_grid_create_regular: out is NULL");
+  NB_REQUIRE(N >= 1 && N <= 8000, NB_EINVAL, "nb_grid_create_regular: N must be in [1, 8000]");
+  NB_GUARD_BEGIN
+  *out = nb::build_grid_pl(N, std::vector<int32_t>(2 * N, 4 * N));
+  return NB_OK;
+  NB_GUARD_END
+}
+
+int nb_grid_create_reduced(int nrows, const int32_t *pl, nb_grid **out) {
+  NB_REQUIRE(out && pl, NB_EINVAL, "nb_grid_create_reduced: NULL argument");
+  NB_REQUIRE(nrows >= 2 && nrows % 2 == 0 && nrows <= 16000, NB_EINVAL,
+             "nb_grid_create_reduced: nrows must be even, in [2, 16000]");
+  int64_t V = 0;
+  for (int j = 0; j < nrows; ++j) {
+    NB_REQUIRE(pl[j] >= 3, NB_EINVAL, "nb_grid_create_reduced: every row needs at least 3 points");
+    V += pl[j];
+  }
+  NB_REQUIRE(V <= INT32_MAX, NB_EINVAL, "nb_grid_create_reduced: more than 2^31 - 1 points");
+  NB_GUARD_BEGIN
+  *out = nb::build_grid_pl(nrows / 2, std::vector<int32_t>(pl, pl + nrows));
+  return NB_OK;
+  NB_GUARD_END
+}
+
+int nb_grid_create_named(const char *name, nb_grid **out) {
+  NB_REQUIRE(name && out, NB_EINVAL, "nb_grid_create_named: NULL argument");
+  const char family = name[0];
+  char *end = nullptr;
+  const long N = std::strtol(name + 1, &end, 10);
+  NB_REQUIRE(name[1] >= '0' && name[1] <= '9' && end && *end == '\0', NB_EINVAL,
+             "nb_grid_create_named: expected O<N> or F<N>");
+  NB_REQUIRE(family != 'N', NB_EINVAL,
+             "nb_grid_create_named: classic N<N> grids need their tabulated PL array "
+             "(nb_grid_create_reduced)");
+  NB_REQUIRE(N >= 1 && N <= 8000, NB_EINVAL, "nb_grid_create_named: N must be in [1, 8000]");
+  if (family == 'O') return nb_grid_create_octahedral((int)N, out);
+  if (family == 'F') return nb_grid_create_regular((int)N, out);
+  set_error("nb_grid_create_named: expected O<N> or F<N>");
+  return NB_EINVAL;
+}
+
 int nb_grid_release(nb_grid *g) {
   nb::release(g);
+  return NB_OK;
+}
+
+int nb_grid_pl(const nb_grid *g, int32_t *pl) {
+  NB_REQUIRE(g && pl, NB_EINVAL, "nb_grid_pl: NULL argument");
+  std::memcpy(pl, g->nx.data(), sizeof(int32_t) * g->nx.size());
   return NB_OK;
 }
 

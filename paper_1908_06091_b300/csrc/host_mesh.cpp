@@ -61,19 +61,22 @@ static void legendre_roots(int N, std::vector<double> &mu) {
   }
 }
 
-nb_grid *build_grid(int N) {
+nb_grid *build_grid_pl(int N, const std::vector<int32_t> &nx) {
   auto *g = new nb_grid();
   g->N = N;
-  g->nx.resize(2 * N);
+  g->nx = nx;
   g->row_off.resize(2 * N + 1);
   g->row_off[0] = 0;
-  for (int j = 0; j < 2 * N; ++j) {
-    g->nx[j] = octa_nx(N, j);
-    g->row_off[j + 1] = g->row_off[j] + g->nx[j];
-  }
+  for (int j = 0; j < 2 * N; ++j) g->row_off[j + 1] = g->row_off[j] + g->nx[j];
   g->V = g->row_off[2 * N];
   legendre_roots(N, g->mu);
   return g;
+}
+
+nb_grid *build_grid(int N) {
+  std::vector<int32_t> nx(2 * N);
+  for (int j = 0; j < 2 * N; ++j) nx[j] = octa_nx(N, j);
+  return build_grid_pl(N, nx);
 }
 
 // --------------------------------------------------- triangulation (grid ids)
@@ -82,7 +85,9 @@ nb_grid *build_grid(int N) {
 // ring whose next point comes first in longitude ((a+1)/n vs (b+1)/n2
 // compared in integers); ties advance the ring with fewer points, the
 // northern one if equal; caps by the chords (k, n-1-k) split along
-// (k+1, n-1-k).  Triangles counter-clockwise seen from outside.
+// (k+1, n-1-k), and an odd ring's last three points (m, m+1, n-1-m),
+// m = n/2 - 1, as one more triangle.  Triangles counter-clockwise seen from
+// outside.
 static void triangulate_grid_ids(const nb_grid *g, std::vector<int32_t> &tri) {
   const int rows = 2 * g->N;
   const int64_t F = 2 * g->V - 4;
@@ -105,6 +110,16 @@ static void triangulate_grid_ids(const nb_grid *g, std::vector<int32_t> &tri) {
         o[3] = B; o[4] = D; o[5] = C;
       }
       t += 2;
+    }
+    if (n & 1) {
+      const int m = n / 2 - 1;
+      const int32_t A = b + m, B = b + m + 1, D = b + n - 1 - m;
+      int32_t *o = &tri[3 * t];
+      if (north) {
+        o[0] = A; o[1] = B; o[2] = D;
+      } else {
+        o[0] = A; o[1] = D; o[2] = B;
+      }
     }
   };
   cap(0, 0, true);

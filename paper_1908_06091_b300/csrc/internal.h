@@ -51,7 +51,8 @@ inline void release(T *p) {
 
 }  // namespace nb
 
-// Octahedral reduced Gaussian grid (Sec. 4.2.3.7).
+// Reduced Gaussian grid (Sec. 4.2.3.7): octahedral O<N>, regular F<N>, or
+// any PL array.
 struct nb_grid : nb::RefCounted {
   int N = 0;
   int64_t V = 0;
@@ -144,7 +145,8 @@ struct nb_fs : nb::RefCounted {
 namespace nb {
 
 // host builders (host_mesh.cpp)
-nb_grid *build_grid(int N);
+nb_grid *build_grid(int N);                                   // O<N>
+nb_grid *build_grid_pl(int N, const std::vector<int32_t> &nx);  // any PL array of 2N rows
 nb_mesh *build_mesh(nb_grid *grid, int reorder);
 void build_geometry(const nb_mesh *m, double R, std::vector<double> &vol, std::vector<double> &S,
                     std::vector<double> &T, std::vector<double> &east, std::vector<double> &north);

@@ -81,6 +81,10 @@ _FP = ctypes.POINTER(nb_field)
 # name -> argtypes; every function returns int except the two string getters
 SIGNATURES = {
     "nb_grid_create_octahedral": [_I, ctypes.POINTER(_P)],
+    "nb_grid_create_regular": [_I, ctypes.POINTER(_P)],
+    "nb_grid_create_reduced": [_I, _P, ctypes.POINTER(_P)],
+    "nb_grid_create_named": [ctypes.c_char_p, ctypes.POINTER(_P)],
+    "nb_grid_pl": [_P, _P],
     "nb_grid_release": [_P],
     "nb_grid_size": [_P, _I64P],
     "nb_grid_gaussian_number": [_P, ctypes.POINTER(_I)],
@@ -222,13 +226,39 @@ class _Handle:
 
 
 class Grid(_Handle):
-    """Octahedral reduced Gaussian grid O<N> (Sec. 4.2.3.7)."""
+    """Reduced Gaussian grid (Sec. 4.2.3): Grid(N) is the octahedral O<N>;
+    Grid.regular(N) the regular F<N>; Grid.reduced(pl) any PL array;
+    Grid.named("O1280") / Grid.named("F640") by name."""
     _release = "nb_grid_release"
 
-    def __init__(self, N: int):
+    def __init__(self, N: int = 0, *, _make=None):
         super().__init__()
-        check(lib().nb_grid_create_octahedral(int(N), ctypes.byref(self._h)))
-        self.N = int(N)
+        if _make is None:
+            check(lib().nb_grid_create_octahedral(int(N), ctypes.byref(self._h)))
+        else:
+            check(_make(ctypes.byref(self._h)))
+        n = ctypes.c_int()
+        check(lib().nb_grid_gaussian_number(self._h, ctypes.byref(n)))
+        self.N = n.value
+
+    @classmethod
+    def regular(cls, N: int) -> "Grid":
+        return cls(_make=lambda out: lib().nb_grid_create_regular(int(N), out))
+
+    @classmethod
+    def reduced(cls, pl) -> "Grid":
+        arr = np.ascontiguousarray(pl, dtype=np.int32)
+        return cls(_make=lambda out: lib().nb_grid_create_reduced(int(arr.size), arr.ctypes.data, out))
+
+    @classmethod
+    def named(cls, name: str) -> "Grid":
+        return cls(_make=lambda out: lib().nb_grid_create_named(name.encode(), out))
+
+    def pl(self) -> np.ndarray:
+        """Points per row, north to south."""
+        out = np.zeros(2 * self.N, dtype=np.int32)
+        check(lib().nb_grid_pl(self._h, out.ctypes.data))
+        return out
 
     @property
     def size(self) -> int:

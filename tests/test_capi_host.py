@@ -149,3 +149,40 @@ def test_allocator_and_server_poll_argument_checks():
     assert L.nb_set_allocator(None) == nabla.NB_OK
     done, res = ctypes.c_int32(), nabla.nb_result()
     assert L.nb_server_poll(None, 1, ctypes.byref(done), ctypes.byref(res)) == nabla.NB_EINVAL
+
+
+def _classic_like_pl(N):
+    o = oracle.row_nx(N)
+    pl = (np.round(o * 1.1 / 5) * 5 + (np.arange(2 * N) % 3 == 0)).astype(np.int32)
+    pl[N:] = pl[:N][::-1]
+    return pl
+
+
+@pytest.mark.parametrize("kind,N", [("F", 8), ("F", 80), ("P", 6), ("P", 32)])
+def test_other_grid_families_match_the_oracle(kind, N):
+    """Regular F<N> (Sec. 4.2.3.6) and PL-array grids (Sec. 4.2.3.7): same
+    points bit for bit and the same triangles as the independent oracle."""
+    pl = oracle.regular_nx(N) if kind == "F" else _classic_like_pl(N)
+    g = nabla.Grid.regular(N) if kind == "F" else nabla.Grid.reduced(pl)
+    assert g.N == N and np.array_equal(g.pl(), pl)
+    lat, lon = oracle.grid_lonlat(N, pl)
+    ll = g.lonlat()
+    assert np.array_equal(ll[:, 0], lon) and np.array_equal(ll[:, 1], lat)
+    canon = lambda t: {tuple(np.roll(r, -int(np.argmin(r)))) for r in t}  # oriented triangles
+    otri = canon(oracle.triangulate(N, pl))
+    for reorder in (0, 1):
+        m = nabla.Mesh(g, reorder)
+        assert (m.V, m.E, m.F) == (g.size, 3 * g.size - 6, 2 * g.size - 4)
+        assert canon(m.permutation()[m.triangles()]) == otri
+
+
+def test_grid_names_and_pl_checks():
+    assert nabla.Grid.named("O32").size == 5248
+    assert nabla.Grid.named("F16").size == 8 * 16 * 16
+    for bad in ("N16", "X16", "O", "O16x", "F0", ""):
+        with pytest.raises(nabla.NablaError) as e:
+            nabla.Grid.named(bad)
+        assert e.value.code == nabla.NB_EINVAL
+    for bad in ([20, 24, 20], [20, 2, 2, 20], [20]):
+        with pytest.raises(nabla.NablaError):
+            nabla.Grid.reduced(bad)
