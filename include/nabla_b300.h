@@ -292,6 +292,16 @@ int nb_nabla_laplacian_noalloc(const nb_method *method, const nb_field *f, const
 int nb_nabla_apply(const nb_method *method, int op, const nb_field *in, const nb_field *out,
                    const nb_field *scratch, void *stream);
 
+/* Copy a whole field between host memory laid out exactly like it (node
+ * stride included: nnodes x node_stride elements) and the device, enqueued
+ * on `stream` without waiting.  Pinned host memory makes the copy
+ * asynchronous and gives full link bandwidth; uploads and downloads on
+ * different streams use the two copy directions at once, and overlap
+ * operators running on a third stream (order them with CUDA events).
+ * Errors: NB_EINVAL (NULL), NB_EDTYPE, NB_ECUDA. */
+int nb_field_upload(const nb_field *dev, const void *host, void *stream);
+int nb_field_download(void *host, const nb_field *dev, void *stream);
+
 /* End-to-end call on HOST buffers: copy host_in (laid out exactly like
  * dev_in, node_stride included) to dev_in, apply op, copy dev_out back to
  * host_out and wait for the stream.  Pinned host memory gives full link

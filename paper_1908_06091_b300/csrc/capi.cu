@@ -633,6 +633,25 @@ int nb_nabla_laplacian(const nb_method *m, const nb_field *f, const nb_field *la
   return nb_nabla_apply(m, NB_OP_LAP, f, lap, scratch, stream);
 }
 
+static int field_copy(void *dst, const void *src, const nb_field *f, cudaMemcpyKind kind, void *stream,
+                      const char *who) {
+  NB_REQUIRE(f && dst && src, NB_EINVAL, std::string(who) + ": NULL argument");
+  NB_REQUIRE(f->dtype == NB_F32 || f->dtype == NB_F64, NB_EDTYPE, std::string(who) + ": unknown dtype");
+  NB_REQUIRE(f->nnodes >= 0 && f->node_stride >= 0, NB_EINVAL, std::string(who) + ": negative size");
+  const size_t bytes = (size_t)(f->nnodes * f->node_stride * (f->dtype == NB_F64 ? 8 : 4));
+  if (bytes == 0) return NB_OK;
+  NB_CUDA(cudaMemcpyAsync(dst, src, bytes, kind, static_cast<cudaStream_t>(stream)));
+  return NB_OK;
+}
+
+int nb_field_upload(const nb_field *dev, const void *host, void *stream) {
+  return field_copy(dev ? dev->data : nullptr, host, dev, cudaMemcpyHostToDevice, stream, "nb_field_upload");
+}
+
+int nb_field_download(void *host, const nb_field *dev, void *stream) {
+  return field_copy(host, dev ? dev->data : nullptr, dev, cudaMemcpyDeviceToHost, stream, "nb_field_download");
+}
+
 int nb_nabla_apply_host(const nb_method *m, int op, const void *host_in, void *host_out,
                         const nb_field *dev_in, const nb_field *dev_out,
                         const nb_field *scratch, void *stream) {

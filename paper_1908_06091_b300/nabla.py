@@ -115,6 +115,8 @@ SIGNATURES = {
     "nb_nabla_curl": [_P, _FP, _FP, _P],
     "nb_nabla_laplacian": [_P, _FP, _FP, _FP, _P],
     "nb_nabla_divcurl": [_P, _FP, _FP, _FP, _P],
+    "nb_field_upload": [_FP, _P, _P],
+    "nb_field_download": [_P, _FP, _P],
     "nb_nabla_apply": [_P, _I, _FP, _FP, _FP, _P],
     "nb_nabla_laplacian_noalloc": [_P, _FP, _FP, _P],
     "nb_nabla_apply_host": [_P, _I, _P, _P, _FP, _FP, _FP, _P],
@@ -431,6 +433,21 @@ def curl(method, uv, z, stream=None):
 
 def laplacian(method, f, lap, scratch=None, stream=None):
     return apply(method, OP_LAP, f, lap, scratch=scratch, stream=stream)
+
+
+def upload(field: torch.Tensor, host: torch.Tensor, nvar: int, stream=None):
+    """Enqueue the copy of a whole host field (laid out like `field`'s base
+    storage, node stride included) into the device field; returns at once."""
+    fv = field_view(field, nvar)
+    check(lib().nb_field_upload(ctypes.byref(fv), ctypes.c_void_p(host.data_ptr()),
+                                ctypes.c_void_p(_stream(stream))))
+
+
+def download(host: torch.Tensor, field: torch.Tensor, nvar: int, stream=None):
+    """Enqueue the copy of a whole device field to host memory; returns at once."""
+    fv = field_view(field, nvar)
+    check(lib().nb_field_download(ctypes.c_void_p(host.data_ptr()), ctypes.byref(fv),
+                                  ctypes.c_void_p(_stream(stream))))
 
 
 def divcurl(method, uv, d, z, stream=None):

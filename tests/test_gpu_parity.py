@@ -202,3 +202,22 @@ def test_host_buffer_entry_point_matches_device_call():
     host_out = torch.empty_like(out._base, device="cpu").pin_memory()
     nabla.apply_host(meth, "lap", host_in, host_out, fd, out)
     assert torch.equal(host_out[:, :9], ref.cpu())
+
+
+def test_field_upload_and_download_round_trip_on_streams():
+    g, m, meth = product(32)
+    fs = nabla.NodeColumns(meth, 9, torch.float32)
+    src = torch.randn((m.V, fs.lp, 2), dtype=torch.float32).pin_memory()
+    dev = fs.create_field(nvar=2, fill=0.0)
+    back = torch.zeros_like(src).pin_memory()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    nabla.upload(dev, src, 2, stream=s1)
+    ev = torch.cuda.Event()
+    ev.record(s1)
+    s2.wait_event(ev)
+    nabla.download(back, dev, 2, stream=s2)
+    s2.synchronize()
+    assert torch.equal(back, src)
+    with pytest.raises(nabla.NablaError):
+        fv = nabla.field_view(dev, 2)
+        nabla.check(nabla.lib().nb_field_upload(None, None, None))
