@@ -262,6 +262,15 @@ int nb_nabla_curl(const nb_method *method, const nb_field *uv, const nb_field *z
 int nb_nabla_divcurl(const nb_method *method, const nb_field *uv, const nb_field *d,
                      const nb_field *z, void *stream);
 
+/* Gradient and Laplacian of the same scalar field: f [V][L] -> g [V][L][2]
+ * and lap [V][L].  The Laplacian is the divergence of the gradient (Fig. 33),
+ * so its first pass is g itself: two launches instead of three.  Each output
+ * equals, bit for bit, what nb_nabla_gradient and nb_nabla_laplacian write
+ * for the same input.  Errors as for those calls (g is checked as the
+ * Laplacian's scratch: it must not overlap f or lap). */
+int nb_nabla_gradlap(const nb_method *method, const nb_field *f, const nb_field *g,
+                     const nb_field *lap, void *stream);
+
 /* Laplacian = divergence of the gradient: f [V][L] -> lap [V][L].
  * scratch: a [V][L][2] field of f's dtype receiving the intermediate
  * gradient, or NULL to let the library take stream-ordered memory from the

@@ -628,6 +628,20 @@ int nb_nabla_divcurl(const nb_method *m, const nb_field *uv, const nb_field *d, 
   NB_GUARD_END
 }
 
+int nb_nabla_gradlap(const nb_method *m, const nb_field *f, const nb_field *g, const nb_field *lap,
+                     void *stream) {
+  int st = nb::validate(m, NB_OP_GRAD, f, g, nullptr);
+  if (st != NB_OK) return st;
+  // g also serves as the Laplacian's scratch: same checks (no aliasing)
+  if ((st = nb::validate(m, NB_OP_LAP, f, lap, g)) != NB_OK) return st;
+  NB_GUARD_BEGIN
+  // the Laplacian's gradient pass is g: its divergence pass reads it
+  st = nb::launch_op(const_cast<nb_method *>(m), NB_OP_GRAD, f, g, nullptr, stream);
+  if (st == NB_OK) st = nb::launch_op(const_cast<nb_method *>(m), NB_OP_DIV, g, lap, nullptr, stream);
+  return st;
+  NB_GUARD_END
+}
+
 int nb_nabla_laplacian(const nb_method *m, const nb_field *f, const nb_field *lap,
                        const nb_field *scratch, void *stream) {
   return nb_nabla_apply(m, NB_OP_LAP, f, lap, scratch, stream);

@@ -115,6 +115,7 @@ SIGNATURES = {
     "nb_nabla_curl": [_P, _FP, _FP, _P],
     "nb_nabla_laplacian": [_P, _FP, _FP, _FP, _P],
     "nb_nabla_divcurl": [_P, _FP, _FP, _FP, _P],
+    "nb_nabla_gradlap": [_P, _FP, _FP, _FP, _P],
     "nb_field_upload": [_FP, _P, _P],
     "nb_field_download": [_P, _FP, _P],
     "nb_nabla_apply": [_P, _I, _FP, _FP, _FP, _P],
@@ -448,6 +449,14 @@ def download(host: torch.Tensor, field: torch.Tensor, nvar: int, stream=None):
     fv = field_view(field, nvar)
     check(lib().nb_field_download(ctypes.c_void_p(host.data_ptr()), ctypes.byref(fv),
                                   ctypes.c_void_p(_stream(stream))))
+
+
+def gradlap(method, f, g, lap, stream=None):
+    """Gradient into g and Laplacian into lap of one field; the Laplacian's
+    divergence pass reads g."""
+    fi, fg, fl = field_view(f, 1), field_view(g, 2), field_view(lap, 1)
+    check(lib().nb_nabla_gradlap(method.handle, ctypes.byref(fi), ctypes.byref(fg), ctypes.byref(fl),
+                                 ctypes.c_void_p(_stream(stream))))
 
 
 def divcurl(method, uv, d, z, stream=None):

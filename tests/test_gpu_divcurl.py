@@ -73,3 +73,32 @@ def test_fused_call_checks_outputs_before_any_launch():
                               None) == nabla.NB_ESHAPE
     assert nabla.launch_count() == before
     assert torch.count_nonzero(d).item() == 0
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64], ids=["f32", "f64"])
+@pytest.mark.parametrize("nlev", [7, 137])
+def test_gradlap_outputs_equal_gradient_and_laplacian_calls(nlev, dtype):
+    """nb_nabla_gradlap: the Laplacian's divergence pass reads the gradient
+    it returns; both outputs equal the single calls bit for bit."""
+    g_, m, meth = product(32)
+    om = oracle_mesh(32)
+    f, _ = inputs(om, nlev, 10, dtype)
+    fs = nabla.NodeColumns(meth, nlev, dtype)
+    fd = to_device(fs, f, m.permutation(), 1)
+    g = fs.create_field(nvar=2, fill=float("nan"))
+    lap = fs.create_field(fill=float("nan"))
+    nabla.gradlap(meth, fd, g, lap)
+    torch.cuda.synchronize()
+    lv = slice(0, nlev)
+    assert torch.equal(g[:, lv], run_op(meth, fs, "grad", fd)[:, lv])
+    assert torch.equal(lap[:, lv], run_op(meth, fs, "lap", fd)[:, lv])
+    ref = oracle_op(om, "lap", f.astype(np.float64))
+    assert rel_l2(to_grid(lap, m.permutation()), ref) <= TOL[dtype]
+    # g may not alias the Laplacian output
+    fl = nabla.field_view(lap, 1)
+    fg = nabla.field_view(g, 2)
+    fi = nabla.field_view(fd, 1)
+    bad = nabla.nb_field.from_buffer_copy(fg)
+    bad.data = fl.data
+    assert nabla.lib().nb_nabla_gradlap(meth.handle, ctypes.byref(fi), ctypes.byref(bad), ctypes.byref(fl),
+                                        None) != nabla.NB_OK
