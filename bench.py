@@ -300,6 +300,22 @@ def bench_ours(a):
             e1.record(stream)
             stream.synchronize()
             single[op] = round(e0.elapsed_time(e1) / a.single_op_reps, 4)
+    # the edge-based baseline (per-edge differences, then a node reduction)
+    edge_ms = {}
+    if a.single_op_reps > 0:
+        method.set_kernel(nabla.KERNEL_EDGE, 0)
+        with torch.cuda.stream(stream):
+            for op, xin, o in (("grad", f, outs[0]), ("div", uv, outs[1])):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                nabla.apply(method, op, xin, o, stream=stream)
+                e0.record(stream)
+                for _ in range(a.single_op_reps):
+                    nabla.apply(method, op, xin, o, stream=stream)
+                e1.record(stream)
+                stream.synchronize()
+                edge_ms[op] = round(e0.elapsed_time(e1) / a.single_op_reps, 4)
+        method.set_kernel(a.variant, a.tile)
+        torch.cuda.empty_cache()
 
     # FP64 GPU path on the same workload (the plain reference GPU path)
     fp64 = None
@@ -387,6 +403,7 @@ def bench_ours(a):
                    "setup_s": round(setup_s, 2)},
         "per_op": per_op,
         "single_op_ms": single,
+        "edge_variant_ms": edge_ms,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
                      "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
                      "peak_kind": peak_kind, "algorithmic_bytes": int(algo),

@@ -458,7 +458,13 @@ int nb_server_run_trace(nb_server *server, const nb_request *requests, const dou
 
 /* Kernel variant used for a call: NB_KERNEL_AUTO lets the library choose
  * (tuned table, else a size heuristic). */
-enum { NB_KERNEL_AUTO = 0, NB_KERNEL_DIRECT = 1, NB_KERNEL_TILED = 2 };
+enum { NB_KERNEL_AUTO = 0, NB_KERNEL_DIRECT = 1, NB_KERNEL_TILED = 2, NB_KERNEL_EDGE = 3 };
+/* NB_KERNEL_EDGE: the edge-based variant (the EdgeColumns pattern, Sec.
+ * 4.5), kept as a baseline: every call first materialises the difference of
+ * each edge's end columns (E x nlev x nvar values of stream-ordered scratch
+ * from the current allocator), then reduces per node through the node ->
+ * edge connectivity.  Results equal NB_KERNEL_DIRECT's bit for bit; the
+ * extra pass and traffic are its cost. */
 
 /* Force a kernel variant for subsequent calls on this method (tests and
  * tuning).  tile_nodes is the tiled variant's nodes per tile (0 = default). */

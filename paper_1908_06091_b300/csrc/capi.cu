@@ -356,7 +356,7 @@ int nb_method_device_bytes(const nb_method *m, int64_t *bytes) {
 
 int nb_method_set_kernel(nb_method *m, int variant, int tile_nodes) {
   NB_REQUIRE(m, NB_EINVAL, "nb_method_set_kernel: NULL method");
-  NB_REQUIRE(variant >= NB_KERNEL_AUTO && variant <= NB_KERNEL_TILED, NB_EINVAL,
+  NB_REQUIRE(variant >= NB_KERNEL_AUTO && variant <= NB_KERNEL_EDGE, NB_EINVAL,
              "nb_method_set_kernel: unknown variant");
   NB_REQUIRE(tile_nodes == 0 || (tile_nodes >= 8 && tile_nodes <= 1024), NB_EINVAL,
              "nb_method_set_kernel: tile_nodes must be 0 or in [8, 1024]");
@@ -532,6 +532,7 @@ int validate_op(const nb_method *m, int op, const nb_field *in, const nb_field *
 // One of grad, div, curl on the chosen kernel variant.
 static int launch_single(nb_method *m, int op, const nb_field *in, const nb_field *out,
                          cudaStream_t st) {
+  if (m->kernel_variant == NB_KERNEL_EDGE) return launch_edge(m, op, in, out, st);
   if (m->kernel_variant != NB_KERNEL_DIRECT) {
     bool handled = false;
     const int rc = launch_tiled(m, op, in, out, nullptr, st, &handled);
@@ -617,7 +618,7 @@ int nb_nabla_divcurl(const nb_method *m, const nb_field *uv, const nb_field *d, 
   nb_method *mm = const_cast<nb_method *>(m);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (mm->mesh->V == 0) return NB_OK;
-  if (mm->kernel_variant != NB_KERNEL_DIRECT) {
+  if (mm->kernel_variant == NB_KERNEL_AUTO || mm->kernel_variant == NB_KERNEL_TILED) {
     bool handled = false;
     const int rc = nb::launch_tiled(mm, NB_OP_DIV, uv, d, z, s, &handled);
     if (handled || rc != NB_OK) return rc;

@@ -112,6 +112,7 @@ struct nb_method : nb::RefCounted {
   int32_t *d_row_ptr = nullptr;     // V+1 (2E < 2^31 for N <= 8000)
   int32_t *d_nbr = nullptr;         // 2E
   int32_t *d_nbr_edge = nullptr;    // 2E
+  int32_t *d_edge = nullptr;        // [E][2] a < b
   // device: FP64 raw geometry
   double *d_vol = nullptr, *d_S = nullptr, *d_T = nullptr, *d_east = nullptr, *d_north = nullptr;
   // device: per CSR entry operator weights (FP64 and FP32 rounding)

@@ -88,6 +88,7 @@ __device__ __forceinline__ void load_vector_f32(const float *col, int l0, int nl
 }
 
 int launch_direct(const nb_method *m, int op, const nb_field *in, const nb_field *out,
-                  cudaStream_t st);
+                  cudaStream_t st, const void *q = nullptr, int64_t q_stride = 0);
+int launch_edge(nb_method *m, int op, const nb_field *in, const nb_field *out, cudaStream_t st);
 
 }  // namespace nb

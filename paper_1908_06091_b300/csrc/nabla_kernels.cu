@@ -111,6 +111,7 @@ int method_upload(nb_method *m) {
   UP(m->d_row_ptr, rp.data(), V + 9);
   UP(m->d_nbr, mesh->nbr.data(), P);
   UP(m->d_nbr_edge, mesh->nbr_edge.data(), P);
+  UP(m->d_edge, mesh->edge.data(), 2 * E);
   UP(m->d_vol, m->vol.data(), V);
   UP(m->d_S, m->S.data(), 3 * E);
   UP(m->d_T, m->T.data(), 3 * E);
@@ -174,10 +175,18 @@ struct DirectArgs {
   int64_t in_stride;
   void *out;
   int64_t out_stride;
+  // edge variant: per-edge differences q[e] = x[b] - x[a] (edges a < b), row
+  // stride q_stride; a node i takes +q for a neighbour j > i and -q otherwise
+  // (the same value x_j - x_i rounds to: IEEE subtraction is antisymmetric)
+  const void *q;
+  int64_t q_stride;
+  const int32_t *nbr_edge;
 };
 
-// op 0: grad.  FP32 arithmetic, compensated or plain accumulation.
-template <int LPT, class Acc>
+// op 0: grad.  FP32 arithmetic, compensated or plain accumulation.  EDGE:
+// neighbour differences come from the per-edge array (non-pole nodes; the
+// FP64 pole rows keep their FP64 differences).
+template <int LPT, class Acc, bool EDGE = false>
 __global__ void __launch_bounds__(256) grad_direct_f32(DirectArgs a) {
   const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t i = item / a.ngroups;
@@ -194,13 +203,23 @@ __global__ void __launch_bounds__(256) grad_direct_f32(DirectArgs a) {
     for (int32_t p = p0; p < p1; ++p) {
       const int32_t j = __ldg(a.nbr + p);
       const float2 wp = __ldg(w + p);
-      float fj[LPT];
-      load_scalar_f32<LPT>(f + (int64_t)j * a.in_stride, l0, a.nlev, fj);
+      float dj[LPT];
+      if (EDGE) {
+        load_scalar_f32<LPT>(static_cast<const float *>(a.q) + (int64_t)__ldg(a.nbr_edge + p) * a.q_stride, l0,
+                             a.nlev, dj);
+        if (j < i)
+#pragma unroll
+          for (int k = 0; k < LPT; ++k) dj[k] = -dj[k];
+      } else {
+        float fj[LPT];
+        load_scalar_f32<LPT>(f + (int64_t)j * a.in_stride, l0, a.nlev, fj);
+#pragma unroll
+        for (int k = 0; k < LPT; ++k) dj[k] = __fsub_rn(fj[k], fi[k]);
+      }
 #pragma unroll
       for (int k = 0; k < LPT; ++k) {
-        const float d = __fsub_rn(fj[k], fi[k]);
-        ax[k].add_prod(wp.x, d);
-        ay[k].add_prod(wp.y, d);
+        ax[k].add_prod(wp.x, dj[k]);
+        ay[k].add_prod(wp.y, dj[k]);
       }
     }
 #pragma unroll
@@ -245,7 +264,7 @@ __global__ void __launch_bounds__(256) grad_direct_f32(DirectArgs a) {
 }
 
 // op 1 / 2: div or curl (same stencil, different weights).
-template <int LPT, class Acc>
+template <int LPT, class Acc, bool EDGE = false>
 __global__ void __launch_bounds__(256) divcurl_direct_f32(DirectArgs a) {
   const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t i = item / a.ngroups;
@@ -263,13 +282,27 @@ __global__ void __launch_bounds__(256) divcurl_direct_f32(DirectArgs a) {
     for (int32_t p = p0; p < p1; ++p) {
       const int32_t j = __ldg(a.nbr + p);
       const float2 wp = __ldg(w + p);
-      float uj[LPT], vj[LPT];
-      load_vector_f32<LPT>(uv + (int64_t)j * a.in_stride, l0, a.nlev, uj, vj);
+      float du[LPT], dv[LPT];
+      if (EDGE) {
+        load_vector_f32<LPT>(static_cast<const float *>(a.q) + (int64_t)__ldg(a.nbr_edge + p) * a.q_stride, l0,
+                             a.nlev, du, dv);
+        if (j < i)
 #pragma unroll
-      for (int k = 0; k < LPT; ++k) {
-        const float du = __fsub_rn(uj[k], ui[k]), dv = __fsub_rn(vj[k], vi[k]);
-        acc[k].add(__fmaf_rn(wp.x, du, __fmul_rn(wp.y, dv)));
+          for (int k = 0; k < LPT; ++k) {
+            du[k] = -du[k];
+            dv[k] = -dv[k];
+          }
+      } else {
+        float uj[LPT], vj[LPT];
+        load_vector_f32<LPT>(uv + (int64_t)j * a.in_stride, l0, a.nlev, uj, vj);
+#pragma unroll
+        for (int k = 0; k < LPT; ++k) {
+          du[k] = __fsub_rn(uj[k], ui[k]);
+          dv[k] = __fsub_rn(vj[k], vi[k]);
+        }
       }
+#pragma unroll
+      for (int k = 0; k < LPT; ++k) acc[k].add(__fmaf_rn(wp.x, du[k], __fmul_rn(wp.y, dv[k])));
     }
 #pragma unroll
     for (int k = 0; k < LPT; ++k) {
@@ -309,7 +342,7 @@ __global__ void __launch_bounds__(256) divcurl_direct_f32(DirectArgs a) {
 }
 
 // FP64 path: plain FP64 arithmetic everywhere (the reference GPU path).
-template <int LPT>
+template <int LPT, bool EDGE = false>
 __global__ void __launch_bounds__(256) grad_direct_f64(DirectArgs a) {
   const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t i = item / a.ngroups;
@@ -326,10 +359,12 @@ __global__ void __launch_bounds__(256) grad_direct_f64(DirectArgs a) {
   for (int32_t p = p0; p < p1; ++p) {
     const int32_t j = __ldg(a.nbr + p);
     const double2 wp = __ldg(w + p);
-    const double *cj = f + (int64_t)j * a.in_stride;
+    const double *cj = EDGE ? static_cast<const double *>(a.q) + (int64_t)__ldg(a.nbr_edge + p) * a.q_stride
+                            : f + (int64_t)j * a.in_stride;
 #pragma unroll
     for (int k = 0; k < LPT; ++k) {
-      const double d = ((l0 + k < a.nlev) ? __ldg(cj + l0 + k) : 0.0) - fi[k];
+      const double x = (l0 + k < a.nlev) ? __ldg(cj + l0 + k) : 0.0;
+      const double d = EDGE ? (j < i ? -x : x) : x - fi[k];
       sx[k] = fma(wp.x, d, sx[k]);
       sy[k] = fma(wp.y, d, sy[k]);
     }
@@ -343,7 +378,7 @@ __global__ void __launch_bounds__(256) grad_direct_f64(DirectArgs a) {
     }
 }
 
-template <int LPT>
+template <int LPT, bool EDGE = false>
 __global__ void __launch_bounds__(256) divcurl_direct_f64(DirectArgs a) {
   const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t i = item / a.ngroups;
@@ -365,14 +400,17 @@ __global__ void __launch_bounds__(256) divcurl_direct_f64(DirectArgs a) {
   for (int32_t p = p0; p < p1; ++p) {
     const int32_t j = __ldg(a.nbr + p);
     const double2 wp = __ldg(w + p);
-    const double *cj = uv + (int64_t)j * a.in_stride;
+    const double *cj = EDGE ? static_cast<const double *>(a.q) + (int64_t)__ldg(a.nbr_edge + p) * a.q_stride
+                            : uv + (int64_t)j * a.in_stride;
 #pragma unroll
     for (int k = 0; k < LPT; ++k) {
       const bool ok = l0 + k < a.nlev;
-      const double uj = ok ? __ldg(cj + 2 * (l0 + k)) : 0.0;
-      const double vj = ok ? __ldg(cj + 2 * (l0 + k) + 1) : 0.0;
-      s[k] = fma(wp.x, uj - ui[k], s[k]);
-      s[k] = fma(wp.y, vj - vi[k], s[k]);
+      const double xu = ok ? __ldg(cj + 2 * (l0 + k)) : 0.0;
+      const double xv = ok ? __ldg(cj + 2 * (l0 + k) + 1) : 0.0;
+      const double du = EDGE ? (j < i ? -xu : xu) : xu - ui[k];
+      const double dv = EDGE ? (j < i ? -xv : xv) : xv - vi[k];
+      s[k] = fma(wp.x, du, s[k]);
+      s[k] = fma(wp.y, dv, s[k]);
     }
   }
   double *oo = o + i * a.out_stride + l0;
@@ -384,13 +422,40 @@ __global__ void __launch_bounds__(256) divcurl_direct_f64(DirectArgs a) {
   }
 }
 
+// Edge pass of the edge variant: q[e][k] = x[b][k] - x[a][k] for the nvals
+// values (levels x components) of every edge (a, b), a < b.  VEC: 16-byte
+// groups (rows 16-byte aligned), else one value per thread.
+template <class T, bool VEC>
+__global__ void __launch_bounds__(256) edge_diff_kernel(int64_t E, const int32_t *__restrict__ edge,
+                                                        const T *__restrict__ x, int64_t x_stride, int nvals,
+                                                        T *__restrict__ q, int64_t q_stride) {
+  constexpr int W = VEC ? 16 / (int)sizeof(T) : 1;
+  const int per = (nvals + W - 1) / W;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t e = t / per;
+  if (e >= E) return;
+  const int k = (int)(t - e * per) * W;
+  const int64_t a = __ldg(edge + 2 * e), b = __ldg(edge + 2 * e + 1);
+  if (VEC) {
+    const float4 xa = __ldg(reinterpret_cast<const float4 *>(x + a * x_stride + k));
+    const float4 xb = __ldg(reinterpret_cast<const float4 *>(x + b * x_stride + k));
+    if constexpr (sizeof(T) == 4) {
+      *reinterpret_cast<float4 *>(q + e * q_stride + k) =
+          make_float4(__fsub_rn(xb.x, xa.x), __fsub_rn(xb.y, xa.y), __fsub_rn(xb.z, xa.z), __fsub_rn(xb.w, xa.w));
+    }
+  } else {
+    q[e * q_stride + k] = x[b * x_stride + k] - x[a * x_stride + k];
+  }
+}
+
 // ------------------------------------------------------------------ launch
 
 static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
-// Launch one op (0 grad, 1 div, 2 curl) with the direct kernels.
+// Launch one op (0 grad, 1 div, 2 curl) with the direct kernels; with q
+// (edge variant) the neighbour differences come from the per-edge array.
 int launch_direct(const nb_method *m, int op, const nb_field *in, const nb_field *out,
-                  cudaStream_t st) {
+                  cudaStream_t st, const void *q, int64_t q_stride) {
   const nb_mesh *mesh = m->mesh;
   const bool f64 = in->dtype == NB_F64;
   DirectArgs a;
@@ -407,9 +472,13 @@ int launch_direct(const nb_method *m, int op, const nb_field *in, const nb_field
   a.in_stride = in->node_stride;
   a.out = out->data;
   a.out_stride = out->node_stride;
+  a.q = q;
+  a.q_stride = q_stride;
+  a.nbr_edge = m->d_nbr_edge;
+  const bool edge = q != nullptr;
   // 16-byte vectors need aligned bases and strides that are multiples of 4 floats
   const bool vec = !f64 && in->nlev >= 4 && aligned16(in->data) && aligned16(out->data) &&
-                   in->node_stride % 4 == 0 && out->node_stride % 4 == 0;
+                   in->node_stride % 4 == 0 && out->node_stride % 4 == 0 && (!edge || q_stride % 4 == 0);
   const int LPT = f64 ? 2 : (vec ? 4 : 1);
   a.ngroups = (in->nlev + LPT - 1) / LPT;
   const int threads = 256;
@@ -421,7 +490,28 @@ int launch_direct(const nb_method *m, int op, const nb_field *in, const nb_field
   }
   const bool comp = m->compensated != 0;
   const unsigned nb = (unsigned)blocks;
-  if (f64) {
+  if (edge) {
+    if (f64) {
+      if (op == 0) grad_direct_f64<2, true><<<nb, threads, 0, st>>>(a);
+      else divcurl_direct_f64<2, true><<<nb, threads, 0, st>>>(a);
+    } else if (vec) {
+      if (op == 0) {
+        if (comp) grad_direct_f32<4, KahanAcc, true><<<nb, threads, 0, st>>>(a);
+        else grad_direct_f32<4, PlainAcc, true><<<nb, threads, 0, st>>>(a);
+      } else {
+        if (comp) divcurl_direct_f32<4, KahanAcc, true><<<nb, threads, 0, st>>>(a);
+        else divcurl_direct_f32<4, PlainAcc, true><<<nb, threads, 0, st>>>(a);
+      }
+    } else {
+      if (op == 0) {
+        if (comp) grad_direct_f32<1, KahanAcc, true><<<nb, threads, 0, st>>>(a);
+        else grad_direct_f32<1, PlainAcc, true><<<nb, threads, 0, st>>>(a);
+      } else {
+        if (comp) divcurl_direct_f32<1, KahanAcc, true><<<nb, threads, 0, st>>>(a);
+        else divcurl_direct_f32<1, PlainAcc, true><<<nb, threads, 0, st>>>(a);
+      }
+    }
+  } else if (f64) {
     if (op == 0) grad_direct_f64<2><<<nb, threads, 0, st>>>(a);
     else divcurl_direct_f64<2><<<nb, threads, 0, st>>>(a);
   } else if (vec) {
@@ -444,6 +534,54 @@ int launch_direct(const nb_method *m, int op, const nb_field *in, const nb_field
   count_launch(1);
   NB_CUDA(cudaGetLastError());
   return NB_OK;
+}
+
+// Edge variant (the EdgeColumns pattern, Sec. 4.5): materialise the
+// difference of every edge's end columns, q[e] = x[b] - x[a] (E x nlev x
+// nvar values, stream-ordered scratch), then reduce per node from q through
+// the node -> edge connectivity.  Results equal the direct kernels' bit for
+// bit; the point of the variant is the cost of the extra pass and traffic.
+int launch_edge(nb_method *m, int op, const nb_field *in, const nb_field *out, cudaStream_t st) {
+  const bool f64 = in->dtype == NB_F64;
+  const int64_t elem = f64 ? 8 : 4;
+  const int q4 = f64 ? 2 : 4;
+  const int64_t lq = (int64_t)((in->nlev + q4 - 1) / q4) * q4;
+  const int64_t q_stride = lq * in->nvar;
+  const int64_t E = m->mesh->E;
+  const size_t bytes = (size_t)(E * q_stride * elem);
+  void *q = nullptr;
+  const DevAlloc alloc = current_allocator();
+  int rc = dev_alloc_async(alloc, &q, bytes, st, "edge variant scratch");
+  if (rc != NB_OK) return rc;
+  const int nvals = in->nlev * in->nvar;
+  const bool vec = !f64 && aligned16(in->data) && in->node_stride % 4 == 0;
+  const int per = vec ? (nvals + 3) / 4 : nvals;
+  const int64_t blocks = (E * per + 255) / 256;
+  if (blocks > 0x7fffffff) {
+    dev_free_async(alloc, q, bytes, st);
+    set_error("edge variant: problem too large for one grid");
+    return NB_EINVAL;
+  }
+  if (f64)
+    edge_diff_kernel<double, false><<<(unsigned)blocks, 256, 0, st>>>(
+        E, m->d_edge, static_cast<const double *>(in->data), in->node_stride, nvals, static_cast<double *>(q),
+        q_stride);
+  else if (vec)
+    edge_diff_kernel<float, true><<<(unsigned)blocks, 256, 0, st>>>(
+        E, m->d_edge, static_cast<const float *>(in->data), in->node_stride, nvals, static_cast<float *>(q),
+        q_stride);
+  else
+    edge_diff_kernel<float, false><<<(unsigned)blocks, 256, 0, st>>>(
+        E, m->d_edge, static_cast<const float *>(in->data), in->node_stride, nvals, static_cast<float *>(q),
+        q_stride);
+  count_launch(1);
+  if ((rc = cudaGetLastError()) != cudaSuccess) {
+    dev_free_async(alloc, q, bytes, st);
+    return cuda_fail((cudaError_t)rc, "edge_diff_kernel");
+  }
+  rc = launch_direct(m, op, in, out, st, q, q_stride);
+  const int rf = dev_free_async(alloc, q, bytes, st);
+  return rc != NB_OK ? rc : rf;
 }
 
 }  // namespace nb

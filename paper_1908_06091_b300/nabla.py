@@ -30,7 +30,7 @@ NB_OK, NB_EINVAL, NB_ESHAPE, NB_EDTYPE, NB_EOOM, NB_ECUDA, NB_ETIMEOUT, NB_EBUDG
 NB_F32, NB_F64 = 0, 1
 OP_GRAD, OP_DIV, OP_CURL, OP_LAP = 0, 1, 2, 3
 OPS = {"grad": OP_GRAD, "div": OP_DIV, "curl": OP_CURL, "lap": OP_LAP}
-KERNEL_AUTO, KERNEL_DIRECT, KERNEL_TILED = 0, 1, 2
+KERNEL_AUTO, KERNEL_DIRECT, KERNEL_TILED, KERNEL_EDGE = 0, 1, 2, 3
 EARTH_RADIUS_M = 6.37122e6
 
 
