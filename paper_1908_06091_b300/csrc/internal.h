@@ -121,6 +121,7 @@ struct nb_method : nb::RefCounted {
   double *d_sdiv64 = nullptr, *d_scurl64 = nullptr;
   float *d_wgrad32 = nullptr, *d_wdiv32 = nullptr, *d_wcurl32 = nullptr;
   float *d_sdiv32 = nullptr, *d_scurl32 = nullptr;
+  float *d_wdc32 = nullptr, *d_sdc32 = nullptr;  // fused div+curl: float4 records
   int64_t device_bytes = 0;
   nb::DevAlloc alloc;                // allocator current at creation
   std::vector<nb::DevBlock> blocks;  // every device block of the method and its plans

@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(256) setup_weights_kernel(
     const double *__restrict__ S, const double *__restrict__ T, const double *__restrict__ east,
     const double *__restrict__ north, double2 *wgrad64, double2 *wdiv64, double2 *wcurl64,
     double2 *sdiv64, double2 *scurl64, float2 *wgrad32, float2 *wdiv32, float2 *wcurl32,
-    float2 *sdiv32, float2 *scurl32) {
+    float2 *sdiv32, float2 *scurl32, float4 *wdc32, float4 *sdc32) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= V) return;
   const double h = 0.5 / vol[i];
@@ -79,11 +79,13 @@ __global__ void __launch_bounds__(256) setup_weights_kernel(
     wgrad32[p] = make_float2((float)gx, (float)gy);
     wdiv32[p] = make_float2((float)du, (float)dv);
     wcurl32[p] = make_float2((float)cu, (float)cv);
+    wdc32[p] = make_float4((float)du, (float)dv, (float)cu, (float)cv);
   }
   sdiv64[i] = make_double2(su, sv);
   scurl64[i] = make_double2(tu, tv);
   sdiv32[i] = make_float2((float)su, (float)sv);
   scurl32[i] = make_float2((float)tu, (float)tv);
+  sdc32[i] = make_float4((float)su, (float)sv, (float)tu, (float)tv);
 }
 
 template <class T>
@@ -128,6 +130,9 @@ int method_upload(nb_method *m) {
   // self weights are staged in even-aligned node pairs: one spare node
   UP(m->d_sdiv32, nullptr, 2 * V + 4);
   UP(m->d_scurl32, nullptr, 2 * V + 4);
+  // fused div+curl records: (du, dv, cu, cv) per CSR entry, (su, sv, tu, tv) per node
+  UP(m->d_wdc32, nullptr, 4 * P);
+  UP(m->d_sdc32, nullptr, 4 * V + 4);
 #undef UP
   const int threads = 256;
   const int64_t blocks = (V + threads - 1) / threads;
@@ -136,7 +141,7 @@ int method_upload(nb_method *m) {
       (double2 *)m->d_wgrad64, (double2 *)m->d_wdiv64, (double2 *)m->d_wcurl64,
       (double2 *)m->d_sdiv64, (double2 *)m->d_scurl64, (float2 *)m->d_wgrad32,
       (float2 *)m->d_wdiv32, (float2 *)m->d_wcurl32, (float2 *)m->d_sdiv32,
-      (float2 *)m->d_scurl32);
+      (float2 *)m->d_scurl32, (float4 *)m->d_wdc32, (float4 *)m->d_sdc32);
   count_launch(1);
   NB_CUDA(cudaGetLastError());
   NB_CUDA(cudaDeviceSynchronize());

@@ -170,9 +170,9 @@ struct TiledArgs {
   const double2 *w64;
   const float2 *s32;
   const double2 *s64;
-  const float2 *w32b;   // fused div+curl: the curl weights (else unused)
-  const double2 *w64b;
-  const float2 *s32b;
+  const float4 *w4;     // fused div+curl: (du, dv, cu, cv) per CSR entry (else unused)
+  const double2 *w64b;  // fused div+curl: FP64 curl weights and self weights (pole rows)
+  const float4 *s4;     // fused div+curl: (su, sv, tu, tv) per node
   const double2 *s64b;
   float *out2;          // fused div+curl: the curl output (same strides as out)
   const char *in;
@@ -188,7 +188,7 @@ struct TiledArgs {
   uint32_t gpitch;     // shared-memory pitch of a group of four halo columns
   uint32_t off_w, off_l, off_r;  // stage offsets of the staged weights, offsets, row pointers
   uint32_t off_s;      // stage offset of the tile's self weights (div / curl; 0 = not staged)
-  uint32_t off_w2, off_s2;  // fused div+curl: stage offsets of the curl weights (0 = not staged)
+  int rec16;           // fused div+curl: weights and self weights staged as 16-byte records
   uint32_t off_h;      // stage offset of the tile header: first and end node
   uint32_t stage_bytes;
   int nstages;
@@ -203,32 +203,36 @@ __device__ __forceinline__ void issue_tile(const TiledArgs &a, const CUtensorMap
   const int32_t h0 = __ldg(a.halo_ptr + t), h1 = __ldg(a.halo_ptr + t + 1);
   const int32_t pa = __ldg(a.row_ptr + n0), pb = __ldg(a.row_ptr + n1);
   const uint32_t n = (uint32_t)(n1 - n0), H = (uint32_t)(h1 - h0);
-  const int32_t wa = pa & ~1, wb = (pb + 1) & ~1;
+  // 8-byte weights are copied from an even entry; 16-byte records as they are
+  const int32_t wa = a.rec16 ? pa : (pa & ~1), wb = a.rec16 ? pb : ((pb + 1) & ~1);
   const int32_t la = pa & ~3, lb = (pb + 3) & ~3;
   const int32_t ra = n0 & ~3, rb = (n1 + 4) & ~3;
   const uint32_t body = (n - 1) * a.row_bytes + a.copy_bytes;
-  const uint32_t wbytes = (uint32_t)(wb - wa) * 8u, lbytes = (uint32_t)(lb - la) * 4u,
+  const uint32_t wbytes = (uint32_t)(wb - wa) * (a.rec16 ? 16u : 8u), lbytes = (uint32_t)(lb - la) * 4u,
                  rbytes = (uint32_t)(rb - ra) * 4u;
   const uint32_t groups = (H + 3u) >> 2;
   const uint32_t hbase = (n * a.row_bytes + 127u) & ~127u;
-  const int32_t sa = n0 & ~1, sb = (n1 + 1) & ~1;
-  const uint32_t sbytes = a.off_s ? (uint32_t)(sb - sa) * 8u : 0u;
-  const uint32_t w2bytes = a.off_w2 ? wbytes : 0u, s2bytes = a.off_w2 ? sbytes : 0u;
+  const int32_t sa = a.rec16 ? n0 : (n0 & ~1), sb = a.rec16 ? n1 : ((n1 + 1) & ~1);
+  const uint32_t sbytes = a.off_s ? (uint32_t)(sb - sa) * (a.rec16 ? 16u : 8u) : 0u;
   if (lane == 0) {
     // header for the consumers, published by the arrive below
     asm volatile("st.shared.v2.s32 [%0], {%1, %2};" ::"r"(stage + a.off_h), "r"(n0), "r"(n1) : "memory");
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   if (lane == 0)
-    mbar_expect_tx(bar, body + wbytes + lbytes + rbytes + sbytes + w2bytes + s2bytes + groups * 4u * a.copy_bytes);
+    mbar_expect_tx(bar, body + wbytes + lbytes + rbytes + sbytes + groups * 4u * a.copy_bytes);
   __syncwarp();
   if (lane == 0) bulk_g2s(stage, a.in + (int64_t)n0 * a.in_stride * 4, body, bar);
-  if (lane == 1) bulk_g2s(stage + a.off_w, a.w32 + wa, wbytes, bar);
+  if (lane == 1) {
+    if (a.rec16) bulk_g2s(stage + a.off_w, a.w4 + wa, wbytes, bar);
+    else bulk_g2s(stage + a.off_w, a.w32 + wa, wbytes, bar);
+  }
   if (lane == 2) bulk_g2s(stage + a.off_l, a.loff + la, lbytes, bar);
   if (lane == 3) bulk_g2s(stage + a.off_r, a.row_ptr + ra, rbytes, bar);
-  if (lane == 4 && sbytes) bulk_g2s(stage + a.off_s, a.s32 + sa, sbytes, bar);
-  if (lane == 5 && w2bytes) bulk_g2s(stage + a.off_w2, a.w32b + wa, w2bytes, bar);
-  if (lane == 6 && s2bytes) bulk_g2s(stage + a.off_s2, a.s32b + sa, s2bytes, bar);
+  if (lane == 4 && sbytes) {
+    if (a.rec16) bulk_g2s(stage + a.off_s, a.s4 + sa, sbytes, bar);
+    else bulk_g2s(stage + a.off_s, a.s32 + sa, sbytes, bar);
+  }
   for (uint32_t g = lane; g < groups; g += 32) {
     // a short last group repeats its last node (the copy fills the group's slots)
     const int32_t *hp = a.halo + h0;
@@ -282,11 +286,11 @@ struct TileView {
     n0 = lds_s32(stage + a.off_h);
     n1 = lds_s32(stage + a.off_h + 4u);
     rows = stage;
-    s = stage + a.off_s - 8u * (uint32_t)(n0 & ~1);
+    s = a.rec16 ? stage + a.off_s - 16u * (uint32_t)n0 : stage + a.off_s - 8u * (uint32_t)(n0 & ~1);
     const int32_t ra = n0 & ~3;
     r = stage + a.off_r - 4u * (uint32_t)ra;
     pa = lds_s32(r + 4u * (uint32_t)n0);
-    w = stage + a.off_w - 8u * (uint32_t)(pa & ~1);
+    w = a.rec16 ? stage + a.off_w - 16u * (uint32_t)pa : stage + a.off_w - 8u * (uint32_t)(pa & ~1);
     l = stage + a.off_l - 4u * (uint32_t)(pa & ~3);
   }
   int32_t pa;  // CSR index of the tile's first entry
@@ -317,9 +321,6 @@ __device__ __forceinline__ void divcurl_tile(const TiledArgs &a, int t, uint32_t
   const int units = (a.nlev + 1) / 2;
   const uint32_t rb = a.row_bytes;
   const uint32_t g16 = 16u * (uint32_t)a.G;
-  // second weight set and self weights (curl of the fused pass)
-  const uint32_t w2base = stage + a.off_w2 - 8u * (uint32_t)(v.pa & ~1);
-  const uint32_t s2base = stage + a.off_s2 - 8u * (uint32_t)(v.n0 & ~1);
   for (uint32_t item = i0 + (threadIdx.x & 31); item < i1; item += 32) {
     const uint32_t il = (uint32_t)(((uint64_t)item * a.g_magic) >> a.g_shift);
     const uint32_t c = item - il * a.G;
@@ -335,7 +336,13 @@ __device__ __forceinline__ void divcurl_tile(const TiledArgs &a, int t, uint32_t
       lds2x64(colA + il * rb, i0p, i1p);
       lds2x64(colB + il * rb, i2p, i3p);
       Kahan2<COMP> k0, k1, k2, k3, q0, q1, q2, q3;
-      const uint32_t pw = v.w + 8u * (uint32_t)p0, pw2 = w2base + 8u * (uint32_t)p0;
+      // weights of entry e: single pass, 8-byte (w.x, w.y) at pw + 8 e; fused,
+      // 16-byte (div, curl) records at pw + 16 e
+      const uint32_t pw = v.w + (FUSED ? 16u : 8u) * (uint32_t)p0;
+      auto weights = [&](uint32_t e, f2_t &wd, f2_t &wc) {
+        if (FUSED) lds2x64(pw + 16u * e, wd, wc);
+        else wd = lds_b64(pw + 8u * e);
+      };
       const uint32_t pl = v.l + 4u * (uint32_t)p0;
       // differences of neighbour entry e: units (c, c + G) minus the node's own
       auto diffs = [&](uint32_t e, f2_t (&d)[4]) {
@@ -353,13 +360,15 @@ __device__ __forceinline__ void divcurl_tile(const TiledArgs &a, int t, uint32_t
         diffs(e, d0);
         diffs(e + 1u, d1);
         diffs(e + 2u, d2);
-        const f2_t w0 = lds_b64(pw + 8u * e), w1 = lds_b64(pw + 8u * e + 8u), w2 = lds_b64(pw + 8u * e + 16u);
+        f2_t w0, w1, w2, x0 = 0ull, x1 = 0ull, x2 = 0ull;
+        weights(e, w0, x0);
+        weights(e + 1u, w1, x1);
+        weights(e + 2u, w2, x2);
         k0.add_triple(w0, d0[0], w1, d1[0], w2, d2[0]);
         k1.add_triple(w0, d0[1], w1, d1[1], w2, d2[1]);
         k2.add_triple(w0, d0[2], w1, d1[2], w2, d2[2]);
         k3.add_triple(w0, d0[3], w1, d1[3], w2, d2[3]);
         if (FUSED) {
-          const f2_t x0 = lds_b64(pw2 + 8u * e), x1 = lds_b64(pw2 + 8u * e + 8u), x2 = lds_b64(pw2 + 8u * e + 16u);
           q0.add_triple(x0, d0[0], x1, d1[0], x2, d2[0]);
           q1.add_triple(x0, d0[1], x1, d1[1], x2, d2[1]);
           q2.add_triple(x0, d0[2], x1, d1[2], x2, d2[2]);
@@ -370,13 +379,14 @@ __device__ __forceinline__ void divcurl_tile(const TiledArgs &a, int t, uint32_t
         f2_t d0[4], d1[4];
         diffs(e, d0);
         diffs(e + 1u, d1);
-        const f2_t w0 = lds_b64(pw + 8u * e), w1 = lds_b64(pw + 8u * e + 8u);
+        f2_t w0, w1, x0 = 0ull, x1 = 0ull;
+        weights(e, w0, x0);
+        weights(e + 1u, w1, x1);
         k0.add_pair(w0, d0[0], w1, d1[0]);
         k1.add_pair(w0, d0[1], w1, d1[1]);
         k2.add_pair(w0, d0[2], w1, d1[2]);
         k3.add_pair(w0, d0[3], w1, d1[3]);
         if (FUSED) {
-          const f2_t x0 = lds_b64(pw2 + 8u * e), x1 = lds_b64(pw2 + 8u * e + 8u);
           q0.add_pair(x0, d0[0], x1, d1[0]);
           q1.add_pair(x0, d0[1], x1, d1[1]);
           q2.add_pair(x0, d0[2], x1, d1[2]);
@@ -386,13 +396,13 @@ __device__ __forceinline__ void divcurl_tile(const TiledArgs &a, int t, uint32_t
       auto single = [&](uint32_t e) {
         f2_t d0[4];
         diffs(e, d0);
-        const f2_t w0 = lds_b64(pw + 8u * e);
+        f2_t w0, x0 = 0ull;
+        weights(e, w0, x0);
         k0.add_prod(w0, d0[0]);
         k1.add_prod(w0, d0[1]);
         k2.add_prod(w0, d0[2]);
         k3.add_prod(w0, d0[3]);
         if (FUSED) {
-          const f2_t x0 = lds_b64(pw2 + 8u * e);
           q0.add_prod(x0, d0[0]);
           q1.add_prod(x0, d0[1]);
           q2.add_prod(x0, d0[2]);
@@ -409,8 +419,11 @@ __device__ __forceinline__ void divcurl_tile(const TiledArgs &a, int t, uint32_t
         if (e < deg) single((uint32_t)e);
       }
       const f2_t self[4] = {i0p, i1p, i2p, i3p};
+      f2_t sw_div, sw_curl = 0ull;
+      if (FUSED) lds2x64(v.s + 16u * (uint32_t)node, sw_div, sw_curl);
+      else sw_div = lds_b64(v.s + 8u * (uint32_t)node);
       {
-        const f2_t sw = lds_b64(v.s + 8u * (uint32_t)node);
+        const f2_t sw = sw_div;
         const f2_t vals[4] = {k0.value(), k1.value(), k2.value(), k3.value()};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -420,7 +433,7 @@ __device__ __forceinline__ void divcurl_tile(const TiledArgs &a, int t, uint32_t
         }
       }
       if (FUSED) {
-        const f2_t sw = lds_b64(s2base + 8u * (uint32_t)node);
+        const f2_t sw = sw_curl;
         const f2_t vals[4] = {q0.value(), q1.value(), q2.value(), q3.value()};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -808,11 +821,11 @@ int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, 
   const int fit_nodes = (int)(stage_target / row_bytes) + 1;
   const int nmax = std::max(1, std::min(nmax_req, fit_nodes));
   const int ecap = 7 * nmax + 16;
-  const uint32_t wsz = up16((uint32_t)(ecap + 2) * 8u), lsz = up16((uint32_t)(ecap + 8) * 4u),
+  const uint32_t rec = fused ? 16u : 8u;  // bytes per weight record and per self-weight record
+  const uint32_t wsz = up16((uint32_t)(ecap + 2) * rec), lsz = up16((uint32_t)(ecap + 8) * 4u),
                  rsz = up16((uint32_t)(nmax + 8) * 4u);
-  const uint32_t ssz = op == NB_OP_GRAD ? 0u : up16((uint32_t)(nmax + 2) * 8u), hsz = 16u;
-  const uint32_t w2sz = fused ? wsz : 0u, s2sz = fused ? ssz : 0u;
-  const uint32_t meta = wsz + lsz + rsz + ssz + w2sz + s2sz + hsz;
+  const uint32_t ssz = op == NB_OP_GRAD ? 0u : up16((uint32_t)(nmax + 2) * rec), hsz = 16u;
+  const uint32_t meta = wsz + lsz + rsz + ssz + hsz;
   if (stage_target <= meta + 4096u) return NB_OK;
   const uint32_t area = ((stage_target - meta) / 128u) * 128u;
   if (area < 24u * row_bytes) return NB_OK;  // columns too tall to stage a useful tile
@@ -852,10 +865,11 @@ int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, 
   a.w64 = reinterpret_cast<const double2 *>(g ? m->d_wgrad64 : op == NB_OP_DIV ? m->d_wdiv64 : m->d_wcurl64);
   a.s32 = reinterpret_cast<const float2 *>(op == NB_OP_CURL ? m->d_scurl32 : m->d_sdiv32);
   a.s64 = reinterpret_cast<const double2 *>(op == NB_OP_CURL ? m->d_scurl64 : m->d_sdiv64);
-  a.w32b = fused ? reinterpret_cast<const float2 *>(m->d_wcurl32) : nullptr;
+  a.w4 = fused ? reinterpret_cast<const float4 *>(m->d_wdc32) : nullptr;
   a.w64b = fused ? reinterpret_cast<const double2 *>(m->d_wcurl64) : nullptr;
-  a.s32b = fused ? reinterpret_cast<const float2 *>(m->d_scurl32) : nullptr;
+  a.s4 = fused ? reinterpret_cast<const float4 *>(m->d_sdc32) : nullptr;
   a.s64b = fused ? reinterpret_cast<const double2 *>(m->d_scurl64) : nullptr;
+  a.rec16 = fused ? 1 : 0;
   a.out2 = fused ? static_cast<float *>(out2->data) : nullptr;
   a.in = static_cast<const char *>(in->data);
   a.row_bytes = row_bytes;
@@ -871,9 +885,7 @@ int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, 
   a.off_l = a.off_w + wsz;
   a.off_r = a.off_l + lsz;
   a.off_s = ssz ? a.off_r + rsz : 0u;
-  a.off_w2 = fused ? a.off_r + rsz + ssz : 0u;
-  a.off_s2 = fused ? a.off_w2 + w2sz : 0u;
-  a.off_h = a.off_r + rsz + ssz + w2sz + s2sz;
+  a.off_h = a.off_r + rsz + ssz;
   a.stage_bytes = (a.off_h + hsz + 127u) & ~127u;
   a.nstages = nstages;
   a.status = nullptr;
