@@ -311,6 +311,17 @@ int nb_nabla_apply(const nb_method *method, int op, const nb_field *in, const nb
 int nb_field_upload(const nb_field *dev, const void *host, void *stream);
 int nb_field_download(void *host, const nb_field *dev, void *stream);
 
+/* NodeColumns reductions (Sec. 4.5: global minimum, maximum and mean values
+ * of a field), per level and component: host_out[l * nvar + c] for l < nlev,
+ * c < nvar, in FP64.  NB_REDUCE_SUM is the plain sum over the nodes;
+ * NB_REDUCE_AREA_MEAN the dual-volume weighted mean sum(V_i x_i) / sum(V_i);
+ * NB_REDUCE_AREA_RMS sqrt(sum(V_i x_i^2) / sum(V_i)), the area-weighted
+ * norm used for error measures.  Deterministic (fixed reduction order); runs
+ * on `stream` and waits for it.  Errors: NB_EINVAL, NB_EDTYPE, NB_ESHAPE
+ * (field not on the method's mesh), NB_EOOM, NB_ECUDA. */
+enum { NB_REDUCE_MIN = 0, NB_REDUCE_MAX = 1, NB_REDUCE_SUM = 2, NB_REDUCE_AREA_MEAN = 3, NB_REDUCE_AREA_RMS = 4 };
+int nb_field_reduce(const nb_method *method, const nb_field *field, int kind, double *host_out, void *stream);
+
 /* End-to-end call on HOST buffers: copy host_in (laid out exactly like
  * dev_in, node_stride included) to dev_in, apply op, copy dev_out back to
  * host_out and wait for the stream.  Pinned host memory gives full link

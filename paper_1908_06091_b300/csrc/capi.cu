@@ -325,6 +325,7 @@ int nb_method_create(const nb_mesh *mesh, double radius_m, nb_method **out) {
   m->R = radius_m > 0 ? radius_m : 6.37122e6;
   m->alloc = nb::current_allocator();
   nb::build_geometry(mesh, m->R, m->vol, m->S, m->T, m->east, m->north);
+  for (double v : m->vol) m->area += v;
   const int st = nb::method_upload(m);
   if (st != NB_OK) {
     nb::release(m);

@@ -106,6 +106,7 @@ struct nb_method : nb::RefCounted {
   double R = 0;
   int device = 0;
   std::vector<double> vol;          // [V]
+  double area = 0;                  // sum of vol (4 pi R^2 to rounding)
   std::vector<double> S, T;         // [E][3]
   std::vector<double> east, north;  // [V][3]
   // device: connectivity

@@ -117,6 +117,7 @@ SIGNATURES = {
     "nb_nabla_divcurl": [_P, _FP, _FP, _FP, _P],
     "nb_nabla_gradlap": [_P, _FP, _FP, _FP, _P],
     "nb_field_upload": [_FP, _P, _P],
+    "nb_field_reduce": [_P, _FP, _I, _P, _P],
     "nb_field_download": [_P, _FP, _P],
     "nb_nabla_apply": [_P, _I, _FP, _FP, _FP, _P],
     "nb_nabla_laplacian_noalloc": [_P, _FP, _FP, _P],
@@ -434,6 +435,19 @@ def curl(method, uv, z, stream=None):
 
 def laplacian(method, f, lap, scratch=None, stream=None):
     return apply(method, OP_LAP, f, lap, scratch=scratch, stream=stream)
+
+
+REDUCE = {"min": 0, "max": 1, "sum": 2, "area_mean": 3, "area_rms": 4}
+
+
+def reduce(method, field: torch.Tensor, kind: str, nvar: int = 1, stream=None) -> np.ndarray:
+    """Per-level (and per-component) reduction over the nodes, in FP64:
+    min, max, sum, area_mean or area_rms (dual-volume weighted)."""
+    fv = field_view(field, nvar)
+    out = np.zeros((fv.nlev, nvar))
+    check(lib().nb_field_reduce(method.handle, ctypes.byref(fv), REDUCE[kind], out.ctypes.data,
+                                ctypes.c_void_p(_stream(stream))))
+    return out if nvar == 2 else out[:, 0]
 
 
 def upload(field: torch.Tensor, host: torch.Tensor, nvar: int, stream=None):
