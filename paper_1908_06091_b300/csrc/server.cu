@@ -64,30 +64,47 @@ __global__ void __launch_bounds__(256) synth_weights_kernel(uint64_t seed, int n
   w[t] = (float)mix_weight(seed, f, r >> 3, r & 7, nlev);
 }
 
-// in[node][k][c] = sum_b w[f][k][b] basis[node][b][c]  (c < nvar), in FP32
+// in[node][k][c] = sum_b w[k][b] basis[node][b][c]  (c < nvar), in FP32
 // arithmetic from an FP32 copy of the basis (these are request inputs, not
-// operator arithmetic); one thread per (node, level).
+// operator arithmetic).  A CTA takes kSynthNodes consecutive nodes: it
+// stages the block's mixing weights (transposed, [b][level], zero past nlev)
+// and its nodes' basis values in shared memory, then its threads walk the
+// (node, level) pairs level-fastest, so that stores are contiguous and
+// shared loads are conflict-free or broadcast.  Each level's sum runs
+// b = 0..7 in order.  Levels from nlev up to the padded stride get 0.
+constexpr int kSynthNodes = 64;
+constexpr int kSynthThreads = 256;
 template <class T>
-__global__ void __launch_bounds__(256) synth_fields_kernel(const float *__restrict__ basis, int nvar,
-                                                           int64_t V, int nlev, int64_t stride,
-                                                           const float *__restrict__ wts, T *out) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= V * nlev) return;
-  const int64_t i = idx / nlev;
-  const int k = (int)(idx - i * nlev);
-  const float4 w0 = __ldg(reinterpret_cast<const float4 *>(wts + 8 * k));
-  const float4 w1 = __ldg(reinterpret_cast<const float4 *>(wts + 8 * k) + 1);
-  const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
-  const float *bi = basis + i * 8 * nvar;
-  float acc0 = 0.f, acc1 = 0.f;
-#pragma unroll
-  for (int b = 0; b < 8; ++b) {
-    acc0 = __fmaf_rn(w[b], bi[b * nvar], acc0);
-    if (nvar == 2) acc1 = __fmaf_rn(w[b], bi[b * 2 + 1], acc1);
+__global__ void __launch_bounds__(kSynthThreads) synth_fields_kernel(const float *__restrict__ basis, int nvar,
+                                                                     int64_t V, int nlev, int64_t stride,
+                                                                     const float *__restrict__ wts, T *out) {
+  extern __shared__ float sm[];
+  const int lb = (int)(stride / nvar);           // padded levels of the column block
+  float *wT = sm;                                // [8][lb]
+  float *bs = sm + 8 * lb;                       // [kSynthNodes][8][nvar]
+  const int64_t n0 = (int64_t)blockIdx.x * kSynthNodes;
+  const int nn = (int)min((int64_t)kSynthNodes, V - n0);
+  for (int t = threadIdx.x; t < 8 * lb; t += blockDim.x) {
+    const int b = t / lb, k = t - b * lb;
+    wT[t] = k < nlev ? __ldg(wts + 8 * k + b) : 0.f;
   }
-  T *o = out + i * stride + (int64_t)k * nvar;
-  o[0] = (T)acc0;
-  if (nvar == 2) o[1] = (T)acc1;
+  for (int t = threadIdx.x; t < nn * 8 * nvar; t += blockDim.x) bs[t] = __ldg(basis + n0 * 8 * nvar + t);
+  __syncthreads();
+  const int total = nn * lb;
+  for (int j = threadIdx.x; j < total; j += blockDim.x) {
+    const int il = j / lb, k = j - il * lb;
+    const float *bi = bs + il * 8 * nvar;
+    float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const float w = wT[b * lb + k];
+      acc0 = __fmaf_rn(w, bi[b * nvar], acc0);
+      if (nvar == 2) acc1 = __fmaf_rn(w, bi[b * 2 + 1], acc1);
+    }
+    T *o = out + (n0 + il) * stride + (int64_t)k * nvar;
+    o[0] = (T)acc0;
+    if (nvar == 2) o[1] = (T)acc1;
+  }
 }
 
 struct SrvGrid {
@@ -195,13 +212,24 @@ static int launch_request(nb_server *s, SrvReq *q) {
     }
     // weights are [field][level][basis]: the block's are contiguous
     const float *wb = wts + (size_t)f0 * r.nlev * 8;
-    const unsigned blocks = (unsigned)((V * nl + 255) / 256);
+    const unsigned blocks = (unsigned)((V + kSynthNodes - 1) / kSynthNodes);
+    const size_t smem = sizeof(float) * (size_t)(8 * lb + kSynthNodes * 8 * in_var);
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [] {
+      // columns of up to 4096 levels: 8 x 4096 weights + the nodes' bases
+      const int bytes = (int)(sizeof(float) * (8 * 4096 + kSynthNodes * 16));
+      attr_err = cudaFuncSetAttribute(synth_fields_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+      if (attr_err == cudaSuccess)
+        attr_err = cudaFuncSetAttribute(synth_fields_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    });
+    NB_CUDA(attr_err);
     if (r.dtype == NB_F64)
-      synth_fields_kernel<double><<<blocks, 256, 0, st>>>(basis, in_var, V, nl, lb * in_var, wb,
-                                                          static_cast<double *>(din));
+      synth_fields_kernel<double><<<blocks, kSynthThreads, smem, st>>>(basis, in_var, V, nl, lb * in_var, wb,
+                                                                       static_cast<double *>(din));
     else
-      synth_fields_kernel<float><<<blocks, 256, 0, st>>>(basis, in_var, V, nl, lb * in_var, wb,
-                                                         static_cast<float *>(din));
+      synth_fields_kernel<float><<<blocks, kSynthThreads, smem, st>>>(basis, in_var, V, nl, lb * in_var, wb,
+                                                                      static_cast<float *>(din));
     count_launch(1);
     NB_CUDA(cudaGetLastError());
     nb_field fi{din, r.dtype, in_var, V, nl, 0, lb * in_var, in_var};
