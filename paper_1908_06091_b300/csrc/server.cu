@@ -68,10 +68,10 @@ __global__ void __launch_bounds__(256) synth_weights_kernel(uint64_t seed, int n
 // arithmetic from an FP32 copy of the basis (these are request inputs, not
 // operator arithmetic).  A CTA takes kSynthNodes consecutive nodes: it
 // stages the block's mixing weights (transposed, [b][level], zero past nlev)
-// and its nodes' basis values in shared memory, then its threads walk the
-// (node, level) pairs level-fastest, so that stores are contiguous and
-// shared loads are conflict-free or broadcast.  Each level's sum runs
-// b = 0..7 in order.  Levels from nlev up to the padded stride get 0.
+// and its nodes' basis values in shared memory.  A lane owns one level of a
+// 32-level chunk (its 8 weights in registers) and a warp walks the nodes, so
+// stores are contiguous and basis loads are broadcasts.  Each level's sum
+// runs b = 0..7 in order.  Levels from nlev up to the padded stride get 0.
 constexpr int kSynthNodes = 64;
 constexpr int kSynthThreads = 256;
 template <class T>
@@ -90,20 +90,26 @@ __global__ void __launch_bounds__(kSynthThreads) synth_fields_kernel(const float
   }
   for (int t = threadIdx.x; t < nn * 8 * nvar; t += blockDim.x) bs[t] = __ldg(basis + n0 * 8 * nvar + t);
   __syncthreads();
-  const int total = nn * lb;
-  for (int j = threadIdx.x; j < total; j += blockDim.x) {
-    const int il = j / lb, k = j - il * lb;
-    const float *bi = bs + il * 8 * nvar;
-    float acc0 = 0.f, acc1 = 0.f;
+  // lane = level within a 32-level chunk (weights held in registers), warp
+  // = a stride over the CTA's nodes
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int k = lane; k - lane < lb; k += 32) {
+    if (k >= lb) continue;
+    float w[8];
 #pragma unroll
-    for (int b = 0; b < 8; ++b) {
-      const float w = wT[b * lb + k];
-      acc0 = __fmaf_rn(w, bi[b * nvar], acc0);
-      if (nvar == 2) acc1 = __fmaf_rn(w, bi[b * 2 + 1], acc1);
+    for (int b = 0; b < 8; ++b) w[b] = wT[b * lb + k];
+    for (int il = warp; il < nn; il += nwarps) {
+      const float *bi = bs + il * 8 * nvar;
+      float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        acc0 = __fmaf_rn(w[b], bi[b * nvar], acc0);
+        if (nvar == 2) acc1 = __fmaf_rn(w[b], bi[b * 2 + 1], acc1);
+      }
+      T *o = out + (n0 + il) * stride + (int64_t)k * nvar;
+      o[0] = (T)acc0;
+      if (nvar == 2) o[1] = (T)acc1;
     }
-    T *o = out + (n0 + il) * stride + (int64_t)k * nvar;
-    o[0] = (T)acc0;
-    if (nvar == 2) o[1] = (T)acc1;
   }
 }
 
