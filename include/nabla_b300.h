@@ -200,6 +200,31 @@ int nb_mesh_tile_plan(const nb_mesh *mesh, int rcap, int nmax, int32_t *ntiles,
  * the first and last grid rows, which the FP32 kernels treat in FP64. */
 int nb_mesh_cap_begin(const nb_mesh *mesh, int64_t *cap_begin);
 
+/* ---------------------------------------------------------- partitions
+ * Host-side building blocks of a horizontally partitioned (multi-GPU) run;
+ * the operators themselves run on one device here. */
+
+/* EqualRegions partition (Sec. 4.2.4.2) of the grid's points into nparts
+ * regions: the zonal equal-area partition of the sphere (two polar caps and
+ * collars, regions per collar rounded with carry) gives the bands north to
+ * south; the points, taken north to south, are dealt to the bands in
+ * proportion to their region counts and, within a band ordered by
+ * longitude, into its regions, so every region holds V / nparts points
+ * (+-1).  part: caller-owned host int32[V] in grid order, part ids
+ * 0..nparts-1 numbered north to south (may be NULL to query the zones).
+ * zones (may be NULL): regions per band, north to south, *nzones of them.
+ * Errors: NB_EINVAL (nparts < 1 or > V). */
+int nb_partition_equal_regions(const nb_grid *grid, int nparts, int32_t *part, int32_t *zones,
+                               int32_t *nzones);
+
+/* Owned nodes and halo of partition p (Sec. 4.4): part is a host int32[V]
+ * in functionspace (mesh) order; owned = nodes with part == p, halo = the
+ * nodes owned elsewhere that neighbour an owned node (what a one-ring
+ * stencil needs), both ascending.  Pass owned/halo NULL to get the counts
+ * first.  Errors: NB_EINVAL. */
+int nb_partition_halo(const nb_mesh *mesh, const int32_t *part, int p, int64_t *nowned, int32_t *owned,
+                      int64_t *nhalo, int32_t *halo);
+
 /* -------------------------------------------------------------- method */
 
 /* fvm::Method (Sec. 4.7): build the median-dual geometry of the mesh on a

@@ -315,6 +315,40 @@ int nb_mesh_cap_begin(const nb_mesh *m, int64_t *cap_begin) {
   return NB_OK;
 }
 
+// ------------------------------------------------------------ partitions
+
+int nb_partition_equal_regions(const nb_grid *g, int nparts, int32_t *part, int32_t *zones,
+                               int32_t *nzones) {
+  NB_REQUIRE(g && (part || nzones), NB_EINVAL, "nb_partition_equal_regions: NULL argument");
+  NB_REQUIRE(nparts >= 1 && nparts <= g->V, NB_EINVAL, "nb_partition_equal_regions: nparts out of range");
+  NB_GUARD_BEGIN
+  const std::vector<int> z = nb::eq_zone_counts(nparts);
+  if (nzones) *nzones = (int32_t)z.size();
+  if (zones)
+    for (size_t k = 0; k < z.size(); ++k) zones[k] = z[k];
+  if (part) {
+    std::vector<int32_t> p;
+    nb::equal_regions(g, nparts, p);
+    std::memcpy(part, p.data(), sizeof(int32_t) * p.size());
+  }
+  return NB_OK;
+  NB_GUARD_END
+}
+
+int nb_partition_halo(const nb_mesh *m, const int32_t *part, int p, int64_t *nowned, int32_t *owned,
+                      int64_t *nhalo, int32_t *halo) {
+  NB_REQUIRE(m && part && nowned && nhalo, NB_EINVAL, "nb_partition_halo: NULL argument");
+  NB_GUARD_BEGIN
+  std::vector<int32_t> o, h;
+  nb::partition_halo(m, part, p, o, h);
+  *nowned = (int64_t)o.size();
+  *nhalo = (int64_t)h.size();
+  if (owned) std::memcpy(owned, o.data(), sizeof(int32_t) * o.size());
+  if (halo) std::memcpy(halo, h.data(), sizeof(int32_t) * h.size());
+  return NB_OK;
+  NB_GUARD_END
+}
+
 // ---------------------------------------------------------------- method
 
 int nb_method_create(const nb_mesh *mesh, double radius_m, nb_method **out) {

@@ -147,6 +147,12 @@ struct nb_fs : nb::RefCounted {
 
 namespace nb {
 
+// partitions (partition.cpp)
+std::vector<int> eq_zone_counts(int nparts);
+void equal_regions(const nb_grid *g, int nparts, std::vector<int32_t> &part);
+void partition_halo(const nb_mesh *m, const int32_t *part, int p, std::vector<int32_t> &owned,
+                    std::vector<int32_t> &halo);
+
 // host builders (host_mesh.cpp)
 nb_grid *build_grid(int N);                                   // O<N>
 nb_grid *build_grid_pl(int N, const std::vector<int32_t> &nx);  // any PL array of 2N rows

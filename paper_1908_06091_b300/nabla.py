@@ -90,6 +90,8 @@ SIGNATURES = {
     "nb_grid_gaussian_number": [_P, ctypes.POINTER(_I)],
     "nb_grid_lonlat": [_P, _P],
     "nb_mesh_create": [_P, _I, ctypes.POINTER(_P)],
+    "nb_partition_equal_regions": [_P, _I, _P, _P, ctypes.POINTER(ctypes.c_int32)],
+    "nb_partition_halo": [_P, _P, _I, _I64P, _P, _I64P, _P],
     "nb_mesh_release": [_P],
     "nb_mesh_sizes": [_P, _I64P, _I64P, _I64P],
     "nb_mesh_permutation": [_P, _P],
@@ -274,6 +276,32 @@ class Grid(_Handle):
         out = np.zeros((self.size, 2))
         check(lib().nb_grid_lonlat(self._h, out.ctypes.data))
         return out
+
+
+def equal_regions(grid: "Grid", nparts: int):
+    """EqualRegions partition (Sec. 4.2.4.2): part id per grid point (grid
+    order) and the regions per band, north to south."""
+    nz = ctypes.c_int32()
+    check(lib().nb_partition_equal_regions(grid.handle, int(nparts), None, None, ctypes.byref(nz)))
+    zones = np.zeros(nz.value, dtype=np.int32)
+    part = np.zeros(grid.size, dtype=np.int32)
+    check(lib().nb_partition_equal_regions(grid.handle, int(nparts), part.ctypes.data, zones.ctypes.data,
+                                           ctypes.byref(nz)))
+    return part, zones
+
+
+def partition_halo(mesh: "Mesh", part_mesh_order: np.ndarray, p: int):
+    """Owned nodes and one-ring halo of partition p (Sec. 4.4), both in
+    functionspace order, from a part id per node in functionspace order."""
+    part = np.ascontiguousarray(part_mesh_order, dtype=np.int32)
+    no, nh = ctypes.c_int64(), ctypes.c_int64()
+    check(lib().nb_partition_halo(mesh.handle, part.ctypes.data, int(p), ctypes.byref(no), None,
+                                  ctypes.byref(nh), None))
+    owned = np.zeros(no.value, dtype=np.int32)
+    halo = np.zeros(nh.value, dtype=np.int32)
+    check(lib().nb_partition_halo(mesh.handle, part.ctypes.data, int(p), ctypes.byref(no), owned.ctypes.data,
+                                  ctypes.byref(nh), halo.ctypes.data))
+    return owned, halo
 
 
 class Mesh(_Handle):
