@@ -22,6 +22,9 @@
  *     example a torch tensor).  Outputs are preallocated by the caller.
  *   - Operators are asynchronous on the caller's CUDA stream, passed as
  *     `void *stream` (a cudaStream_t; NULL = the legacy default stream).
+ *     The first call for a method and column layout builds tile plans
+ *     (host work and synchronous uploads); after it, the same calls can be
+ *     captured into a CUDA graph (library scratch is stream-ordered).
  *   - Node order of fields is the functionspace (reordered) order, see
  *     nb_mesh_permutation.  Layout is [node][level][var]: a vertical column
  *     is contiguous (Sec. 4.5, Fig. 31) and vector fields carry their local

@@ -102,3 +102,38 @@ def test_gradlap_outputs_equal_gradient_and_laplacian_calls(nlev, dtype):
     bad.data = fl.data
     assert nabla.lib().nb_nabla_gradlap(meth.handle, ctypes.byref(fi), ctypes.byref(bad), ctypes.byref(fl),
                                         None) != nabla.NB_OK
+
+
+def test_operator_calls_capture_into_a_cuda_graph_after_first_use():
+    """After one eager call (tile plans built), the staged operators, the
+    fused calls and the Laplacian with library scratch (stream-ordered) can
+    be captured in a CUDA graph; replays give the eager results bit for bit."""
+    g_, m, meth = product(48)
+    om = oracle_mesh(48)
+    f, uv = inputs(om, 37, 10, torch.float32)
+    perm = m.permutation()
+    fs = nabla.NodeColumns(meth, 37, torch.float32)
+    fd, uvd = to_device(fs, f, perm, 1), to_device(fs, uv, perm, 2)
+    outs = [fs.create_field(nvar=2), fs.create_field(), fs.create_field(), fs.create_field(), fs.create_field()]
+    s = torch.cuda.Stream()
+
+    def step():
+        nabla.gradlap(meth, fd, outs[0], outs[1], stream=s)
+        nabla.divcurl(meth, uvd, outs[2], outs[3], stream=s)
+        nabla.apply(meth, "lap", fd, outs[4], stream=s)
+
+    with torch.cuda.stream(s):
+        step()
+    s.synchronize()
+    eager = [o.clone() for o in outs]
+    for o in outs:
+        o.zero_()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        step()
+    for _ in range(2):
+        graph.replay()
+    torch.cuda.synchronize()
+    assert all(torch.equal(a, b) for a, b in zip(eager, outs))
+    assert torch.equal(outs[1], outs[4])  # gradlap's Laplacian == nb_nabla_laplacian
+    assert nabla.device_status() == 0
