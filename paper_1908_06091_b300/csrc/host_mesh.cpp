@@ -507,12 +507,12 @@ static void plan_tiles(const nb_mesh *m, Fits fits, int nmax, int ecap, std::vec
   std::vector<int32_t> mark(V, -1);
   node0.clear();
   int32_t stamp = 0;
-  auto cover = [&](int64_t a, int64_t b) {
+  auto cover = [&](int64_t a, int64_t b, int64_t cap) {
     int64_t n0 = a;
     while (n0 < b) {
       ++stamp;
       int64_t n1 = n0, H = 0;
-      while (n1 < b && n1 - n0 < nmax) {
+      while (n1 < b && n1 - n0 < cap) {
         const int64_t v = n1;
         if (n1 > n0 && m->row_ptr[v + 1] - m->row_ptr[n0] > ecap) break;
         int64_t add = 0;
@@ -535,9 +535,11 @@ static void plan_tiles(const nb_mesh *m, Fits fits, int nmax, int ecap, std::vec
       n0 = n1;
     }
   };
-  cover(0, m->cap_begin);
+  cover(0, m->cap_begin, nmax);
   ntiles_main = (int)node0.size();
-  cover(m->cap_begin, V);
+  // one pole-row node per tile: the pole rows take a slower path, which the
+  // staged kernels spread over many CTAs
+  cover(m->cap_begin, V, 1);
   node0.push_back((int32_t)V);
   const int nt = (int)node0.size() - 1;
   std::vector<std::vector<int32_t>> hal(nt);

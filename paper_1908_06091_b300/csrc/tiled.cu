@@ -8,10 +8,11 @@
 // halo columns four at a time with tile::gather4 tensor copies (the copy
 // engine's cost is per copy, so scattered halo columns are gathered in
 // fours).  Two stages alternate, so tile k+1 is copied while tile k is
-// computed.  Sixteen consumer warps take (node, 4-level group) items, read
-// the node's and its neighbours' columns from shared memory with 16-byte
-// loads and accumulate with packed FP32x2 compensated sums; pole tiles (the
-// first and last grid rows) run in FP64.  Every mbarrier wait is bounded:
+// computed.  Eleven or twelve consumer warps take (node, 4-level group)
+// items, read the node's and its neighbours' columns from shared memory
+// with 16-byte loads and accumulate with packed FP32x2 compensated sums;
+// pole tiles (one node of the first or last grid row each, walked first)
+// run in FP64.  Every mbarrier wait is bounded:
 // on timeout the kernel records NB_ETIMEOUT in a device status word, waits
 // (bounded) for its own copies and returns.
 #include <cuda.h>
@@ -605,18 +606,35 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-constexpr int kConsumerWarps = 16;
-constexpr int kStagedThreads = 32 * (kConsumerWarps + 1);
+// Consumer warps per operator.  Fewer warps than the SM could hold: timed on
+// B300 at O1280 x 137 levels, 11-12 consumer warps beat 16 by 1-7 % (more
+// warps only queue more shared-memory requests behind the same pipeline),
+// and a block of at most 4 warps per scheduler leaves up to 128 registers a
+// thread.
+template <int OP>
+struct StagedShape {
+  static constexpr int warps = OP == 0 ? 12 : 11;
+  static constexpr int threads = 32 * (warps + 1);
+};
 
-// Warp-specialised pipeline.  Warp kConsumerWarps is the producer: for
+// Tile of the i-th position in the walk: the pole tiles first (one node
+// each, FP64 and slow), so that they overlap the main tiles on other CTAs
+// instead of running alone at the end of the launch.
+__device__ __forceinline__ int tile_at(const TiledArgs &a, int i) {
+  const int npole = a.ntiles - a.ntiles_main;
+  return i < npole ? a.ntiles_main + i : i - npole;
+}
+
+// Warp-specialised pipeline.  The last warp (warp W) is the producer: for
 // iteration k it waits until stage k % NS has been released by every
-// consumer warp ("empty" barrier), then issues the copies of tile
-// blockIdx.x + k * gridDim.x into it ("full" barrier, transaction count).
-// Each consumer warp waits for "full", computes its 1/16 share of the
+// consumer warp ("empty" barrier), then issues the copies of the k-th tile
+// of this CTA's walk into it ("full" barrier, transaction count).  Each of
+// the W consumer warps waits for "full", computes its 1/W share of the
 // tile's items and releases the stage; no block-wide barrier is used.
 template <int OP, bool COMP>
-__global__ void __launch_bounds__(kStagedThreads, 1) staged_f32(const TiledArgs a,
-                                                                 const __grid_constant__ CUtensorMap map) {
+__global__ void __launch_bounds__(StagedShape<OP>::threads, 1)
+    staged_f32(const TiledArgs a, const __grid_constant__ CUtensorMap map) {
+  constexpr int W = StagedShape<OP>::warps;
   extern __shared__ __align__(128) unsigned char smem[];
   const int NS = a.nstages;
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)NS * a.stage_bytes);
@@ -626,17 +644,18 @@ __global__ void __launch_bounds__(kStagedThreads, 1) staged_f32(const TiledArgs 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NS; ++s) {
       mbar_init(full0 + 8 * s, 1);
-      mbar_init(empty0 + 8 * s, kConsumerWarps);
+      mbar_init(empty0 + 8 * s, W);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
   const int G = gridDim.x;
-  if (warp == kConsumerWarps) {
+  if (warp == W) {
     // producer
     int k = 0;
     bool failed = false;
-    for (int t = blockIdx.x; t < a.ntiles; t += G, ++k) {
+    for (int i = blockIdx.x; i < a.ntiles; i += G, ++k) {
+      const int t = tile_at(a, i);
       const int s = k % NS;
       if (k >= NS && !mbar_wait_bounded(empty0 + 8 * s, (uint32_t)(k / NS - 1) & 1u, a.timeout_ns)) {
         failed = true;
@@ -654,16 +673,17 @@ __global__ void __launch_bounds__(kStagedThreads, 1) staged_f32(const TiledArgs 
   }
   // consumers
   int k = 0;
-  for (int t = blockIdx.x; t < a.ntiles; t += G, ++k) {
+  for (int i = blockIdx.x; i < a.ntiles; i += G, ++k) {
+    const int t = tile_at(a, i);
     const int s = k % NS;
     if (!mbar_wait_bounded(full0 + 8 * s, (uint32_t)(k / NS) & 1u, a.timeout_ns)) {
       if (lane == 0) atomicCAS(a.status, 0, (int)NB_ETIMEOUT);
       break;
     }
     const uint32_t rows = stage0 + (uint32_t)s * a.stage_bytes;
-    if (OP == 0) grad_tile<COMP>(a, t, rows, warp, kConsumerWarps);
-    else if (OP == 1) divcurl_tile<COMP, false>(a, t, rows, warp, kConsumerWarps);
-    else divcurl_tile<COMP, true>(a, t, rows, warp, kConsumerWarps);
+    if (OP == 0) grad_tile<COMP>(a, t, rows, warp, W);
+    else if (OP == 1) divcurl_tile<COMP, false>(a, t, rows, warp, W);
+    else divcurl_tile<COMP, true>(a, t, rows, warp, W);
     __syncwarp();
     if (lane == 0) mbar_arrive(empty0 + 8 * s);
   }
@@ -757,7 +777,7 @@ static int launch_staged_t(const TiledArgs &a, const CUtensorMap &map, int grid,
                                     227 * 1024);
   });
   NB_CUDA(attr_err);
-  staged_f32<OP, COMP><<<grid, kStagedThreads, smem, st>>>(a, map);
+  staged_f32<OP, COMP><<<grid, StagedShape<OP>::threads, smem, st>>>(a, map);
   count_launch(1);
   NB_CUDA(cudaGetLastError());
   return NB_OK;
