@@ -30,6 +30,9 @@ OPS = ("grad", "div", "curl", "lap")
 # one step: grad(f) -> g; lap(f) = div(g), the divergence of the step's own
 # gradient (as nb_nabla_gradlap computes it); div and curl of uv in one pass
 PARTS = ("grad", "lap_from_grad", "divcurl")
+# Nominal dense FP64 rate of a B300 (TFLOP/s), the FP64 path's ALU roofline.
+# A cuBLAS DGEMM on this part measured 1.05.
+FP64_PEAK_TFLOPS = 1.25
 METRIC = "Gnode-levels/s per nabla op (O1280x137, fp32 vs fp64), % HBM roofline; p99 ms"
 
 
@@ -336,11 +339,24 @@ def bench_ours(a):
         stream.synchronize()
         ms64 = {op: statistics.median(ev64[k][i].elapsed_time(ev64[k][i + 1]) for k in range(a.fp64_steps))
                 for i, op in enumerate(PARTS)}
+        # The FP64 path is bound by B300's FP64 ALUs, not by HBM.  FP64
+        # flops per node-level of a six-neighbour node, as the direct kernels
+        # issue them: grad 6 x (1 sub + 2 fma) = 30; div (and curl) 6 x
+        # (2 sub + 2 fma) + 2 fma of the self term = 40; div+curl = 80.
+        flops = {"grad": 30, "lap_from_grad": 40, "divcurl": 80}
+        dom64 = max(ms64, key=ms64.get)
+        tf = flops[dom64] * nl / (ms64[dom64] * 1e-3) / 1e12
         fp64 = {"ms_per_step": round(sum(ms64.values()), 3),
                 "value": round(4 * nl / (sum(ms64.values()) * 1e-3) / 1e9, 2),
                 "per_op": {op: {"ms": round(ms64[op], 3),
-                                "gnl_s": round((2 if op == "divcurl" else 1) * nl / ms64[op] / 1e6, 1)}
-                           for op in PARTS}}
+                                "gnl_s": round((2 if op == "divcurl" else 1) * nl / ms64[op] / 1e6, 1),
+                                "tflops": round(flops[op] * nl / (ms64[op] * 1e-3) / 1e12, 3)}
+                           for op in PARTS},
+                "roofline": {"bound": "alu", "kernel": dom64, "achieved": round(tf, 3),
+                             "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                             "frac": round(tf / FP64_PEAK_TFLOPS, 3),
+                             "peak_kind": "nominal B300 FP64 (no measured FP64 peak on file)",
+                             "flops_per_node_level": flops[dom64]}}
         del f64, uv64, outs64, scr64
         torch.cuda.empty_cache()
 
