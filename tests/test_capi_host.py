@@ -133,6 +133,9 @@ def test_tile_plan_fits_stage_and_maps_every_neighbour(N, rcap, nmax):
         hi = np.clip(loc - (b - a), 0, max(len(h) - 1, 0))
         res = np.where(loc < b - a, a + loc, h[hi] if len(h) else a + loc)
         assert np.array_equal(res, nbr[p])
+    # the pole rows (nodes from cap_begin on) are one node per tile, so the
+    # staged kernels can spread their slower FP64 path over many CTAs
+    assert np.all(n[ntm:] == 1) and len(n) - ntm == m.V - m.cap_begin
     # neighbour lists agree with the edge list
     e = m.edges()
     deg = np.bincount(e.ravel(), minlength=m.V)
