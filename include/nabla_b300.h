@@ -194,8 +194,9 @@ int nb_mesh_csr(const nb_mesh *mesh, int64_t *row_ptr, int32_t *nbr);
  * nodes <= nmax.  Call with NULL arrays to get *ntiles and *nhalo; then pass
  * node0[ntiles+1], halo_ptr[ntiles+1], halo[nhalo] and lnbr[2E] (staged row
  * of every CSR neighbour: k < n is the tile's node k, n + h its halo node h).
- * *ntiles_main counts the tiles before the pole block; the pole block is one
- * node per tile. */
+ * *ntiles_main counts the tiles before the pole block; here the pole block is
+ * one node per tile (the staged kernels cut it into at most one tile per
+ * CTA of their persistent grid). */
 int nb_mesh_tile_plan(const nb_mesh *mesh, int rcap, int nmax, int32_t *ntiles,
                       int32_t *ntiles_main, int64_t *nhalo, int32_t *node0, int32_t *halo_ptr,
                       int32_t *halo, uint16_t *lnbr);

@@ -498,9 +498,10 @@ void build_geometry(const nb_mesh *m, double R, std::vector<double> &vol, std::v
 // greedily along the node order while fits(n, H) holds for the tile's n own
 // nodes and H halo nodes (neighbours outside it), with at most nmax nodes and
 // ecap CSR entries.  Main tiles cover [0, cap_begin), pole tiles
-// [cap_begin, V).  halo[t] lists the sorted halo nodes of tile t.
+// [cap_begin, V) with at most pole_cap nodes each.  halo[t] lists the sorted
+// halo nodes of tile t.
 template <class Fits>
-static void plan_tiles(const nb_mesh *m, Fits fits, int nmax, int ecap, std::vector<int32_t> &node0,
+static void plan_tiles(const nb_mesh *m, Fits fits, int nmax, int ecap, int pole_cap, std::vector<int32_t> &node0,
                        std::vector<int32_t> &halo_ptr, std::vector<int32_t> &halo, int &max_halo,
                        int &max_entries, int &ntiles_main) {
   const int64_t V = m->V;
@@ -537,9 +538,7 @@ static void plan_tiles(const nb_mesh *m, Fits fits, int nmax, int ecap, std::vec
   };
   cover(0, m->cap_begin, nmax);
   ntiles_main = (int)node0.size();
-  // one pole-row node per tile: the pole rows take a slower path, which the
-  // staged kernels spread over many CTAs
-  cover(m->cap_begin, V, 1);
+  cover(m->cap_begin, V, std::max(1, std::min(pole_cap, nmax)));
   node0.push_back((int32_t)V);
   const int nt = (int)node0.size() - 1;
   std::vector<std::vector<int32_t>> hal(nt);
@@ -594,7 +593,7 @@ void build_tile_plan_host(const nb_mesh *m, int rcap, int nmax, int ecap, std::v
                           std::vector<int32_t> &halo_ptr, std::vector<int32_t> &halo,
                           std::vector<uint16_t> &lnbr, int &max_halo, int &max_entries,
                           int &ntiles_main) {
-  plan_tiles(m, [&](int64_t n, int64_t H) { return n + H <= rcap; }, nmax, ecap, node0, halo_ptr, halo,
+  plan_tiles(m, [&](int64_t n, int64_t H) { return n + H <= rcap; }, nmax, ecap, 1, node0, halo_ptr, halo,
              max_halo, max_entries, ntiles_main);
   lnbr.assign(m->row_ptr[m->V], 0);
   staged_index(m, node0, halo_ptr, halo,
@@ -607,14 +606,14 @@ void build_tile_plan_host(const nb_mesh *m, int rcap, int nmax, int ecap, std::v
 // (group pitch = 4 copy_bytes rounded up to 128).  Tiles grow while the
 // layout fits `area` bytes; loff[p] is the byte offset of CSR neighbour p.
 void build_tile_plan_bytes(const nb_mesh *m, int64_t area, int64_t row_bytes, int64_t copy_bytes,
-                           int nmax, int ecap, std::vector<int32_t> &node0,
+                           int nmax, int ecap, int pole_cap, std::vector<int32_t> &node0,
                            std::vector<int32_t> &halo_ptr, std::vector<int32_t> &halo,
                            std::vector<uint32_t> &loff, int &max_halo, int &max_entries,
                            int &ntiles_main) {
   const int64_t gpitch = (4 * copy_bytes + 127) / 128 * 128;
   auto hbase = [&](int64_t n) { return (n * row_bytes + 127) / 128 * 128; };
   plan_tiles(m, [&](int64_t n, int64_t H) { return hbase(n) + (H + 3) / 4 * gpitch <= area; }, nmax,
-             ecap, node0, halo_ptr, halo, max_halo, max_entries, ntiles_main);
+             ecap, pole_cap, node0, halo_ptr, halo, max_halo, max_entries, ntiles_main);
   loff.assign(m->row_ptr[m->V], 0);
   staged_index(m, node0, halo_ptr, halo, [&](int64_t p, int, int64_t n, int64_t k) {
     loff[p] = (uint32_t)(k < n ? k * row_bytes : hbase(n) + ((k - n) >> 2) * gpitch + ((k - n) & 3) * copy_bytes);

@@ -89,6 +89,7 @@ struct TilePlan {
   int64_t copy_bytes = 0;// bytes copied per column (halo pitch)
   int nmax = 0;          // nodes per tile at most
   int ecap = 0;          // CSR entries per tile at most
+  int pole_cap = 1;      // nodes per pole-row tile at most
   int ntiles = 0;
   int ntiles_main = 0;               // tiles before the pole block
   int max_halo = 0;
@@ -133,7 +134,7 @@ struct nb_method : nb::RefCounted {
   int stage_kb = 0;     // staged kernels: KB per stage (0 = default)
   int compensated = 1;
   std::mutex plan_mu;
-  std::map<std::tuple<int64_t, int64_t, int64_t, int, int>, std::unique_ptr<TilePlan>> plans;
+  std::map<std::tuple<int64_t, int64_t, int64_t, int, int, int>, std::unique_ptr<TilePlan>> plans;
   ~nb_method() override;
 };
 
@@ -165,8 +166,9 @@ void build_tile_plan_host(const nb_mesh *m, int rcap, int nmax, int ecap, std::v
                           std::vector<uint16_t> &lnbr, int &max_halo, int &max_entries,
                           int &ntiles_main);
 
+// pole_cap: nodes per pole-row tile at most
 void build_tile_plan_bytes(const nb_mesh *m, int64_t area, int64_t row_bytes, int64_t copy_bytes,
-                           int nmax, int ecap, std::vector<int32_t> &node0,
+                           int nmax, int ecap, int pole_cap, std::vector<int32_t> &node0,
                            std::vector<int32_t> &halo_ptr, std::vector<int32_t> &halo,
                            std::vector<uint32_t> &loff, int &max_halo, int &max_entries,
                            int &ntiles_main);

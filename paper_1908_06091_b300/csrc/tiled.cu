@@ -11,8 +11,8 @@
 // computed.  Eleven or twelve consumer warps take (node, 4-level group)
 // items, read the node's and its neighbours' columns from shared memory
 // with 16-byte loads and accumulate with packed FP32x2 compensated sums;
-// pole tiles (one node of the first or last grid row each, walked first)
-// run in FP64.  Every mbarrier wait is bounded:
+// pole tiles (the first and last grid rows cut into at most one tile per
+// CTA, walked first) run in FP64.  Every mbarrier wait is bounded:
 // on timeout the kernel records NB_ETIMEOUT in a device status word, waits
 // (bounded) for its own copies and returns.
 #include <cuda.h>
@@ -627,9 +627,9 @@ struct StagedShape {
   static constexpr int ahead = OP == 2 ? 2 : 1;
 };
 
-// Tile of the i-th position in the walk: the pole tiles first (one node
-// each, FP64 and slow), so that they overlap the main tiles on other CTAs
-// instead of running alone at the end of the launch.
+// Tile of the i-th position in the walk: the pole tiles first (FP64 and
+// slow, at most one per CTA), so that they overlap the main tiles on other
+// CTAs instead of running alone at the end of the launch.
 __device__ __forceinline__ int tile_at(const TiledArgs &a, int i) {
   const int npole = a.ntiles - a.ntiles_main;
   return i < npole ? a.ntiles_main + i : i - npole;
@@ -712,7 +712,7 @@ static int plan_upload(TilePlan *tp, nb_method *m) {
   const nb_mesh *mesh = m->mesh;
   std::vector<int32_t> node0, hptr, halo;
   std::vector<uint32_t> loff;
-  build_tile_plan_bytes(mesh, tp->area, tp->row_bytes, tp->copy_bytes, tp->nmax, tp->ecap, node0, hptr,
+  build_tile_plan_bytes(mesh, tp->area, tp->row_bytes, tp->copy_bytes, tp->nmax, tp->ecap, tp->pole_cap, node0, hptr,
                         halo, loff, tp->max_halo, tp->max_entries, tp->ntiles_main);
   loff.resize(loff.size() + 8, 0);  // slack for 16-byte bounding copies
   if (halo.empty()) halo.push_back(0);
@@ -734,10 +734,16 @@ static int plan_upload(TilePlan *tp, nb_method *m) {
   return NB_OK;
 }
 
+// Pole-row tiles: the pole rows take the FP64 path, far slower per node on
+// B300 than the FP32 one.  They are cut into at most one tile per CTA of the
+// persistent grid (one node each for the 20-point rows of O<N>; ~70 for the
+// 5,120-point rows of F1280), and the walk takes them first.
 static TilePlan *get_plan(nb_method *m, int64_t area, int64_t row_bytes, int64_t copy_bytes, int nmax,
-                          int ecap, int *status) {
+                          int ecap, int nctas, int *status) {
+  const int64_t npole = m->mesh->V - m->mesh->cap_begin;
+  const int pole_cap = (int)std::max<int64_t>(1, (npole + nctas - 1) / std::max(1, nctas));
   std::lock_guard<std::mutex> lk(m->plan_mu);
-  auto key = std::make_tuple(area, row_bytes, copy_bytes, nmax, ecap);
+  auto key = std::make_tuple(area, row_bytes, copy_bytes, nmax, ecap, pole_cap);
   auto it = m->plans.find(key);
   if (it != m->plans.end()) return it->second.get();
   auto tp = std::make_unique<TilePlan>();
@@ -746,6 +752,7 @@ static TilePlan *get_plan(nb_method *m, int64_t area, int64_t row_bytes, int64_t
   tp->copy_bytes = copy_bytes;
   tp->nmax = nmax;
   tp->ecap = ecap;
+  tp->pole_cap = pole_cap;
   *status = plan_upload(tp.get(), m);
   if (*status != NB_OK) return nullptr;
   TilePlan *raw = tp.get();
@@ -866,14 +873,14 @@ int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, 
   if (stage_target <= meta + 4096u) return NB_OK;
   const uint32_t area = ((stage_target - meta) / 128u) * 128u;
   if (area < 24u * row_bytes) return NB_OK;  // columns too tall to stage a useful tile
-  int status = NB_OK;
-  TilePlan *tp = get_plan(m, area, row_bytes, copy_bytes, nmax, ecap, &status);
-  if (!tp) return status;
   if (g_sm_count == 0) {
     int dev = 0;
     NB_CUDA(cudaGetDevice(&dev));
     NB_CUDA(cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev));
   }
+  int status = NB_OK;
+  TilePlan *tp = get_plan(m, area, row_bytes, copy_bytes, nmax, ecap, g_sm_count, &status);
+  if (!tp) return status;
   // tensor map over the input columns: rows = nodes (pitch row_bytes), the
   // first copy_bytes of each row
   CUtensorMap map;
