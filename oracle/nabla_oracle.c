@@ -124,9 +124,13 @@ void or_grid_lonlat_pl(int rows, const int *nx, double *lat, double *lon) {
   long id = 0;
   for (int j = 0; j < 2 * N; ++j) {
     double phi = asin(mu[j]);
+    /* planted: equally spaced latitudes instead of the Gaussian rows */
+    if (g_mutation == 12) phi = 0.5 * OR_PI - OR_PI * (j + 0.5) / (2.0 * N);
     for (int i = 0; i < nx[j]; ++i) {
       lat[id] = phi;
       lon[id] = 2.0 * OR_PI * (double)i / (double)nx[j];
+      /* planted: rows start half a spacing east of longitude 0 */
+      if (g_mutation == 13) lon[id] = 2.0 * OR_PI * ((double)i + 0.5) / (double)nx[j];
       ++id;
     }
   }
@@ -376,6 +380,10 @@ static double spherical_excess(const double A[3], const double B[3], const doubl
 static void tri_centroid(const double *xyz, const int32_t *tri, long t, double c[3]) {
   for (int d = 0; d < 3; ++d)
     c[d] = xyz[3 * tri[3 * t] + d] + xyz[3 * tri[3 * t + 1] + d] + xyz[3 * tri[3 * t + 2] + d];
+  if (g_mutation == 10) { /* planted: planar centroid, not projected to the sphere */
+    for (int d = 0; d < 3; ++d) c[d] /= 3.0;
+    return;
+  }
   normalize3(c);
 }
 
@@ -489,7 +497,9 @@ void or_grad(long V, const int64_t *nptr, const int32_t *nlist, const int32_t *e
         if (g_mutation == 1) half_df = 0.5 * (f[j * L + k] + f[i * L + k]); /* planted */
         for (int d = 0; d < 3; ++d) g[d] += half_df * s * S[3 * e + d];
       }
-      for (int d = 0; d < 3; ++d) g[d] /= vol[i];
+      /* planted: normalised by the first neighbour's dual volume */
+      const double vi = g_mutation == 9 ? vol[other(edge, nlist[nptr[i]], i)] : vol[i];
+      for (int d = 0; d < 3; ++d) g[d] /= vi;
       out[(i * L + k) * 2 + 0] = dot3(g, east + 3 * i);
       out[(i * L + k) * 2 + 1] = dot3(g, north + 3 * i);
       if (g_mutation == 6) { /* planted: east and north swapped */
@@ -522,6 +532,8 @@ void or_div(long V, const int64_t *nptr, const int32_t *nlist, const int32_t *ed
         double s = side(edge, e, i), wj[3], wf[3];
         wind3(east, north, j, uv[(j * L + k) * 2], uv[(j * L + k) * 2 + 1], wj);
         for (int d = 0; d < 3; ++d) wf[d] = 0.5 * (wi[d] + wj[d]);
+        if (g_mutation == 7) /* planted: the node's own wind dropped from the edge average */
+          for (int d = 0; d < 3; ++d) wf[d] = 0.5 * wj[d];
         acc += s * dot3(wf, S + 3 * e);
       }
       out[i * L + k] = acc / vol[i];
@@ -546,6 +558,7 @@ void or_curl(long V, const int64_t *nptr, const int32_t *nlist, const int32_t *e
         double s = side(edge, e, i), wj[3], wf[3];
         wind3(east, north, j, uv[(j * L + k) * 2], uv[(j * L + k) * 2 + 1], wj);
         for (int d = 0; d < 3; ++d) wf[d] = 0.5 * (wi[d] + wj[d]);
+        if (g_mutation == 8) s = 1.0; /* planted: tangent not negated for the edge's second node */
         acc += s * dot3(wf, T + 3 * e);
       }
       out[i * L + k] = acc / vol[i];
@@ -560,6 +573,12 @@ void or_lap(long V, const int64_t *nptr, const int32_t *nlist, const int32_t *ed
             const double *S, const double *vol, const double *east, const double *north,
             long L, const double *f, double *tmp, double *out) {
   or_grad(V, nptr, nlist, edge, S, vol, east, north, L, f, tmp);
+  if (g_mutation == 14) /* planted: gradient components swapped before the divergence */
+    for (long q = 0; q < V * L; ++q) {
+      const double x = tmp[2 * q];
+      tmp[2 * q] = tmp[2 * q + 1];
+      tmp[2 * q + 1] = x;
+    }
   or_div(V, nptr, nlist, edge, S, vol, east, north, L, tmp, out);
 }
 

@@ -32,6 +32,29 @@ def pin_orientation(m):
     return bool((det > 0).all()), f"min det {det.min():.3e}"
 
 
+def _row_starts(m):
+    nx = np.asarray(oracle.row_nx(m.N))
+    return nx, np.concatenate([[0], np.cumsum(nx)])
+
+
+def pin_gaussian_rows(m, tol=1e-14):
+    """Row latitudes are the Gauss-Legendre nodes of degree 2N, north to
+    south (numpy's leggauss)."""
+    nx, off = _row_starts(m)
+    x, _ = np.polynomial.legendre.leggauss(2 * m.N)
+    err = np.abs(np.sin(m.lat[off[:-1]]) - x[::-1]).max()
+    same = all(np.all(m.lat[off[j]:off[j + 1]] == m.lat[off[j]]) for j in range(len(nx)))
+    return bool(err <= tol and same), f"max |sin(lat) - x| {err:.3e}"
+
+
+def pin_longitudes(m, tol=1e-15):
+    """Each row starts at longitude 0 and its points are equispaced."""
+    nx, off = _row_starts(m)
+    err = max(np.abs(m.lon[off[j]:off[j + 1]] - 2 * np.pi * np.arange(n) / n).max()
+              for j, n in enumerate(nx))
+    return bool(err <= tol), f"max lon error {err:.3e}"
+
+
 def pin_total_volume(m, tol=1e-13):
     """Dual cells tile the sphere: sum V_i = 4 pi R^2."""
     rel = abs(m.vol.sum() / (4 * np.pi * m.R ** 2) - 1.0)

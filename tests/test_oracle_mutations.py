@@ -13,11 +13,20 @@ MUTATIONS = {
     3: "face tangent sign reversed",
     5: "one of the two sub-triangles dropped from the dual volume",
     6: "east and north gradient components swapped",
+    7: "divergence: the node's own wind dropped from the edge average",
+    8: "curl: tangent not negated for the edge's second node",
+    9: "gradient normalised by a neighbour's dual volume",
+    10: "triangle centroid not projected to the sphere",
+    12: "equally spaced latitudes instead of the Gaussian rows",
+    13: "rows start half a spacing east of longitude 0",
+    14: "Laplacian: gradient components swapped before the divergence",
 }
 
 
 def _all_pins(m):
     return {
+        "gauss_rows": _pins.pin_gaussian_rows(m),
+        "longitudes": _pins.pin_longitudes(m),
         "grad_const": _pins.pin_grad_constant(m),
         "volume": _pins.pin_total_volume(m),
         "closed": _pins.pin_closed_tangent(m),
