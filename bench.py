@@ -615,9 +615,31 @@ def cpu_baseline(a, samples=1):
         ts.append(time.perf_counter() - t)
     dt = statistics.median(ts)
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": round(4 * m.V * L / dt / 1e9, 5), "unit": "Gnode-levels/s", "cores": cores,
-            "kind": "oracle", "seconds": round(dt, 2),
-            "sample": f"O{a.grid}, first {L} of {a.nlev} levels, grad+div+curl+lap, FP64 C + OpenMP"}
+    out = {"value": round(4 * m.V * L / dt / 1e9, 5), "unit": "Gnode-levels/s", "cores": cores,
+           "kind": "oracle", "seconds": round(dt, 2),
+           "sample": f"O{a.grid}, first {L} of {a.nlev} levels, grad+div+curl+lap, FP64 C + OpenMP"}
+    # the same oracle on one core, on a smaller sample (OpenMP runtime of
+    # this process set to one thread, then restored)
+    L1 = max(1, L // 16)
+    try:
+        import ctypes
+        gomp = ctypes.CDLL("libgomp.so.1")
+        prev = gomp.omp_get_max_threads()
+        gomp.omp_set_num_threads(1)
+        try:
+            t = time.perf_counter()
+            oracle.grad(m, f[:, :L1])
+            oracle.div(m, uv[:, :L1])
+            oracle.curl(m, uv[:, :L1])
+            oracle.lap(m, f[:, :L1])
+            dt1 = time.perf_counter() - t
+        finally:
+            gomp.omp_set_num_threads(prev)
+        out["single_core"] = {"value": round(4 * m.V * L1 / dt1 / 1e9, 5), "seconds": round(dt1, 2),
+                              "sample": f"O{a.grid}, first {L1} levels, one thread"}
+    except OSError:
+        out["single_core"] = None
+    return out
 
 
 def bench_reference(a):
