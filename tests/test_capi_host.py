@@ -189,3 +189,26 @@ def test_grid_names_and_pl_checks():
     for bad in ([20, 24, 20], [20, 2, 2, 20], [20]):
         with pytest.raises(nabla.NablaError):
             nabla.Grid.reduced(bad)
+
+
+def test_last_error_is_per_thread():
+    """nb_last_error() is thread-local: an error raised on one thread does not
+    overwrite the message another thread reads."""
+    import ctypes
+    import threading
+    L = nabla.lib()
+    barrier = threading.Barrier(2)
+    seen = {}
+
+    def worker(name, bad_call):
+        rc = bad_call()
+        barrier.wait()          # both threads have failed before either reads
+        seen[name] = (rc, L.nb_last_error().decode())
+
+    g = ctypes.c_void_p()
+    t1 = threading.Thread(target=worker, args=("grid", lambda: L.nb_grid_create_octahedral(0, ctypes.byref(g))))
+    t2 = threading.Thread(target=worker, args=("mesh", lambda: L.nb_mesh_create(None, 1, ctypes.byref(g))))
+    t1.start(); t2.start(); t1.join(); t2.join()
+    assert seen["grid"][0] == nabla.NB_EINVAL and seen["mesh"][0] == nabla.NB_EINVAL
+    assert seen["grid"][1] and seen["mesh"][1]
+    assert seen["grid"][1] != seen["mesh"][1], seen
