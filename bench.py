@@ -47,8 +47,8 @@ def parse():
     p.add_argument("--lmax", type=int, default=40)
     p.add_argument("--e2e-steps", type=int, default=4)
     p.add_argument("--fp64-steps", type=int, default=3)
-    p.add_argument("--cpu-levels", type=int, default=64,
-                   help="levels of the oracle's bounded CPU sample")
+    p.add_argument("--cpu-levels", type=int, default=32,
+                   help="levels of the oracle's bounded CPU sample (also the levels of the error figures)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--single-op-reps", type=int, default=3,
                    help="timed single-operator div, curl and Laplacian calls after the timed region (0 = none)")
@@ -289,6 +289,11 @@ def bench_ours(a):
                       "gnl_s": round((2 if op == "divcurl" else 1) * nl / per_op_ms[op] / 1e6, 1),
                       "algo_GBs": round(b / per_op_ms[op] / 1e6, 1),
                       "frac_hbm": round(b / per_op_ms[op] / 1e6 / hbm, 3)}
+    # a level sample of this run's own inputs and outputs (grid order, host),
+    # for the oracle comparison of the CPU-baseline leg
+    sample = None
+    if rank == 0 and not a.no_cpu_baseline:
+        sample = take_sample(mesh, f, uv, outs, a.cpu_levels)
     # the single-operator passes, outside the timed region (for reference)
     single = {}
     with torch.cuda.stream(stream):
@@ -357,6 +362,8 @@ def bench_ours(a):
                              "frac": round(tf / FP64_PEAK_TFLOPS, 3),
                              "peak_kind": "nominal B300 FP64 (no measured FP64 peak on file)",
                              "flops_per_node_level": flops[dom64]}}
+        if sample is not None:
+            sample["out64"] = sample_outputs(mesh, outs64, sample["levels"])
         del f64, uv64, outs64, scr64
         torch.cuda.empty_cache()
 
@@ -449,8 +456,8 @@ def bench_ours(a):
         line["batched"] = bench_batched(a, nabla, synth, stream)
     if a.serve_seconds > 0:
         line["served"] = bench_served(a, nabla, synth)
-    if rank == 0 and not a.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(a, samples=1)
+    if sample is not None:
+        line["cpu_baseline"], line["errors"] = cpu_baseline(a, sample)
     if world > 1:
         dist.destroy_process_group()
     return line if rank == 0 else None
@@ -595,51 +602,115 @@ def bench_served(a, nabla, synth):
 
 # ---------------------------------------------------------- oracle timing
 
-def cpu_baseline(a, samples=1):
-    """The FP64 oracle (as it stands) on the host cores: all four operators
-    on the first `cpu_levels` levels of the same grid."""
+def take_sample(mesh, f, uv, outs, nlev_sample):
+    """Levels of this run's FP32 inputs and step outputs, copied to the host
+    in grid order: nlev_sample levels spread over the column (first and last
+    included).  Inputs are kept as FP64 (their exact FP32 values)."""
+    import numpy as np
+    L = f.shape[1]
+    levels = sorted(set(int(round(x)) for x in np.linspace(0, L - 1, max(1, min(nlev_sample, L)))))
+    perm = mesh.permutation()
+
+    def host(t):
+        x = t[:, levels].detach().cpu().numpy()
+        out = np.empty(x.shape, dtype=np.float64)
+        out[perm] = x
+        return out
+    return {"levels": levels, "f": host(f), "uv": host(uv), "out32": sample_outputs(mesh, outs, levels)}
+
+
+def sample_outputs(mesh, outs, levels):
+    """Step outputs (grad, div, curl, lap) at `levels`, grid order, host."""
+    import numpy as np
+    perm = mesh.permutation()
+    res = {}
+    for name, t in zip(("grad", "div", "curl", "lap"), outs):
+        x = t[:, levels].detach().cpu().numpy()
+        out = np.empty(x.shape, dtype=x.dtype)
+        out[perm] = x
+        res[name] = out
+    return res
+
+
+def _omp_threads():
+    """OpenMP threads the oracle runs on: the libgomp runtime's setting, else
+    the CPUs this process may run on."""
+    try:
+        import ctypes
+        return int(ctypes.CDLL("libgomp.so.1").omp_get_max_threads())
+    except OSError:
+        return len(os.sched_getaffinity(0))
+
+
+def cpu_baseline(a, sample):
+    """The FP64 oracle (as it stands) on the host cores, on a level sample of
+    this run's own inputs: all four operators.  Its outputs are also the
+    reference of the per-op error figures of the FP32 and FP64 GPU paths on
+    the same levels (relative L2, per-node maximum, pole rows alone)."""
     import numpy as np
     import oracle
-    from paper_1908_06091_b300 import synth
     m = oracle.build_mesh(a.grid, oracle.EARTH_RADIUS_M)
-    L = a.cpu_levels
-    f = synth.scalar_field(m.lat, m.lon, L, a.lmax).numpy()
-    uv = synth.wind_field(m.lat, m.lon, L, a.lmax, m.R).numpy()
-    ts = []
-    for _ in range(samples):
-        t = time.perf_counter()
-        oracle.grad(m, f)
-        oracle.div(m, uv)
-        oracle.curl(m, uv)
-        oracle.lap(m, f)
-        ts.append(time.perf_counter() - t)
-    dt = statistics.median(ts)
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    f, uv = sample["f"], sample["uv"]
+    L = f.shape[1]
+    t = time.perf_counter()
+    ref = {"grad": oracle.grad(m, f), "div": oracle.div(m, uv), "curl": oracle.curl(m, uv),
+           "lap": oracle.lap(m, f)}
+    dt = time.perf_counter() - t
+    cores = _omp_threads()
     out = {"value": round(4 * m.V * L / dt / 1e9, 5), "unit": "Gnode-levels/s", "cores": cores,
            "kind": "oracle", "seconds": round(dt, 2),
-           "sample": f"O{a.grid}, first {L} of {a.nlev} levels, grad+div+curl+lap, FP64 C + OpenMP"}
-    # the same oracle on one core, on a smaller sample (OpenMP runtime of
-    # this process set to one thread, then restored)
-    L1 = max(1, L // 16)
+           "sample": f"O{a.grid}, {L} of {a.nlev} levels (spread over the column) of the run's own "
+                     "inputs, grad+div+curl+lap, FP64 C + OpenMP"}
+    # the same oracle on one thread (OpenMP runtime of this process set to
+    # one thread, then restored), median of three runs on two levels
+    L1 = min(2, L)
     try:
         import ctypes
         gomp = ctypes.CDLL("libgomp.so.1")
         prev = gomp.omp_get_max_threads()
         gomp.omp_set_num_threads(1)
+        ts = []
         try:
-            t = time.perf_counter()
-            oracle.grad(m, f[:, :L1])
-            oracle.div(m, uv[:, :L1])
-            oracle.curl(m, uv[:, :L1])
-            oracle.lap(m, f[:, :L1])
-            dt1 = time.perf_counter() - t
+            f1, uv1 = np.ascontiguousarray(f[:, :L1]), np.ascontiguousarray(uv[:, :L1])
+            for _ in range(3):
+                t = time.perf_counter()
+                oracle.grad(m, f1)
+                oracle.div(m, uv1)
+                oracle.curl(m, uv1)
+                oracle.lap(m, f1)
+                ts.append(time.perf_counter() - t)
         finally:
             gomp.omp_set_num_threads(prev)
+        dt1 = statistics.median(ts)
         out["single_core"] = {"value": round(4 * m.V * L1 / dt1 / 1e9, 5), "seconds": round(dt1, 2),
-                              "sample": f"O{a.grid}, first {L1} levels, one thread"}
+                              "sample": f"O{a.grid}, {L1} levels, one thread, median of 3"}
     except OSError:
         out["single_core"] = None
-    return out
+    # error figures of the GPU paths against these oracle outputs
+    nx0 = int(np.argmax(m.lat != m.lat[0]))
+    nx1 = int(np.argmax(m.lat[::-1] != m.lat[-1]))
+    pole = np.zeros(m.V, dtype=bool)
+    pole[:nx0] = True
+    pole[m.V - nx1:] = True
+
+    def stats(x, r):
+        if x.ndim == 3:
+            parts = [stats(x[..., c], r[..., c]) for c in range(x.shape[-1])]
+            return {k: max(p[k] for p in parts) for k in parts[0]}
+        d = x.astype(np.float64) - r
+        return {"rel_l2": float(np.linalg.norm(d.ravel()) / np.linalg.norm(r.ravel())),
+                "max_rel": float(np.abs(d).max() / np.abs(r).max()),
+                "max_abs": float(np.abs(d).max()),
+                "pole_rel_l2": float(np.linalg.norm(d[pole].ravel()) / np.linalg.norm(r[pole].ravel()))}
+    errors = {"reference": "FP64 oracle on the same inputs", "levels": sample["levels"],
+              "definitions": {"rel_l2": "||x-ref||/||ref|| over all nodes of the sampled levels",
+                              "max_rel": "max|x-ref| / max|ref|", "max_abs": "max|x-ref|",
+                              "pole_rel_l2": "relative L2 over the first and last grid rows"}}
+    for key, name in (("out32", "f32"), ("out64", "f64")):
+        if key in sample:
+            errors[name] = {op: {k: float(f"{v:.3e}") for k, v in stats(sample[key][op], ref[op]).items()}
+                            for op in ("grad", "div", "curl", "lap")}
+    return out, errors
 
 
 def bench_reference(a):
@@ -667,7 +738,7 @@ def bench_reference(a):
         step()
     dt = time.perf_counter() - t
     value = 4 * m.V * L * a.steps / dt / 1e9
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = _omp_threads()
     sample = f"O{a.grid}, {L} of {a.nlev} levels per step, grad+div+curl+lap, FP64 C + OpenMP"
     return {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "Gnode-levels/s",
             "n_gpus": world, "steps": a.steps, "warmup": a.warmup,

@@ -313,13 +313,18 @@ int nb_nabla_laplacian(const nb_method *method, const nb_field *f, const nb_fiel
  * a component embedded in a larger model with a device-memory budget fixed at
  * start-up, or a latency-critical loop in which cudaMalloc/cudaFree (which can
  * synchronise the whole device) are not allowed.  The intermediate gradient
- * lives in a fixed array of NB_NOALLOC_SCRATCH_BYTES inside the library, held
- * on every GPU that loads the library until the process exits; it fits
- * [V][Lq][2] values of f's dtype with Lq = nlev rounded up to a multiple of 4
- * (FP32) or 2 (FP64), and larger problems get NB_ESHAPE (use
- * nb_nabla_laplacian with a scratch field).  The first call on a device looks
- * up the array's device address, so make that first call before any stream
- * capture.  All calls share the one array and it keeps the last call's
+ * lives in a fixed array of NB_NOALLOC_SCRATCH_BYTES inside the library; it
+ * fits [V][Lq][2] values of f's dtype with Lq = nlev rounded up to a multiple
+ * of 4 (FP32) or 2 (FP64), and larger problems get NB_ESHAPE (use
+ * nb_nabla_laplacian with a scratch field).  The CUDA runtime loads the
+ * library's device code lazily (its default): the array's device memory is
+ * taken on a device when this call first runs there, which also looks up
+ * the array's device address and may synchronise the device.  So make the
+ * first call on each device at start-up, inside the caller's memory budget
+ * and before any stream capture; from then on the array stays on that
+ * device until the process exits and no call allocates.  (A process started
+ * with CUDA_MODULE_LOADING=EAGER takes the memory when the library loads.)
+ * All calls share the one array and it keeps the last call's
  * contents (nothing in it needs to start at zero); calls whose work overlaps
  * on the GPU, on any stream, race on it, so serialise them.  Same argument
  * rules and errors as nb_nabla_laplacian. */
@@ -486,6 +491,18 @@ int nb_server_output(nb_server *server, uint64_t ticket, void *host_out, int64_t
  * [V][Lp][nvar_in] of its dtype, to host memory of exactly `bytes`. */
 int nb_server_input(nb_server *server, uint64_t ticket, void *host_in, int64_t bytes);
 
+/* Fault injection for tests of the serving loop.  Every request submitted
+ * afterwards whose seed is `seed` has its alloc_index-th device allocation
+ * refused, as a pool with no memory left would refuse it (index 0 is the
+ * request's mixing weights, then per column block of its fields the input,
+ * the output and, for a Laplacian, the scratch field).  Such a request ends
+ * with status NB_EOOM once the work it had already enqueued has run, and
+ * frees what it holds and its share of the budget; requests in flight beside
+ * it are not touched.  alloc_index = -1 removes the injection for `seed`.
+ * Host-side only: no device fault is involved.  (No counterpart in the
+ * paper.)  Errors: NB_EINVAL. */
+int nb_server_inject_failure(nb_server *server, uint64_t seed, int32_t alloc_index);
+
 /* Budget in use, its peak, queued and in-flight request counts. */
 int nb_server_stats(nb_server *server, int64_t *used, int64_t *peak_used, int32_t *pending,
                     int32_t *inflight);
@@ -520,6 +537,21 @@ int nb_method_set_staging(nb_method *method, int nstages, int stage_kb);
 /* Accumulation mode of the FP32 path: 1 = compensated (Kahan, default),
  * 0 = plain FP32 FMA chain (for accuracy/throughput comparison). */
 int nb_method_set_compensated(nb_method *method, int on);
+
+/* Limit of every wait inside the staged kernels' copy pipeline (a warp
+ * waiting for a stage's copies to land, or for the consumer warps to release
+ * a stage), in nanoseconds of the GPU's global timer.
+ *   limit_ns = -1: the default, 2 s.  limit_ns = 0: every wait tests its
+ *   barrier once, without suspending, and gives up at once if the phase is
+ *   not complete.  Otherwise 1 ns .. 60 s.
+ * A wait that runs out makes the kernel record NB_ETIMEOUT in the device
+ * status word (nb_device_status) and return early, its outputs incomplete;
+ * a CTA first waits (up to a fixed 4 s, independent of this limit) for the
+ * copies it has already issued, so that none is in flight when it exits.
+ * The GPU context stays usable.  Used to test failure detection: a short
+ * limit makes the waits run out without any fault.  Returns NB_EINVAL for
+ * other values.  (No counterpart in the paper.) */
+int nb_method_set_wait_limit(nb_method *method, int64_t limit_ns);
 
 /* Number of this library's kernel launches since load (all devices). */
 int nb_launch_count(int64_t *count);

@@ -416,6 +416,14 @@ int nb_method_set_compensated(nb_method *m, int on) {
   return NB_OK;
 }
 
+int nb_method_set_wait_limit(nb_method *m, int64_t limit_ns) {
+  NB_REQUIRE(m, NB_EINVAL, "nb_method_set_wait_limit: NULL method");
+  NB_REQUIRE(limit_ns >= -1 && limit_ns <= 60000000000ll, NB_EINVAL,
+             "nb_method_set_wait_limit: limit_ns must be -1 (default) or in [0, 60 s]");
+  m->wait_limit_ns = limit_ns;
+  return NB_OK;
+}
+
 // --------------------------------------------------------- functionspace
 
 int nb_fs_nodecolumns(const nb_method *m, int nlev, nb_dtype dtype, nb_fs **out) {

@@ -133,6 +133,7 @@ struct nb_method : nb::RefCounted {
   int nstages = 0;      // staged kernels: pipeline stages (0 = default)
   int stage_kb = 0;     // staged kernels: KB per stage (0 = default)
   int compensated = 1;
+  int64_t wait_limit_ns = -1;  // staged kernels' pipeline wait limit (-1 = default)
   std::mutex plan_mu;
   std::map<std::tuple<int64_t, int64_t, int64_t, int, int, int>, std::unique_ptr<TilePlan>> plans;
   ~nb_method() override;

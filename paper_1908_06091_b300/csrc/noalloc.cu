@@ -5,9 +5,11 @@
 // budget set at start-up, or a latency-critical loop in which cudaMalloc /
 // cudaFree (which may synchronise the whole device) are not allowed.  The
 // Laplacian needs an intermediate gradient field, so for these callers it
-// is kept in a fixed-size array that is part of the library image: every
-// GPU that loads the library holds NB_NOALLOC_SCRATCH_BYTES of device memory
-// for it until the process exits.
+// is kept in a fixed-size array that is part of the library image.  Under
+// the CUDA runtime's default lazy module loading, a device takes the array's
+// NB_NOALLOC_SCRATCH_BYTES when the first call runs on it (the address
+// lookup below loads the module); it keeps them until the process exits.
+// Callers make that first call at start-up, inside their memory budget.
 #include <cuda_runtime.h>
 
 #include <mutex>

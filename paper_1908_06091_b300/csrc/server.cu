@@ -131,7 +131,21 @@ struct SrvReq {
   void *wts = nullptr;         // mixing weights of the request's fields
   std::vector<char> host_out;  // kept outputs (tests)
   std::vector<char> host_in;   // kept inputs (keep_output == 2)
+  int fail_at = -1;            // injected failure: index of the refused allocation
+  int nalloc = 0;              // device allocations made so far
 };
+
+// One device allocation of a request from the stream-ordered pool.  The
+// allocation the fault injector marks (nb_server_inject_failure) is refused
+// as a full pool would refuse it.
+static int req_alloc(SrvReq *q, void **p, size_t bytes, cudaStream_t st) {
+  if (q->nalloc++ == q->fail_at) {
+    set_error("server request: device allocation refused (injected failure)");
+    return NB_EOOM;
+  }
+  NB_CUDA(cudaMallocAsync(p, bytes, st));
+  return NB_OK;
+}
 
 }  // namespace nb
 
@@ -146,6 +160,7 @@ struct nb_server : nb::RefCounted {
   std::deque<nb::SrvReq *> pending;  // arrived, not admitted
   std::vector<nb::SrvReq *> inflight;
   std::map<uint64_t, nb::SrvReq *> all;
+  std::map<uint64_t, int> inject;  // request seed -> index of the allocation to refuse
   std::atomic<uint64_t> next_ticket{1};
   int64_t used = 0, peak_used = 0;
   int rr = 0;
@@ -196,7 +211,7 @@ static int launch_request(nb_server *s, SrvReq *q) {
   const int out_var = r.op == NB_OP_GRAD ? 2 : 1;
   float *wts = nullptr;
   const int nw = r.nfields * r.nlev * 8;
-  NB_CUDA(cudaMallocAsync((void **)&wts, (size_t)nw * sizeof(float), st));
+  if (const int rc = req_alloc(q, (void **)&wts, (size_t)nw * sizeof(float), st)) return rc;
   q->wts = wts;
   synth_weights_kernel<<<(nw + 255) / 256, 256, 0, st>>>(r.seed, r.nfields, r.nlev, wts);
   count_launch(1);
@@ -208,12 +223,12 @@ static int launch_request(nb_server *s, SrvReq *q) {
     const int nl = nf * r.nlev;  // levels of the block in use
     const int64_t lb = block_stride(r, nf);
     void *din = nullptr, *dout = nullptr, *dscr = nullptr;
-    NB_CUDA(cudaMallocAsync(&din, (size_t)(V * lb * in_var * elem), st));
+    if (const int rc = req_alloc(q, &din, (size_t)(V * lb * in_var * elem), st)) return rc;
     q->bufs.push_back(din);
-    NB_CUDA(cudaMallocAsync(&dout, (size_t)(V * lb * out_var * elem), st));
+    if (const int rc = req_alloc(q, &dout, (size_t)(V * lb * out_var * elem), st)) return rc;
     q->bufs.push_back(dout);
     if (r.op == NB_OP_LAP) {
-      NB_CUDA(cudaMallocAsync(&dscr, (size_t)(V * lb * 2 * elem), st));
+      if (const int rc = req_alloc(q, &dscr, (size_t)(V * lb * 2 * elem), st)) return rc;
       q->bufs.push_back(dscr);
     }
     // weights are [field][level][basis]: the block's are contiguous
@@ -469,6 +484,10 @@ int nb_server_submit(nb_server *s, const nb_request *r, uint64_t *ticket) {
   }
   auto *q = new nb::SrvReq();
   q->r = *r;
+  {
+    auto fi = s->inject.find(r->seed);
+    if (fi != s->inject.end()) q->fail_at = fi->second;
+  }
   q->bytes = nb::req_bytes(s, *r, g->second.method->mesh->V);
   if (q->bytes > s->budget) {
     delete q;
@@ -483,6 +502,17 @@ int nb_server_submit(nb_server *s, const nb_request *r, uint64_t *ticket) {
   *ticket = q->ticket;
   lk.unlock();
   s->cv.notify_all();
+  return NB_OK;
+}
+
+int nb_server_inject_failure(nb_server *s, uint64_t seed, int32_t alloc_index) {
+  if (!s || alloc_index < -1) {
+    nb::set_error("nb_server_inject_failure: NULL server or alloc_index < -1");
+    return NB_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (alloc_index < 0) s->inject.erase(seed);
+  else s->inject[seed] = alloc_index;
   return NB_OK;
 }
 

@@ -83,8 +83,23 @@ __device__ __forceinline__ uint64_t globaltimer() {
   return t;
 }
 
+// Non-blocking test of the phase (never suspends the thread).
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
 // Wait for `parity` on the barrier for at most ~`limit_ns`; false on timeout.
+// A limit of 0 tests the phase once without suspending.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+  if (limit_ns == 0) return mbar_test_wait(bar, parity);
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   for (uint32_t it = 1;; ++it) {
@@ -199,8 +214,15 @@ struct TiledArgs {
   uint32_t stage_bytes;
   int nstages;
   int *status;
-  uint64_t timeout_ns;
+  uint64_t timeout_ns;  // limit of every pipeline wait (the method's wait limit)
 };
+
+// Limit of the producer's drain after a failed wait.  The copies it waits for
+// were issued already and complete without any other warp, so this wait
+// does not depend on the (possibly tiny) pipeline limit.
+constexpr uint64_t kDrainLimitNs = 4000000000ull;
+// Pipeline wait limit when the method sets none.
+constexpr uint64_t kDefaultWaitNs = 2000000000ull;
 
 // Issue the copies of tile t into the stage at `stage` (one whole warp).
 __device__ __forceinline__ void issue_tile(const TiledArgs &a, const CUtensorMap *map, int t,
@@ -684,7 +706,7 @@ __global__ void __launch_bounds__(StagedShape<OP>::threads, 1)
       if (lane == 0) atomicCAS(a.status, 0, (int)NB_ETIMEOUT);
       // copies already issued (iterations k-NS .. k-1) land before exit (bounded)
       for (int j = (k >= NS ? k - NS : 0); j < k; ++j)
-        if (!mbar_wait_bounded(full0 + 8 * (j % NS), (uint32_t)(j / NS) & 1u, a.timeout_ns)) break;
+        if (!mbar_wait_bounded(full0 + 8 * (j % NS), (uint32_t)(j / NS) & 1u, kDrainLimitNs)) break;
     }
     return;
   }
@@ -934,7 +956,7 @@ int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, 
   a.nstages = nstages;
   a.status = nullptr;
   if (const int rc = status_word(&a.status)) return rc;
-  a.timeout_ns = 2000000000ull;
+  a.timeout_ns = m->wait_limit_ns >= 0 ? (uint64_t)m->wait_limit_ns : kDefaultWaitNs;
   const size_t smem = (size_t)nstages * a.stage_bytes + 16 * (size_t)nstages;
   if (smem > 227 * 1024) {
     set_error("staged kernel: nstages * stage size exceeds 227 KB of shared memory");

@@ -108,6 +108,7 @@ SIGNATURES = {
     "nb_method_set_kernel": [_P, _I, _I],
     "nb_method_set_compensated": [_P, _I],
     "nb_method_set_staging": [_P, _I, _I],
+    "nb_method_set_wait_limit": [_P, ctypes.c_int64],
     "nb_fs_nodecolumns": [_P, _I, _I, ctypes.POINTER(_P)],
     "nb_fs_release": [_P],
     "nb_fs_level_stride": [_P, _I64P],
@@ -141,6 +142,7 @@ SIGNATURES = {
     "nb_server_poll": [_P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(nb_result)],
     "nb_server_output": [_P, ctypes.c_uint64, _P, ctypes.c_int64],
     "nb_server_input": [_P, ctypes.c_uint64, _P, ctypes.c_int64],
+    "nb_server_inject_failure": [_P, ctypes.c_uint64, ctypes.c_int32],
     "nb_server_stats": [_P, _I64P, _I64P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)],
     "nb_server_run_trace": [_P, ctypes.POINTER(nb_request), _P, _I, ctypes.POINTER(nb_result)],
 }
@@ -384,6 +386,12 @@ class Method(_Handle):
     def set_compensated(self, on: bool) -> None:
         check(lib().nb_method_set_compensated(self._h, 1 if on else 0))
 
+    def set_wait_limit(self, limit_ns: int = -1) -> None:
+        """Limit of the staged kernels' pipeline waits in ns (-1 = default
+        2 s; 0 = test once).  A wait that runs out records NB_ETIMEOUT in the
+        device status word."""
+        check(lib().nb_method_set_wait_limit(self._h, int(limit_ns)))
+
 
 _DT = {torch.float32: NB_F32, torch.float64: NB_F64}
 
@@ -610,6 +618,12 @@ class Server(_Handle):
         x = np.zeros((req.nfields, meth.mesh.V, lp, nvar), dtype=dt)
         check(lib().nb_server_input(self._h, ticket, x.ctypes.data, x.nbytes))
         return x[:, :, :req.nlev, :] if nvar == 2 else x[:, :, :req.nlev, 0]
+
+    def inject_failure(self, seed: int, alloc_index: int) -> None:
+        """Refuse the alloc_index-th device allocation of every request
+        submitted afterwards with this seed (-1 removes it); such a request
+        ends with NB_EOOM (see nb_server_inject_failure)."""
+        check(lib().nb_server_inject_failure(self._h, int(seed), int(alloc_index)))
 
     def stats(self):
         u, p = ctypes.c_int64(), ctypes.c_int64()

@@ -63,6 +63,37 @@ def rel_l2(x: np.ndarray, ref: np.ndarray) -> float:
     return float(np.linalg.norm((x - ref).ravel()) / np.linalg.norm(ref.ravel()))
 
 
+def pole_mask(om) -> np.ndarray:
+    """Grid-order mask of the first and last grid rows (the pole-row nodes,
+    evaluated by the kernels' FP64 pole tiles)."""
+    V = om.V
+    # rows are north to south; a row is the run of nodes sharing its latitude
+    first = int(np.argmax(om.lat != om.lat[0]))
+    last = int(np.argmax(om.lat[::-1] != om.lat[-1]))
+    m = np.zeros(V, dtype=bool)
+    m[:first] = True
+    m[V - last:] = True
+    return m
+
+
+def error_stats(x: np.ndarray, ref: np.ndarray, pole: np.ndarray) -> dict:
+    """Per-op error figures against the oracle, component-wise maximum for
+    vector fields:
+      rel_l2      ||x - ref||_2 / ||ref||_2 over all node-levels;
+      max_rel     max |x - ref| / max |ref| (the per-node maximum error,
+                  scaled by the field's largest value);
+      max_abs     max |x - ref|;
+      pole_rel_l2 relative L2 over the pole-row nodes alone."""
+    if x.ndim == 3:
+        parts = [error_stats(x[..., c], ref[..., c], pole) for c in range(x.shape[-1])]
+        return {k: max(p[k] for p in parts) for k in parts[0]}
+    d = x - ref
+    return {"rel_l2": float(np.linalg.norm(d.ravel()) / np.linalg.norm(ref.ravel())),
+            "max_rel": float(np.abs(d).max() / np.abs(ref).max()),
+            "max_abs": float(np.abs(d).max()),
+            "pole_rel_l2": float(np.linalg.norm(d[pole].ravel()) / np.linalg.norm(ref[pole].ravel()))}
+
+
 def oracle_op(om, op: str, x: np.ndarray) -> np.ndarray:
     return {"grad": oracle.grad, "div": oracle.div, "curl": oracle.curl, "lap": oracle.lap}[op](om, x)
 

@@ -73,3 +73,35 @@ def test_defaults_keep_the_timing_rules(monkeypatch):
     assert a.warmup >= 3 and a.steps >= 1
     assert a.grid == 1280 and a.nlev == 137 and a.gpus == 1
     assert bench.FP64_PEAK_TFLOPS == 1.25
+
+
+def test_cpu_baseline_reports_errors_against_the_oracle():
+    """The CPU-baseline leg times the oracle on the run's own sampled inputs
+    and reports the GPU outputs' error figures against it.  Here the 'GPU'
+    outputs are the oracle's own (rounded to FP32) and a copy with one
+    planted error, so the figures are known."""
+    import types
+
+    import numpy as np
+
+    import oracle
+    N, L = 16, 3
+    m = oracle.build_mesh(N)
+    rng = np.random.default_rng(0)
+    f = rng.standard_normal((m.V, L))
+    uv = rng.standard_normal((m.V, L, 2))
+    exact = {"grad": oracle.grad(m, f), "div": oracle.div(m, uv), "curl": oracle.curl(m, uv),
+             "lap": oracle.lap(m, f)}
+    planted = dict(exact)
+    planted["div"] = exact["div"].copy()
+    planted["div"][0, 1] += 1.0  # a pole-row node (the first grid row)
+    sample = {"levels": [0, 1, 2], "f": f, "uv": uv,
+              "out32": {k: v.astype(np.float32) for k, v in exact.items()}, "out64": planted}
+    cb, err = bench.cpu_baseline(types.SimpleNamespace(grid=N, nlev=L), sample)
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] > 0
+    assert cb["single_core"]["value"] > 0
+    for op in ("grad", "div", "curl", "lap"):
+        assert err["f32"][op]["rel_l2"] < 1e-6 and err["f32"][op]["max_rel"] < 1e-6
+        assert err["f64"][op]["max_abs"] == (1.0 if op == "div" else 0.0)
+    assert err["f64"]["div"]["pole_rel_l2"] > 0
+    assert err["f64"]["div"]["max_rel"] == pytest.approx(1.0 / np.abs(exact["div"]).max(), rel=1e-3)

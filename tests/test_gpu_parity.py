@@ -10,12 +10,15 @@ import torch
 
 import oracle
 from paper_1908_06091_b300 import nabla
-from gpu_helpers import (inputs, oracle_mesh, oracle_op, product, rel_l2, run_op, to_device,
-                         to_grid)
+from gpu_helpers import (error_stats, inputs, oracle_mesh, oracle_op, pole_mask, product, rel_l2,
+                         run_op, to_device, to_grid)
 
 pytestmark = pytest.mark.gpu
 
 TOL = {torch.float64: 1e-12, torch.float32: 1e-5}
+# Per-node gate: max |x - ref| <= MAXTOL * max |ref| (the bound is derived in
+# the docstring of _path_case).
+MAXTOL = {torch.float64: 1e-12, torch.float32: 1e-5}
 OPS = ["grad", "div", "curl", "lap"]
 
 
@@ -78,23 +81,96 @@ def test_plain_fp32_accumulation_also_within_gate():
     assert max(errs.values()) <= 1e-5, errs
 
 
-def test_o640_137_levels_fp32_and_fp64():
-    """O640 x 137: every node, every level (the workload of the second
-    configuration), both precisions."""
-    for dtype in (torch.float32, torch.float64):
-        errs = _case(640, 137, dtype, lmax=40)
-        print(dtype, errs)
-        assert max(errs.values()) <= TOL[dtype], (dtype, errs)
+def _levels_to_grid(t: torch.Tensor, perm: np.ndarray, levels) -> np.ndarray:
+    """Device field -> grid-order float64 host array of the chosen levels."""
+    x = (t if levels is None else t[:, levels]).detach().cpu().numpy().astype(np.float64)
+    out = np.empty_like(x)
+    out[perm] = x
+    return out
 
 
-def test_o1280_137_levels_sampled_levels():
-    """O1280 x 137 (the benchmark workload, same launch configuration): the
-    GPU computes all levels; levels {0, 68, 136} are compared with the
-    oracle element by element over all nodes."""
-    errs = _case(1280, 137, torch.float32, lmax=40, ops=["grad", "div", "curl"],
-                 levels=[0, 68, 136])
-    print(errs)
-    assert max(errs.values()) <= 1e-5, errs
+def _path_case(N, nlev, dtype, lmax, levels=None):
+    """Every call of the operator path on one set of seeded inputs, in the
+    default launch configuration (the one bench.py times): the single
+    operators, nb_nabla_gradlap (the gradient and the divergence of it, the
+    Laplacian), nb_nabla_divcurl and the standalone Laplacian.  Returns the
+    error figures of gpu_helpers.error_stats for each output against the
+    oracle on `levels` (all levels when None).
+
+    The per-node bound.  In the FP32 path each output is a sum of at most
+    d + 1 terms (d <= 7 neighbours in the main region, plus the self term of
+    div and curl), and each term is of the size of the result: the
+    difference form multiplies a weight of size |S|/V ~ 1/h by a difference
+    of size h |grad x|.  The sum is rounded at most d + 3 times (one FMA per
+    term, the combination of the partial sums, the two vector halves), so
+    |err| <= (d + 3) u sum|term| ~ 10 * 2^-24 * 7 max|ref| ~ 4e-6 max|ref| at
+    the node where the terms are largest; the pole rows run in FP64 and are
+    rounded once to FP32.  The gate is 1e-5 of max|ref|, the same figure as
+    the relative-L2 gate.  The FP64 path differs from the oracle only in
+    summation order and in the projection of the weights (a few tens of
+    roundings of 1.1e-16 of terms of the result's size), so 1e-12 of
+    max|ref| leaves a wide margin.  The pole rows alone are gated by their
+    relative L2 at the dtype's tolerance."""
+    g, m, meth = product(N)
+    om = oracle_mesh(N)
+    f, uv = inputs(om, nlev, lmax, dtype)
+    perm = m.permutation()
+    fs = nabla.NodeColumns(meth, nlev, dtype)
+    fd, uvd = to_device(fs, f, perm, 1), to_device(fs, uv, perm, 2)
+    sel = slice(None) if levels is None else levels
+    refs = {"grad": oracle_op(om, "grad", f[:, sel].astype(np.float64)),
+            "lap": oracle_op(om, "lap", f[:, sel].astype(np.float64)),
+            "div": oracle_op(om, "div", uv[:, sel].astype(np.float64)),
+            "curl": oracle_op(om, "curl", uv[:, sel].astype(np.float64))}
+    del f, uv
+    pole = pole_mask(om)
+    nan = float("nan")
+    G, Lg = fs.create_field(nvar=2, fill=nan), fs.create_field(fill=nan)
+    D, Z = fs.create_field(fill=nan), fs.create_field(fill=nan)
+    nabla.gradlap(meth, fd, G, Lg)
+    nabla.divcurl(meth, uvd, D, Z)
+    torch.cuda.synchronize()
+    assert nabla.device_status() == 0
+    got = {"gradlap.grad": (G, "grad"), "gradlap.lap": (Lg, "lap"),
+           "divcurl.div": (D, "div"), "divcurl.curl": (Z, "curl")}
+    stats = {}
+    for name, (t, op) in got.items():
+        x = _levels_to_grid(t, perm, levels)
+        assert np.isfinite(x).all(), name
+        stats[name] = error_stats(x, refs[op], pole)
+    del G, Lg, D, Z, got
+    for op in ("grad", "div", "curl", "lap"):
+        x = _levels_to_grid(run_op(meth, fs, op, fd if op in ("grad", "lap") else uvd), perm, levels)
+        assert np.isfinite(x).all(), op
+        stats[op] = error_stats(x, refs[op], pole)
+    return stats
+
+
+def _gate(stats, dtype):
+    for name, s in stats.items():
+        print(f"{name:14s} rel_l2 {s['rel_l2']:.3e}  max_rel {s['max_rel']:.3e}  "
+              f"max_abs {s['max_abs']:.3e}  pole_rel_l2 {s['pole_rel_l2']:.3e}")
+    bad = {n: s for n, s in stats.items()
+           if not (s["rel_l2"] <= TOL[dtype] and s["max_rel"] <= MAXTOL[dtype]
+                   and s["pole_rel_l2"] <= TOL[dtype])}
+    assert not bad, bad
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64], ids=["f32", "f64"])
+def test_o640_137_levels_every_call(dtype):
+    """O640 x 137, every node and level (the workload of the second
+    configuration), both precisions: relative-L2, per-node maximum and
+    pole-row gates on every call of the operator path."""
+    _gate(_path_case(640, 137, dtype, 40), dtype)
+
+
+def test_o1280_137_levels_every_timed_call():
+    """O1280 x 137 FP32, the benchmark workload in its launch configuration.
+    The GPU computes all levels; levels {0, 68, 136} of the gradient and the
+    Laplacian of nb_nabla_gradlap, the div and curl of nb_nabla_divcurl and
+    the single-operator calls are compared with the oracle over all nodes,
+    with the relative-L2, per-node maximum and pole-row gates."""
+    _gate(_path_case(1280, 137, torch.float32, 40, levels=[0, 68, 136]), torch.float32)
 
 
 def test_gradient_of_constant_is_zero_on_gpu():

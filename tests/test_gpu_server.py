@@ -146,3 +146,39 @@ def test_poll_reports_pending_then_the_waited_result(server):
     assert isinstance(seen_pending, bool)
     with pytest.raises(nabla.NablaError):
         server.poll(t + 10_000)
+
+
+def test_injected_failure_mid_request_spares_the_requests_beside_it(server):
+    """A request whose fifth device allocation is refused (host-side
+    injection: the second column block's output buffer, after the first
+    block's synthesis and operator have been enqueued) ends with NB_EOOM,
+    returns its budget, and leaves the requests in flight beside it bitwise
+    equal to their runs alone; the same request succeeds once the injection
+    is removed."""
+    mix = [nabla.Server.request(op, N, L, nfields=nf, dtype=dt, seed=500 + k, keep_output=True)
+           for k, (op, N, L, nf, dt) in enumerate([("lap", 24, 37, 3, nabla.NB_F32),
+                                                   ("grad", 16, 7, 2, nabla.NB_F64),
+                                                   ("div", 24, 37, 4, nabla.NB_F32),
+                                                   ("curl", 16, 37, 1, nabla.NB_F32),
+                                                   ("lap", 16, 1, 8, nabla.NB_F64)])]
+    alone = [server.output(server.wait(server.submit(r)).ticket, r) for r in mix]
+    # 8 fields of 37 levels: 3 fields per column block of at most 144 levels
+    bad = nabla.Server.request("grad", 24, 37, nfields=8, seed=999, keep_output=True)
+    server.inject_failure(999, 4)  # weights, block 0 in/out, block 1 in, block 1 out
+    try:
+        tickets = []
+        for k, r in enumerate(mix):
+            tickets.append(server.submit(r))
+            if k == 1:
+                t_bad = server.submit(bad)
+        assert server.wait(t_bad).status == nabla.NB_EOOM
+        for t, r, ref in zip(tickets, mix, alone):
+            assert server.wait(t).status == nabla.NB_OK
+            assert np.array_equal(server.output(t, r), ref)
+    finally:
+        server.inject_failure(999, -1)
+    assert server.wait(server.submit(bad)).status == nabla.NB_OK
+    st = server.stats()
+    assert st["used"] == 0 and st["inflight"] == 0 and st["pending"] == 0
+    with pytest.raises(nabla.NablaError):
+        server.inject_failure(1, -2)

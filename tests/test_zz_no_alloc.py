@@ -39,6 +39,29 @@ def _rel(a, b):
     return (torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)).item()
 
 
+class _CountingAllocator:
+    """A caller's allocator (nb_set_allocator) that counts the library's
+    device allocations and serves them from torch's caching allocator."""
+
+    def __init__(self):
+        self.allocs = 0
+
+        def alloc(ctx, nbytes, stream):
+            self.allocs += 1
+            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+
+        def release(ctx, ptr, nbytes, stream):
+            torch.cuda.caching_allocator_delete(ptr)
+        self._a = nabla.nb_allocator(None, nabla._ALLOC_FN(alloc), nabla._RELEASE_FN(release))
+
+    def __enter__(self):
+        nabla.check(nabla.lib().nb_set_allocator(ctypes.byref(self._a)))
+        return self
+
+    def __exit__(self, *exc):
+        nabla.check(nabla.lib().nb_set_allocator(None))
+
+
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64], ids=["f32", "f64"])
 def test_noalloc_laplacian_matches_regular_entry_twice_in_a_row(dtype):
     N, nlev = 48, 37
@@ -50,9 +73,17 @@ def test_noalloc_laplacian_matches_regular_entry_twice_in_a_row(dtype):
         f.copy_(torch.randn(f.shape, dtype=dtype, device="cuda", generator=gen) * (1 + call))
         ref = fs.create_field(fill=float("nan"))
         got = fs.create_field(fill=float("nan"))
-        _lap_regular(meth, f, ref)
-        assert _lap_noalloc(meth, f, got) == nabla.NB_OK, nabla.lib().nb_last_error()
-        torch.cuda.synchronize()
+        with _CountingAllocator() as counter:
+            _lap_regular(meth, f, ref)  # library scratch: one allocation through the caller's allocator
+            torch.cuda.synchronize()
+            assert counter.allocs >= 1
+            counter.allocs = 0
+            free0 = torch.cuda.mem_get_info()[0]
+            assert _lap_noalloc(meth, f, got) == nabla.NB_OK, nabla.lib().nb_last_error()
+            torch.cuda.synchronize()
+            assert counter.allocs == 0
+            if call == 1:  # the array was taken on the first call; nothing is allocated now
+                assert torch.cuda.mem_get_info()[0] == free0
         assert torch.isfinite(got).all()
         assert _rel(got, ref) <= TOL[dtype], (call, _rel(got, ref))
     assert nabla.device_status() == 0
