@@ -30,8 +30,8 @@ OPS = ("grad", "div", "curl", "lap")
 # one step: grad(f) -> g; lap(f) = div(g), the divergence of the step's own
 # gradient (as nb_nabla_gradlap computes it); div and curl of uv in one pass
 PARTS = ("grad", "lap_from_grad", "divcurl")
-# Nominal dense FP64 rate of a B300 (TFLOP/s), the FP64 path's ALU roofline.
-# A cuBLAS DGEMM on this part measured 1.05.
+# Nominal dense FP64 rate of a B300 (TFLOP/s), reported beside the measured
+# rate of the FMA-chain probe that the FP64 path's roofline uses.
 FP64_PEAK_TFLOPS = 1.25
 METRIC = "Gnode-levels/s per nabla op (O1280x137, fp32 vs fp64), % HBM roofline; p99 ms"
 
@@ -308,6 +308,19 @@ def bench_ours(a):
             e1.record(stream)
             stream.synchronize()
             single[op] = round(e0.elapsed_time(e1) / a.single_op_reps, 4)
+        # the single-pass Laplacian (NB_LAP_FUSED), bit-identical to the
+        # two-pass route timed above
+        if a.single_op_reps > 0:
+            method.set_laplacian_route(nabla.LAP_FUSED)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            nabla.apply(method, "lap", f, outs[3], stream=stream)
+            e0.record(stream)
+            for _ in range(a.single_op_reps):
+                nabla.apply(method, "lap", f, outs[3], stream=stream)
+            e1.record(stream)
+            stream.synchronize()
+            method.set_laplacian_route(nabla.LAP_TWO_PASS)
+            single["lap_fused_single_pass"] = round(e0.elapsed_time(e1) / a.single_op_reps, 4)
     # the edge-based baseline (per-edge differences, then a node reduction)
     edge_ms = {}
     if a.single_op_reps > 0:
@@ -351,6 +364,10 @@ def bench_ours(a):
         flops = {"grad": 30, "lap_from_grad": 40, "divcurl": 80}
         dom64 = max(ms64, key=ms64.get)
         tf = flops[dom64] * nl / (ms64[dom64] * 1e-3) / 1e12
+        # the FP64 units' rate on this GPU, measured by an FMA-chain probe
+        # (median of three launches)
+        probes = [nabla.probe_fp64_rate(40000, stream=stream) for _ in range(3)]
+        fp64_peak = statistics.median(p[0] for p in probes)
         fp64 = {"ms_per_step": round(sum(ms64.values()), 3),
                 "value": round(4 * nl / (sum(ms64.values()) * 1e-3) / 1e9, 2),
                 "per_op": {op: {"ms": round(ms64[op], 3),
@@ -358,9 +375,11 @@ def bench_ours(a):
                                 "tflops": round(flops[op] * nl / (ms64[op] * 1e-3) / 1e12, 3)}
                            for op in PARTS},
                 "roofline": {"bound": "alu", "kernel": dom64, "achieved": round(tf, 3),
-                             "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                             "frac": round(tf / FP64_PEAK_TFLOPS, 3),
-                             "peak_kind": "nominal B300 FP64 (no measured FP64 peak on file)",
+                             "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
+                             "frac": round(tf / fp64_peak, 3),
+                             "peak_kind": "measured: FP64 FMA-chain probe on this GPU (nb_probe_fp64_rate, "
+                                          "median of 3)",
+                             "nominal_peak": FP64_PEAK_TFLOPS,
                              "flops_per_node_level": flops[dom64]}}
         if sample is not None:
             sample["out64"] = sample_outputs(mesh, outs64, sample["levels"])
@@ -652,15 +671,18 @@ def cpu_baseline(a, sample):
     m = oracle.build_mesh(a.grid, oracle.EARTH_RADIUS_M)
     f, uv = sample["f"], sample["uv"]
     L = f.shape[1]
-    t = time.perf_counter()
-    ref = {"grad": oracle.grad(m, f), "div": oracle.div(m, uv), "curl": oracle.curl(m, uv),
-           "lap": oracle.lap(m, f)}
-    dt = time.perf_counter() - t
+    ts = []
+    for _ in range(3):  # median of three runs of the sample
+        t = time.perf_counter()
+        ref = {"grad": oracle.grad(m, f), "div": oracle.div(m, uv), "curl": oracle.curl(m, uv),
+               "lap": oracle.lap(m, f)}
+        ts.append(time.perf_counter() - t)
+    dt = statistics.median(ts)
     cores = _omp_threads()
     out = {"value": round(4 * m.V * L / dt / 1e9, 5), "unit": "Gnode-levels/s", "cores": cores,
            "kind": "oracle", "seconds": round(dt, 2),
            "sample": f"O{a.grid}, {L} of {a.nlev} levels (spread over the column) of the run's own "
-                     "inputs, grad+div+curl+lap, FP64 C + OpenMP"}
+                     "inputs, grad+div+curl+lap, FP64 C + OpenMP, median of 3 runs"}
     # the same oracle on one thread (OpenMP runtime of this process set to
     # one thread, then restored), median of three runs on two levels
     L1 = min(2, L)

@@ -201,6 +201,27 @@ int nb_mesh_tile_plan(const nb_mesh *mesh, int rcap, int nmax, int32_t *ntiles,
                       int32_t *ntiles_main, int64_t *nhalo, int32_t *node0, int32_t *halo_ptr,
                       int32_t *halo, uint16_t *lnbr);
 
+/* Host-side check of a tile plan in the format nb_mesh_tile_plan returns
+ * (ntiles tiles; node0[ntiles + 1], halo_ptr[ntiles + 1], halo[], lnbr[2E]):
+ * the tiles cover the nodes in order, each halo entry is a valid node
+ * outside its tile, and lnbr maps every CSR neighbour of a tile's node to
+ * the staged row holding it (own node k: row k; halo entry h: n + h).  The
+ * library runs the same check on each plan of its staged kernels before
+ * uploading it, so a corrupted plan is refused before any launch.
+ * Errors: NB_EINVAL with the first violation in nb_last_error. */
+int nb_check_tile_plan(const nb_mesh *mesh, int32_t ntiles, const int32_t *node0, const int32_t *halo_ptr,
+                       const int32_t *halo, const uint16_t *lnbr);
+
+/* Host-side statistics of the tile plan the single-pass Laplacian
+ * (NB_LAP_FUSED) builds for FP32 columns of nlev levels at the padded
+ * stride: tiles, tiles before the pole-row tiles, the largest number of
+ * g-nodes (own plus first-ring nodes) of a tile, and fits = 1 when every
+ * tile, its rings counted exactly, fits the kernel's shared-memory layout
+ * (the library refuses to launch a plan that does not).  Runs on the host
+ * only (for tests).  Errors: NB_EINVAL (nlev outside [16, 1020]). */
+int nb_mesh_lap_plan(const nb_mesh *mesh, int nlev, int32_t *ntiles, int32_t *ntiles_main,
+                     int32_t *max_gnodes, int32_t *fits);
+
 /* First node of the pole-row block: nodes [cap_begin, V) are the nodes of
  * the first and last grid rows, which the FP32 kernels treat in FP64. */
 int nb_mesh_cap_begin(const nb_mesh *mesh, int64_t *cap_begin);
@@ -534,9 +555,38 @@ int nb_method_set_kernel(nb_method *method, int variant, int tile_nodes);
  * fill one stage. */
 int nb_method_set_staging(nb_method *method, int nstages, int stage_kb);
 
-/* Accumulation mode of the FP32 path: 1 = compensated (Kahan, default),
- * 0 = plain FP32 FMA chain (for accuracy/throughput comparison). */
+/* Accumulation mode of the FP32 path: 1 = compensated (default): per node
+ * the edge terms are summed in groups by FMA chains, the group sums are
+ * combined by error-free Fast2Sum steps and their rounding error is added
+ * last (after the self term of div and curl); 0 = the same sums without the
+ * correction (for accuracy/throughput comparison). */
 int nb_method_set_compensated(nb_method *method, int on);
+
+/* Route of the Laplacian (nb_nabla_laplacian, nb_nabla_apply with
+ * NB_OP_LAP, nb_nabla_gradlap) for FP32 fields the staged kernels take
+ * (16-byte aligned columns of at least 16 levels, kernel variant AUTO or
+ * TILED); other fields always take two passes.
+ *   NB_LAP_TWO_PASS (default): a gradient pass into scratch (or g) and a
+ *     divergence pass of it; the gradient goes through HBM.
+ *   NB_LAP_FUSED: one pass (Sec. 4.7, Fig. 33: the Laplacian is one Nabla
+ *     operator): each tile stages f on its nodes and two rings of
+ *     neighbours, computes the gradient on its nodes and the first ring in
+ *     shared memory and the divergence of it on its nodes; the gradient
+ *     reaches HBM only when nb_nabla_gradlap asks for it.  Bit-identical to
+ *     the two-pass route.
+ * Errors: NB_EINVAL. */
+enum { NB_LAP_TWO_PASS = 0, NB_LAP_FUSED = 1 };
+int nb_method_set_laplacian_route(nb_method *method, int route);
+
+/* Item shape of the staged FP32 div / curl kernels (and the fused pass):
+ * each consumer thread takes `units` 16-byte units (two levels of (u, v))
+ * of one node's column per item, spread G units apart, G items per node.
+ * aligned = 1 rounds G up to a multiple of 8, so that no quarter-warp reads
+ * two nodes' columns (no shared-memory bank conflicts) at the price of idle
+ * items; 0 does not round.  units = 0 / aligned = -1 let the library choose
+ * per level count.  Results do not depend on the shape (each level's
+ * arithmetic is the same).  For tuning and tests; errors: NB_EINVAL. */
+int nb_method_set_item_shape(nb_method *method, int units, int aligned);
 
 /* Limit of every wait inside the staged kernels' copy pipeline (a warp
  * waiting for a stage's copies to land, or for the consumer warps to release
@@ -552,6 +602,15 @@ int nb_method_set_compensated(nb_method *method, int on);
  * limit makes the waits run out without any fault.  Returns NB_EINVAL for
  * other values.  (No counterpart in the paper.) */
 int nb_method_set_wait_limit(nb_method *method, int64_t limit_ns);
+
+/* Measured FP64 FMA rate of the current device, the roofline of the FP64
+ * operator path (which B300's FP64 units bound, not HBM): one launch of
+ * independent FMA chains (8 per thread, `iters` steps, 4 CTAs of 256
+ * threads per SM) timed with CUDA events on `stream` after a warm-up
+ * launch; *tflops = 2 x FMAs / time, *ms the launch time.  Waits for the
+ * stream.  ~40000 iters take ~0.1 s on a B300.  (No counterpart in the
+ * paper.)  Errors: NB_EINVAL, NB_ECUDA. */
+int nb_probe_fp64_rate(int64_t iters, void *stream, double *tflops, double *ms);
 
 /* Number of this library's kernel launches since load (all devices). */
 int nb_launch_count(int64_t *count);

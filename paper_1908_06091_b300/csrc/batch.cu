@@ -47,6 +47,7 @@ struct BItem {
   const void *in;
   void *out;
   int64_t in_stride, out_stride;
+  int *status;  // device status word (index checks of the bounds-checked build)
 };
 
 constexpr int kBatchThreads = 256;
@@ -66,7 +67,7 @@ __device__ __forceinline__ void unit_point_f32(const BItem &it, int64_t i, int l
       KahanAcc ax, ay;
       PlainAcc px, py;
       for (int32_t p = p0; p < p1; ++p) {
-        const int32_t j = __ldg(it.nbr + p);
+        const int32_t j = (int32_t)NB_IDX(__ldg(it.nbr + p), 0, it.V, it.status);
         const float2 wp = __ldg(w + p);
         const float d = __fsub_rn(__ldg(f + (int64_t)j * it.in_stride + l), fi);
         if (comp) {
@@ -83,7 +84,7 @@ __device__ __forceinline__ void unit_point_f32(const BItem &it, int64_t i, int l
       const double2 *w = static_cast<const double2 *>(it.w64);
       double sx = 0, sy = 0;
       for (int32_t p = p0; p < p1; ++p) {
-        const int32_t j = __ldg(it.nbr + p);
+        const int32_t j = (int32_t)NB_IDX(__ldg(it.nbr + p), 0, it.V, it.status);
         const double2 wp = __ldg(w + p);
         const double d = (double)__ldg(f + (int64_t)j * it.in_stride + l) - (double)fi;
         sx = fma(wp.x, d, sx);
@@ -105,7 +106,7 @@ __device__ __forceinline__ void unit_point_f32(const BItem &it, int64_t i, int l
       KahanAcc acc;
       PlainAcc pacc;
       for (int32_t p = p0; p < p1; ++p) {
-        const int32_t j = __ldg(it.nbr + p);
+        const int32_t j = (int32_t)NB_IDX(__ldg(it.nbr + p), 0, it.V, it.status);
         const float2 wp = __ldg(w + p);
         const float *cj = uv + (int64_t)j * it.in_stride + 2 * l;
         const float du = __fsub_rn(__ldg(cj), ui), dv = __fsub_rn(__ldg(cj + 1), vi);
@@ -126,7 +127,7 @@ __device__ __forceinline__ void unit_point_f32(const BItem &it, int64_t i, int l
       const double2 sw = __ldg(static_cast<const double2 *>(it.s64) + i);
       double s = 0;
       for (int32_t p = p0; p < p1; ++p) {
-        const int32_t j = __ldg(it.nbr + p);
+        const int32_t j = (int32_t)NB_IDX(__ldg(it.nbr + p), 0, it.V, it.status);
         const double2 wp = __ldg(w + p);
         const float *cj = uv + (int64_t)j * it.in_stride + 2 * l;
         s = fma(wp.x, (double)__ldg(cj) - (double)ui, s);
@@ -153,7 +154,7 @@ __device__ __forceinline__ void unit_group4_f32(const BItem &it, int64_t i, int 
       KahanAcc ax[4], ay[4];
       PlainAcc px[4], py[4];
       for (int32_t p = p0; p < p1; ++p) {
-        const int32_t j = __ldg(it.nbr + p);
+        const int32_t j = (int32_t)NB_IDX(__ldg(it.nbr + p), 0, it.V, it.status);
         const float2 wp = __ldg(w + p);
         float fj[4];
         load_scalar_f32<4>(f + (int64_t)j * it.in_stride, l0, it.nlev, fj);
@@ -178,7 +179,7 @@ __device__ __forceinline__ void unit_group4_f32(const BItem &it, int64_t i, int 
       const double2 *w = static_cast<const double2 *>(it.w64);
       double sx[4] = {0, 0, 0, 0}, sy[4] = {0, 0, 0, 0};
       for (int32_t p = p0; p < p1; ++p) {
-        const int32_t j = __ldg(it.nbr + p);
+        const int32_t j = (int32_t)NB_IDX(__ldg(it.nbr + p), 0, it.V, it.status);
         const double2 wp = __ldg(w + p);
         float fj[4];
         load_scalar_f32<4>(f + (int64_t)j * it.in_stride, l0, it.nlev, fj);
@@ -217,7 +218,7 @@ __device__ __forceinline__ void unit_group4_f32(const BItem &it, int64_t i, int 
       KahanAcc acc[4];
       PlainAcc pacc[4];
       for (int32_t p = p0; p < p1; ++p) {
-        const int32_t j = __ldg(it.nbr + p);
+        const int32_t j = (int32_t)NB_IDX(__ldg(it.nbr + p), 0, it.V, it.status);
         const float2 wp = __ldg(w + p);
         float uj[4], vj[4];
         load_vector_f32<4>(uv + (int64_t)j * it.in_stride, l0, it.nlev, uj, vj);
@@ -245,7 +246,7 @@ __device__ __forceinline__ void unit_group4_f32(const BItem &it, int64_t i, int 
       const double2 sw = __ldg(static_cast<const double2 *>(it.s64) + i);
       double sacc[4] = {0, 0, 0, 0};
       for (int32_t p = p0; p < p1; ++p) {
-        const int32_t j = __ldg(it.nbr + p);
+        const int32_t j = (int32_t)NB_IDX(__ldg(it.nbr + p), 0, it.V, it.status);
         const double2 wp = __ldg(w + p);
         float uj[4], vj[4];
         load_vector_f32<4>(uv + (int64_t)j * it.in_stride, l0, it.nlev, uj, vj);
@@ -281,7 +282,7 @@ __device__ __forceinline__ void unit_point_f64(const BItem &it, int64_t i, int l
     const double fi = __ldg(f + i * it.in_stride + l);
     double sx = 0, sy = 0;
     for (int32_t p = p0; p < p1; ++p) {
-      const int32_t j = __ldg(it.nbr + p);
+      const int32_t j = (int32_t)NB_IDX(__ldg(it.nbr + p), 0, it.V, it.status);
       const double2 wp = __ldg(w + p);
       const double d = __ldg(f + (int64_t)j * it.in_stride + l) - fi;
       sx = fma(wp.x, d, sx);
@@ -296,7 +297,7 @@ __device__ __forceinline__ void unit_point_f64(const BItem &it, int64_t i, int l
     const double2 sw = __ldg(static_cast<const double2 *>(it.s64) + i);
     double s = 0;
     for (int32_t p = p0; p < p1; ++p) {
-      const int32_t j = __ldg(it.nbr + p);
+      const int32_t j = (int32_t)NB_IDX(__ldg(it.nbr + p), 0, it.V, it.status);
       const double2 wp = __ldg(w + p);
       const double *cj = uv + (int64_t)j * it.in_stride + 2 * l;
       s = fma(wp.x, __ldg(cj) - ui, s);
@@ -509,6 +510,10 @@ static BItem make_item(const nb_method *m, int op, const nb_field &in, const nb_
   b.out = out.data;
   b.in_stride = in.node_stride;
   b.out_stride = out.node_stride;
+  b.status = nullptr;
+#ifdef NB_BOUNDS_CHECK
+  status_word(&b.status);  // NULL on failure: the checks still clamp, unrecorded
+#endif
   return b;
 }
 

@@ -83,6 +83,10 @@ int dev_free_async(const DevAlloc &a, void *ptr, size_t bytes, void *stream) {
   return e == cudaSuccess ? NB_OK : cuda_fail(e, "cudaFreeAsync");
 }
 
+int launch_fused_lap(nb_method *m, const nb_field *f, const nb_field *lap, const nb_field *g, cudaStream_t st,
+                     bool *handled);
+int lap_plan_info(const nb_mesh *mesh, int nlev, int32_t *ntiles, int32_t *ntiles_main, int32_t *max_gnodes,
+                  int32_t *fits);
 int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, const nb_field *out2,
                  cudaStream_t st, bool *handled, int comp = -1);
 int device_status(int clear, int *code);
@@ -122,7 +126,11 @@ using nb::set_error;
 
 extern "C" {
 
+#ifdef NB_BOUNDS_CHECK
+const char *nb_version(void) { return "nabla_b300 0.1.0 sm_103a bounds-checked"; }
+#else
 const char *nb_version(void) { return "nabla_b300 0.1.0 sm_103a"; }
+#endif
 
 const char *nb_last_error(void) { return nb::t_last_error.c_str(); }
 
@@ -309,6 +317,27 @@ int nb_mesh_tile_plan(const nb_mesh *m, int rcap, int nmax, int32_t *ntiles, int
   NB_GUARD_END
 }
 
+int nb_check_tile_plan(const nb_mesh *m, int32_t ntiles, const int32_t *node0, const int32_t *halo_ptr,
+                       const int32_t *halo, const uint16_t *lnbr) {
+  NB_REQUIRE(m && node0 && halo_ptr && halo && lnbr, NB_EINVAL, "nb_check_tile_plan: NULL argument");
+  NB_GUARD_BEGIN
+  std::string why;
+  const bool ok = nb::check_tile_plan(m, ntiles, node0, halo_ptr, halo,
+                                      [&](int64_t p, int, int64_t) { return (int64_t)lnbr[p]; }, why);
+  NB_REQUIRE(ok, NB_EINVAL, "nb_check_tile_plan: " + why);
+  return NB_OK;
+  NB_GUARD_END
+}
+
+int nb_mesh_lap_plan(const nb_mesh *m, int nlev, int32_t *ntiles, int32_t *ntiles_main, int32_t *max_gnodes,
+                     int32_t *fits) {
+  NB_REQUIRE(m && ntiles && ntiles_main && max_gnodes && fits, NB_EINVAL, "nb_mesh_lap_plan: NULL argument");
+  NB_REQUIRE(nlev >= 16 && nlev <= 1020, NB_EINVAL, "nb_mesh_lap_plan: nlev in [16, 1020]");
+  NB_GUARD_BEGIN
+  return nb::lap_plan_info(m, nlev, ntiles, ntiles_main, max_gnodes, fits);
+  NB_GUARD_END
+}
+
 int nb_mesh_cap_begin(const nb_mesh *m, int64_t *cap_begin) {
   NB_REQUIRE(m && cap_begin, NB_EINVAL, "nb_mesh_cap_begin: NULL argument");
   *cap_begin = m->cap_begin;
@@ -413,6 +442,24 @@ int nb_method_set_staging(nb_method *m, int nstages, int stage_kb) {
 int nb_method_set_compensated(nb_method *m, int on) {
   NB_REQUIRE(m, NB_EINVAL, "nb_method_set_compensated: NULL method");
   m->compensated = on ? 1 : 0;
+  return NB_OK;
+}
+
+int nb_method_set_laplacian_route(nb_method *m, int route) {
+  NB_REQUIRE(m, NB_EINVAL, "nb_method_set_laplacian_route: NULL method");
+  NB_REQUIRE(route == NB_LAP_TWO_PASS || route == NB_LAP_FUSED, NB_EINVAL,
+             "nb_method_set_laplacian_route: route must be NB_LAP_TWO_PASS or NB_LAP_FUSED");
+  m->lap_route = route;
+  return NB_OK;
+}
+
+int nb_method_set_item_shape(nb_method *m, int units, int aligned) {
+  NB_REQUIRE(m, NB_EINVAL, "nb_method_set_item_shape: NULL method");
+  NB_REQUIRE(units == 0 || units == 2 || units == 3, NB_EINVAL,
+             "nb_method_set_item_shape: units must be 0 (chosen), 2 or 3");
+  NB_REQUIRE(aligned >= -1 && aligned <= 1, NB_EINVAL, "nb_method_set_item_shape: aligned must be -1, 0 or 1");
+  m->item_units = units;
+  m->item_align = aligned;
   return NB_OK;
 }
 
@@ -589,6 +636,12 @@ int launch_op(nb_method *m, int op, const nb_field *in, const nb_field *out,
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (m->mesh->V == 0) return NB_OK;
   if (op != NB_OP_LAP) return launch_single(m, op, in, out, st);
+  if (m->lap_route == NB_LAP_FUSED &&
+      (m->kernel_variant == NB_KERNEL_AUTO || m->kernel_variant == NB_KERNEL_TILED)) {
+    bool handled = false;
+    const int rc = launch_fused_lap(m, in, out, nullptr, st, &handled);
+    if (handled || rc != NB_OK) return rc;
+  }
   // Laplacian: gradient into scratch, then the divergence of it
   nb_field tmp;
   void *owned = nullptr;
@@ -679,6 +732,14 @@ int nb_nabla_gradlap(const nb_method *m, const nb_field *f, const nb_field *g, c
   // g also serves as the Laplacian's scratch: same checks (no aliasing)
   if ((st = nb::validate(m, NB_OP_LAP, f, lap, g)) != NB_OK) return st;
   NB_GUARD_BEGIN
+  nb_method *mm = const_cast<nb_method *>(m);
+  if (mm->mesh->V == 0) return NB_OK;
+  if (mm->lap_route == NB_LAP_FUSED &&
+      (mm->kernel_variant == NB_KERNEL_AUTO || mm->kernel_variant == NB_KERNEL_TILED)) {
+    bool handled = false;
+    const int rc = nb::launch_fused_lap(mm, f, lap, g, static_cast<cudaStream_t>(stream), &handled);
+    if (handled || rc != NB_OK) return rc;
+  }
   // the Laplacian's gradient pass is g: its divergence pass reads it
   st = nb::launch_op(const_cast<nb_method *>(m), NB_OP_GRAD, f, g, nullptr, stream);
   if (st == NB_OK) st = nb::launch_op(const_cast<nb_method *>(m), NB_OP_DIV, g, lap, nullptr, stream);

@@ -8,6 +8,7 @@
 #include <omp.h>
 
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -618,6 +619,258 @@ void build_tile_plan_bytes(const nb_mesh *m, int64_t area, int64_t row_bytes, in
   staged_index(m, node0, halo_ptr, halo, [&](int64_t p, int, int64_t n, int64_t k) {
     loff[p] = (uint32_t)(k < n ? k * row_bytes : hbase(n) + ((k - n) >> 2) * gpitch + ((k - n) & 3) * copy_bytes);
   });
+}
+
+}  // namespace nb
+
+namespace nb {
+
+// ------------------------------------------------ fused Laplacian plans
+
+// Tiles of the single-pass Laplacian.  A tile's own nodes are a run of
+// consecutive nodes; ring 1 = the neighbours of own nodes outside the tile,
+// ring 2 = the neighbours of ring-1 nodes outside own and ring 1.  The
+// kernel stages f on own, ring-1 and ring-2 nodes, computes the gradient on
+// own and ring-1 nodes (the "g-nodes"), then the divergence of it on own
+// nodes.  Tiles grow along the node order while fits(n, H1, H2, own entries,
+// ring-1 entries) holds; the rings are tracked incrementally (a node that
+// joins the tile turns its neighbours into ring 1 and theirs into ring 2;
+// no node ever leaves a ring except by joining the tile), with an undo log
+// for the node that no longer fits.
+template <class Fits>
+static void plan_lap_tiles(const nb_mesh *m, Fits fits, int nmax, int pole_cap, std::vector<int32_t> &node0,
+                           int &ntiles_main) {
+  const int64_t V = m->V;
+  std::vector<int32_t> stamp(V, -1);
+  std::vector<uint8_t> state(V, 0);  // valid when stamp == tile: 1 own, 2 ring 1, 3 ring 2
+  auto deg = [&](int64_t x) { return (int64_t)(m->row_ptr[x + 1] - m->row_ptr[x]); };
+  int32_t tile = 0;
+  node0.clear();
+  struct Undo {
+    int32_t node;
+    int32_t stamp;
+    uint8_t state;
+  };
+  std::vector<Undo> undo;
+  auto cover = [&](int64_t a, int64_t b, int64_t cap) {
+    int64_t n0 = a;
+    while (n0 < b) {
+      ++tile;
+      int64_t n = 0, H1 = 0, H2 = 0, Eo = 0, E1 = 0;
+      auto st = [&](int64_t x) -> uint8_t { return stamp[x] == tile ? state[x] : 0; };
+      auto set = [&](int64_t x, uint8_t s) {
+        undo.push_back({(int32_t)x, stamp[x], state[x]});
+        stamp[x] = tile;
+        state[x] = s;
+      };
+      int64_t n1 = n0;
+      while (n1 < b && n < cap) {
+        undo.clear();
+        const int64_t v = n1;
+        const int64_t sn = n, s1 = H1, s2 = H2, so = Eo, se = E1;
+        const uint8_t old = st(v);
+        if (old == 2) --H1, E1 -= deg(v);
+        if (old == 3) --H2;
+        set(v, 1);
+        ++n;
+        Eo += deg(v);
+        for (int64_t p = m->row_ptr[v]; p < m->row_ptr[v + 1]; ++p) {
+          const int32_t j = m->nbr[p];
+          const uint8_t sj = st(j);
+          if (sj == 1 || sj == 2) continue;
+          if (sj == 3) --H2;
+          set(j, 2);
+          ++H1;
+          E1 += deg(j);
+        }
+        // ring 2: neighbours of ring-1 nodes that are in no ring yet (only
+        // the neighbours of v's neighbours can have changed)
+        for (int64_t p = m->row_ptr[v]; p < m->row_ptr[v + 1]; ++p) {
+          const int32_t j = m->nbr[p];
+          if (st(j) != 2) continue;
+          for (int64_t q = m->row_ptr[j]; q < m->row_ptr[j + 1]; ++q) {
+            const int32_t k = m->nbr[q];
+            if (st(k) == 0) {
+              set(k, 3);
+              ++H2;
+            }
+          }
+        }
+        if (n > 1 && !fits(n, H1, H2, Eo, E1)) {
+          for (auto it = undo.rbegin(); it != undo.rend(); ++it) {
+            stamp[it->node] = it->stamp;
+            state[it->node] = it->state;
+          }
+          n = sn, H1 = s1, H2 = s2, Eo = so, E1 = se;
+          break;
+        }
+        ++n1;
+      }
+      node0.push_back((int32_t)n0);
+      n0 = n1;
+    }
+  };
+  cover(0, m->cap_begin, nmax);
+  ntiles_main = (int)node0.size();
+  cover(m->cap_begin, V, std::max(1, std::min(pole_cap, nmax)));
+  node0.push_back((int32_t)V);
+}
+
+void build_lap_plan(const nb_mesh *m, const LapLayout &L, int nmax, int pole_cap, LapPlanHost &out) {
+  const int64_t hb_unit = 128;
+  auto hbase = [&](int64_t n) { return (n * L.row_bytes + hb_unit - 1) / hb_unit * hb_unit; };
+  auto fits = [&](int64_t n, int64_t H1, int64_t H2, int64_t Eo, int64_t E1) {
+    if (n > L.nmax || n + H1 > L.gcap || Eo > L.ecap || Eo + E1 > L.rcap) return false;
+    return hbase(n) + (H1 + H2 + 3) / 4 * L.gpitch <= L.farea;
+  };
+  plan_lap_tiles(m, fits, nmax, pole_cap, out.node0, out.ntiles_main);
+  const int nt = (int)out.node0.size() - 1;
+  // per tile: rings (each sorted), then the offsets and g-phase records
+  std::vector<std::vector<int32_t>> r1(nt), r2(nt);
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int t = 0; t < nt; ++t) {
+    const int32_t a = out.node0[t], b = out.node0[t + 1];
+    std::vector<int32_t> &h1 = r1[t], &h2 = r2[t];
+    for (int64_t p = m->row_ptr[a]; p < m->row_ptr[b]; ++p) {
+      const int32_t j = m->nbr[p];
+      if (j < a || j >= b) h1.push_back(j);
+    }
+    std::sort(h1.begin(), h1.end());
+    h1.erase(std::unique(h1.begin(), h1.end()), h1.end());
+    for (int32_t j : h1)
+      for (int64_t q = m->row_ptr[j]; q < m->row_ptr[j + 1]; ++q) {
+        const int32_t k = m->nbr[q];
+        if ((k < a || k >= b) && !std::binary_search(h1.begin(), h1.end(), k)) h2.push_back(k);
+      }
+    std::sort(h2.begin(), h2.end());
+    h2.erase(std::unique(h2.begin(), h2.end()), h2.end());
+  }
+  out.halo_ptr.assign(nt + 1, 0);
+  out.r1_count.assign(nt, 0);
+  out.gn_ptr.assign(nt + 1, 0);
+  out.rec_ptr.assign(nt + 1, 0);
+  for (int t = 0; t < nt; ++t) {
+    const int32_t a = out.node0[t], b = out.node0[t + 1];
+    out.r1_count[t] = (int32_t)r1[t].size();
+    out.halo_ptr[t + 1] = out.halo_ptr[t] + (int32_t)(r1[t].size() + r2[t].size());
+    // g-node entries: one per own and ring-1 node, plus the end
+    out.gn_ptr[t + 1] = out.gn_ptr[t] + (int32_t)((b - a) + r1[t].size() + 1);
+    int64_t recs = m->row_ptr[b] - m->row_ptr[a];
+    for (int32_t j : r1[t]) recs += m->row_ptr[j + 1] - m->row_ptr[j];
+    out.rec_ptr[t + 1] = out.rec_ptr[t] + (int32_t)recs;
+  }
+  out.halo.resize(out.halo_ptr[nt]);
+  out.gn.resize(out.gn_ptr[nt]);
+  out.rec_p.resize(out.rec_ptr[nt]);
+  out.rec_foff.resize(out.rec_ptr[nt]);
+  out.loff.assign(m->row_ptr[m->V], 0);
+  out.goff.assign(m->row_ptr[m->V], 0);
+  int mg = 0, mr = 0;
+  out.fits = true;
+  for (int t = 0; t < nt; ++t) {
+    mg = std::max(mg, out.gn_ptr[t + 1] - out.gn_ptr[t] - 1);
+    mr = std::max(mr, out.rec_ptr[t + 1] - out.rec_ptr[t]);
+    // every tile, with its exact rings, must fit the layout the kernel uses
+    const int64_t n = out.node0[t + 1] - out.node0[t];
+    const int64_t Eo = m->row_ptr[out.node0[t + 1]] - m->row_ptr[out.node0[t]];
+    const int64_t E1 = (out.rec_ptr[t + 1] - out.rec_ptr[t]) - Eo;
+    if (n < 1 || !fits(n, (int64_t)r1[t].size(), (int64_t)r2[t].size(), Eo, E1)) out.fits = false;
+  }
+  out.max_gnodes = mg;
+  out.max_recs = mr;
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int t = 0; t < nt; ++t) {
+    const int32_t a = out.node0[t], b = out.node0[t + 1];
+    const int64_t n = b - a;
+    const std::vector<int32_t> &h1 = r1[t], &h2 = r2[t];
+    std::copy(h1.begin(), h1.end(), out.halo.begin() + out.halo_ptr[t]);
+    std::copy(h2.begin(), h2.end(), out.halo.begin() + out.halo_ptr[t] + h1.size());
+    // staged slot of node x: own k -> k, ring 1 r -> n + r, ring 2 s -> n + H1 + s
+    auto slot = [&](int32_t x) -> int64_t {
+      if (x >= a && x < b) return x - a;
+      auto it = std::lower_bound(h1.begin(), h1.end(), x);
+      if (it != h1.end() && *it == x) return n + (it - h1.begin());
+      return n + (int64_t)h1.size() + (std::lower_bound(h2.begin(), h2.end(), x) - h2.begin());
+    };
+    auto fbyte = [&](int64_t k) -> uint32_t {
+      return (uint32_t)(k < n ? k * L.row_bytes : hbase(n) + ((k - n) >> 2) * L.gpitch + ((k - n) & 3) * L.copy_bytes);
+    };
+    for (int64_t p = m->row_ptr[a]; p < m->row_ptr[b]; ++p) {
+      const int64_t k = slot(m->nbr[p]);
+      out.loff[p] = fbyte(k);
+      out.goff[p] = (uint32_t)(k * L.g_pitch);  // own or ring 1: k < n + H1
+    }
+    // g-phase records: own nodes then ring-1 nodes, each node's entries in
+    // CSR order; gn = record start relative to the tile | pole-row flag
+    int64_t r = out.rec_ptr[t], g = out.gn_ptr[t];
+    auto add_gnode = [&](int32_t x) {
+      out.gn[g++] = (uint32_t)(r - out.rec_ptr[t]) | (x >= m->cap_begin ? 0x80000000u : 0u);
+      for (int64_t p = m->row_ptr[x]; p < m->row_ptr[x + 1]; ++p) {
+        out.rec_p[r] = (int32_t)p;
+        out.rec_foff[r] = fbyte(slot(m->nbr[p]));
+        ++r;
+      }
+    };
+    for (int32_t x = a; x < b; ++x) add_gnode(x);
+    for (int32_t x : h1) add_gnode(x);
+    out.gn[g] = (uint32_t)(r - out.rec_ptr[t]);
+  }
+}
+
+}  // namespace nb
+
+namespace nb {
+
+// ------------------------------------------------------ plan validation
+
+// A tile plan is valid when its tiles cover [0, V) in order, each halo
+// list holds valid nodes outside its tile, and every CSR neighbour of
+// a tile's node maps (slot(p, t, n)) to the staged slot that holds it: own
+// node k at slot k, halo entry h at slot n + h.  slot returns -1 for an
+// entry it cannot decode.  Run on every plan before it is uploaded, so a
+// corrupted plan is refused before any launch.
+bool check_tile_plan(const nb_mesh *m, int ntiles, const int32_t *node0, const int32_t *halo_ptr,
+                     const int32_t *halo, const std::function<int64_t(int64_t, int, int64_t)> &slot,
+                     std::string &why) {
+  if (ntiles < 0 || (ntiles == 0 && m->V > 0)) {
+    why = "no tiles";
+    return false;
+  }
+  if (node0[0] != 0 || node0[ntiles] != m->V || halo_ptr[0] != 0) {
+    why = "tiles do not cover the nodes";
+    return false;
+  }
+  for (int t = 0; t < ntiles; ++t) {
+    const int32_t a = node0[t], b = node0[t + 1];
+    if (b <= a) {
+      why = "tile " + std::to_string(t) + " is empty or out of order";
+      return false;
+    }
+    const int32_t h0 = halo_ptr[t], h1 = halo_ptr[t + 1];
+    if (h1 < h0) {
+      why = "halo range of tile " + std::to_string(t) + " is reversed";
+      return false;
+    }
+    for (int32_t h = h0; h < h1; ++h) {
+      const int32_t x = halo[h];
+      if (x < 0 || x >= m->V || (x >= a && x < b)) {
+        why = "halo entry " + std::to_string(h) + " of tile " + std::to_string(t) + " is invalid";
+        return false;
+      }
+    }
+    const int64_t n = b - a;
+    for (int64_t p = m->row_ptr[a]; p < m->row_ptr[b]; ++p) {
+      const int32_t j = m->nbr[p];
+      const int64_t k = slot(p, t, n);
+      const bool ok = (k >= 0 && k < n) ? (a + k == j)
+                                        : (k >= n && k - n < h1 - h0 && halo[h0 + (k - n)] == j);
+      if (!ok) {
+        why = "CSR entry " + std::to_string(p) + " of tile " + std::to_string(t) + " maps to the wrong staged column";
+        return false;
+      }
+    }
+  }
+  return true;
 }
 
 }  // namespace nb

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <atomic>
+#include <functional>
 #include <cstdint>
 #include <map>
 #include <memory>
@@ -101,6 +102,16 @@ struct TilePlan {
   uint32_t *d_loff = nullptr;        // 2E (+4): stage byte offset of each CSR neighbour
 };
 
+// Device side of a single-pass Laplacian plan (fusedlap.cu).
+struct LapPlan {
+  int ntiles = 0, ntiles_main = 0, max_gnodes = 0;
+  int64_t bytes = 0;
+  int32_t *d_tile_node0 = nullptr, *d_halo_ptr = nullptr, *d_halo = nullptr, *d_r1_count = nullptr;
+  int32_t *d_gn_ptr = nullptr, *d_rec_ptr = nullptr;
+  uint32_t *d_gn = nullptr, *d_goff = nullptr;
+  void *d_rec = nullptr;  // float4 records
+};
+
 // fvm::Method: geometry and operator weights resident on one device.
 struct nb_method : nb::RefCounted {
   nb_mesh *mesh = nullptr;
@@ -134,8 +145,12 @@ struct nb_method : nb::RefCounted {
   int stage_kb = 0;     // staged kernels: KB per stage (0 = default)
   int compensated = 1;
   int64_t wait_limit_ns = -1;  // staged kernels' pipeline wait limit (-1 = default)
+  int item_units = 0;   // staged div / curl: 2-level units per item (0 = chosen per column)
+  int item_align = -1;  // staged div / curl: items per node a multiple of 8 (1), not (0), chosen (-1)
   std::mutex plan_mu;
   std::map<std::tuple<int64_t, int64_t, int64_t, int, int, int>, std::unique_ptr<TilePlan>> plans;
+  std::map<std::tuple<int64_t, int64_t, int64_t, int64_t, int64_t, int, int>, std::unique_ptr<LapPlan>> lap_plans;
+  int lap_route = 0;    // Laplacian: 0 two passes, 1 single fused pass (FP32 staged)
   ~nb_method() override;
 };
 
@@ -173,6 +188,36 @@ void build_tile_plan_bytes(const nb_mesh *m, int64_t area, int64_t row_bytes, in
                            std::vector<int32_t> &halo_ptr, std::vector<int32_t> &halo,
                            std::vector<uint32_t> &loff, int &max_halo, int &max_entries,
                            int &ntiles_main);
+
+// Stage layout of the single-pass Laplacian (sizes in bytes): f columns of
+// own nodes at row_bytes pitch, of ring nodes in groups of four at gpitch
+// (copy_bytes each), within farea; g columns at g_pitch for at most gcap
+// g-nodes; at most nmax own nodes, ecap own CSR entries, rcap g-phase
+// records (the CSR entries of own and ring-1 nodes).
+struct LapLayout {
+  int64_t row_bytes = 0, copy_bytes = 0, gpitch = 0, farea = 0, g_pitch = 0;
+  int64_t nmax = 0, gcap = 0, ecap = 0, rcap = 0;
+};
+struct LapPlanHost {
+  std::vector<int32_t> node0;     // ntiles + 1
+  int ntiles_main = 0;
+  std::vector<int32_t> halo_ptr;  // ntiles + 1: ring 1 then ring 2 of each tile, each sorted
+  std::vector<int32_t> r1_count;  // ntiles
+  std::vector<int32_t> halo;
+  std::vector<int32_t> gn_ptr;    // ntiles + 1: g-node entries of each tile (own, ring 1, end)
+  std::vector<uint32_t> gn;       // record start relative to the tile | 0x80000000 for pole-row nodes
+  std::vector<int32_t> rec_ptr;   // ntiles + 1
+  std::vector<int32_t> rec_p;     // per record: CSR index of the entry
+  std::vector<uint32_t> rec_foff; // per record: staged byte offset of the entry's neighbour's f column
+  std::vector<uint32_t> loff;     // per CSR entry of an own node: staged f byte offset of the neighbour
+  std::vector<uint32_t> goff;     // per CSR entry of an own node: g byte offset of the neighbour
+  int max_gnodes = 0, max_recs = 0;
+  bool fits = false;  // every tile, rings counted exactly, fits the layout
+};
+void build_lap_plan(const nb_mesh *m, const LapLayout &layout, int nmax, int pole_cap, LapPlanHost &out);
+bool check_tile_plan(const nb_mesh *m, int ntiles, const int32_t *node0, const int32_t *halo_ptr,
+                     const int32_t *halo, const std::function<int64_t(int64_t, int, int64_t)> &slot,
+                     std::string &why);
 
 // device side (nabla_kernels.cu)
 int method_upload(nb_method *m);            // returns NB_* status

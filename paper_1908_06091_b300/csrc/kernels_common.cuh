@@ -9,12 +9,30 @@ namespace nb {
 
 int cuda_fail(cudaError_t e, const char *what);
 void count_launch(int n);
+// device address of the status word on the current device (tiled.cu)
+int status_word(int **out);
 
 #define NB_CUDA(call)                                       \
   do {                                                      \
     cudaError_t _e = (call);                                \
     if (_e != cudaSuccess) return ::nb::cuda_fail(_e, #call); \
   } while (0)
+
+// Index checks of the bounds-checked build (-DNB_BOUNDS_CHECK): an index
+// outside [lo, hi) records NB_EINVAL in the device status word and is
+// replaced by lo, so that no access leaves its buffer; the host sees the
+// error after synchronising (nb_device_status).  Other builds compile the
+// check away.
+#ifdef NB_BOUNDS_CHECK
+__device__ __forceinline__ int64_t nb_checked_index(int64_t x, int64_t lo, int64_t hi, int *status) {
+  if (x >= lo && x < hi) return x;
+  if (status) atomicCAS(status, 0, (int)NB_EINVAL);
+  return lo;
+}
+#define NB_IDX(x, lo, hi, status) nb_checked_index((x), (lo), (hi), (status))
+#else
+#define NB_IDX(x, lo, hi, status) (x)
+#endif
 
 // Compensated (Kahan) accumulation.  add_prod forms the product w * d and
 // subtracts the running correction in one FMA, so each term costs one FFMA

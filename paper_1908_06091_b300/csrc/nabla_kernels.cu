@@ -186,6 +186,8 @@ struct DirectArgs {
   const void *q;
   int64_t q_stride;
   const int32_t *nbr_edge;
+  int64_t E;
+  int *status;  // device status word (index checks of the bounds-checked build)
 };
 
 // op 0: grad.  FP32 arithmetic, compensated or plain accumulation.  EDGE:
@@ -206,11 +208,11 @@ __global__ void __launch_bounds__(256) grad_direct_f32(DirectArgs a) {
     Acc ax[LPT], ay[LPT];
     const float2 *w = static_cast<const float2 *>(a.w32);
     for (int32_t p = p0; p < p1; ++p) {
-      const int32_t j = __ldg(a.nbr + p);
+      const int32_t j = (int32_t)NB_IDX(__ldg(a.nbr + p), 0, a.V, a.status);
       const float2 wp = __ldg(w + p);
       float dj[LPT];
       if (EDGE) {
-        load_scalar_f32<LPT>(static_cast<const float *>(a.q) + (int64_t)__ldg(a.nbr_edge + p) * a.q_stride, l0,
+        load_scalar_f32<LPT>(static_cast<const float *>(a.q) + NB_IDX(__ldg(a.nbr_edge + p), 0, a.E, a.status) * a.q_stride, l0,
                              a.nlev, dj);
         if (j < i)
 #pragma unroll
@@ -237,7 +239,7 @@ __global__ void __launch_bounds__(256) grad_direct_f32(DirectArgs a) {
     const double2 *w = static_cast<const double2 *>(a.w64);
     double sx[LPT] = {}, sy[LPT] = {};
     for (int32_t p = p0; p < p1; ++p) {
-      const int32_t j = __ldg(a.nbr + p);
+      const int32_t j = (int32_t)NB_IDX(__ldg(a.nbr + p), 0, a.V, a.status);
       const double2 wp = __ldg(w + p);
       float fj[LPT];
       load_scalar_f32<LPT>(f + (int64_t)j * a.in_stride, l0, a.nlev, fj);
@@ -285,11 +287,11 @@ __global__ void __launch_bounds__(256) divcurl_direct_f32(DirectArgs a) {
     const float2 sw = __ldg(static_cast<const float2 *>(a.s32) + i);
     Acc acc[LPT];
     for (int32_t p = p0; p < p1; ++p) {
-      const int32_t j = __ldg(a.nbr + p);
+      const int32_t j = (int32_t)NB_IDX(__ldg(a.nbr + p), 0, a.V, a.status);
       const float2 wp = __ldg(w + p);
       float du[LPT], dv[LPT];
       if (EDGE) {
-        load_vector_f32<LPT>(static_cast<const float *>(a.q) + (int64_t)__ldg(a.nbr_edge + p) * a.q_stride, l0,
+        load_vector_f32<LPT>(static_cast<const float *>(a.q) + NB_IDX(__ldg(a.nbr_edge + p), 0, a.E, a.status) * a.q_stride, l0,
                              a.nlev, du, dv);
         if (j < i)
 #pragma unroll
@@ -319,7 +321,7 @@ __global__ void __launch_bounds__(256) divcurl_direct_f32(DirectArgs a) {
     const double2 sw = __ldg(static_cast<const double2 *>(a.s64) + i);
     double s[LPT] = {};
     for (int32_t p = p0; p < p1; ++p) {
-      const int32_t j = __ldg(a.nbr + p);
+      const int32_t j = (int32_t)NB_IDX(__ldg(a.nbr + p), 0, a.V, a.status);
       const double2 wp = __ldg(w + p);
       float uj[LPT], vj[LPT];
       load_vector_f32<LPT>(uv + (int64_t)j * a.in_stride, l0, a.nlev, uj, vj);
@@ -362,9 +364,9 @@ __global__ void __launch_bounds__(256) grad_direct_f64(DirectArgs a) {
 #pragma unroll
   for (int k = 0; k < LPT; ++k) fi[k] = (l0 + k < a.nlev) ? __ldg(ci + l0 + k) : 0.0;
   for (int32_t p = p0; p < p1; ++p) {
-    const int32_t j = __ldg(a.nbr + p);
+    const int32_t j = (int32_t)NB_IDX(__ldg(a.nbr + p), 0, a.V, a.status);
     const double2 wp = __ldg(w + p);
-    const double *cj = EDGE ? static_cast<const double *>(a.q) + (int64_t)__ldg(a.nbr_edge + p) * a.q_stride
+    const double *cj = EDGE ? static_cast<const double *>(a.q) + NB_IDX(__ldg(a.nbr_edge + p), 0, a.E, a.status) * a.q_stride
                             : f + (int64_t)j * a.in_stride;
 #pragma unroll
     for (int k = 0; k < LPT; ++k) {
@@ -403,9 +405,9 @@ __global__ void __launch_bounds__(256) divcurl_direct_f64(DirectArgs a) {
     vi[k] = ok ? __ldg(ci + 2 * (l0 + k) + 1) : 0.0;
   }
   for (int32_t p = p0; p < p1; ++p) {
-    const int32_t j = __ldg(a.nbr + p);
+    const int32_t j = (int32_t)NB_IDX(__ldg(a.nbr + p), 0, a.V, a.status);
     const double2 wp = __ldg(w + p);
-    const double *cj = EDGE ? static_cast<const double *>(a.q) + (int64_t)__ldg(a.nbr_edge + p) * a.q_stride
+    const double *cj = EDGE ? static_cast<const double *>(a.q) + NB_IDX(__ldg(a.nbr_edge + p), 0, a.E, a.status) * a.q_stride
                             : uv + (int64_t)j * a.in_stride;
 #pragma unroll
     for (int k = 0; k < LPT; ++k) {
@@ -480,6 +482,11 @@ int launch_direct(const nb_method *m, int op, const nb_field *in, const nb_field
   a.q = q;
   a.q_stride = q_stride;
   a.nbr_edge = m->d_nbr_edge;
+  a.E = mesh->E;
+  a.status = nullptr;
+#ifdef NB_BOUNDS_CHECK
+  if (const int rc = status_word(&a.status)) return rc;
+#endif
   const bool edge = q != nullptr;
   // 16-byte vectors need aligned bases and strides that are multiples of 4 floats
   const bool vec = !f64 && in->nlev >= 4 && aligned16(in->data) && aligned16(out->data) &&

@@ -24,6 +24,7 @@
 #include <string>
 
 #include "kernels_common.cuh"
+#include "staged_common.cuh"
 
 namespace nb {
 
@@ -32,151 +33,6 @@ __device__ int g_device_status = 0;
 
 int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, const nb_field *out2,
                  cudaStream_t st, bool *handled, int comp = -1);
-
-// ------------------------------------------------------------ PTX helpers
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t done;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(done)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return done != 0;
-}
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-      "l"(src), "r"(bytes), "r"(bar)
-      : "memory");
-}
-// Fire-and-forget prefetch of a global range into L2 (16-byte aligned
-// address, size a multiple of 16).
-__device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
-}
-// Four rows (y0..y3) of a 2-D tensor, one box row each, into consecutive
-// shared memory at `dst` (128-byte aligned).
-__device__ __forceinline__ void gather4_g2s(uint32_t dst, const CUtensorMap *map, int32_t y0, int32_t y1,
-                                           int32_t y2, int32_t y3, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(y0), "r"(y1), "r"(y2), "r"(y3), "r"(bar)
-      : "memory");
-}
-__device__ __forceinline__ uint64_t globaltimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Non-blocking test of the phase (never suspends the thread).
-__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
-  uint32_t done;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(done)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return done != 0;
-}
-
-// Wait for `parity` on the barrier for at most ~`limit_ns`; false on timeout.
-// A limit of 0 tests the phase once without suspending.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
-  if (limit_ns == 0) return mbar_test_wait(bar, parity);
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = globaltimer();
-  for (uint32_t it = 1;; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 255u) == 0 && globaltimer() - t0 > limit_ns) return false;
-  }
-}
-
-// packed FP32x2 arithmetic (two lanes per register pair, IEEE round-to-nearest)
-typedef unsigned long long f2_t;
-__device__ __forceinline__ f2_t pk(float a, float b) {
-  f2_t r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-  return r;
-}
-__device__ __forceinline__ void upk(f2_t r, float &a, float &b) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
-}
-__device__ __forceinline__ f2_t fma2(f2_t a, f2_t b, f2_t c) {
-  f2_t d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-__device__ __forceinline__ f2_t add2(f2_t a, f2_t b) {
-  f2_t d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2_t sub2(f2_t a, f2_t b) {
-  f2_t d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-
-// Kahan accumulation of two independent sums at once.  nc holds the
-// negated running correction.  One term w*d costs one fma2 and three
-// add/sub2: y = w*d + nc; t = s + y; nc = y - (t - s); s = t.  A pair of
-// edge terms is summed as one summand, y = w1*d1 + (w0*d0 + nc) by two
-// fma2, then compensated into s: 2.5 operations per term.  (Each product is
-// rounded once without compensation in either form; the compensation keeps
-// the running sum's rounding out of the result.)
-template <bool COMP>
-struct Kahan2 {
-  f2_t s = 0ull, nc = 0ull;
-  __device__ __forceinline__ void add_prod(f2_t w, f2_t d) {
-    if (COMP) {
-      const f2_t y = fma2(w, d, nc);
-      const f2_t t = add2(s, y);
-      nc = sub2(y, sub2(t, s));
-      s = t;
-    } else {
-      s = fma2(w, d, s);
-    }
-  }
-  __device__ __forceinline__ void add_pair(f2_t w0, f2_t d0, f2_t w1, f2_t d1) {
-    if (COMP) {
-      const f2_t y = fma2(w1, d1, fma2(w0, d0, nc));
-      const f2_t t = add2(s, y);
-      nc = sub2(y, sub2(t, s));
-      s = t;
-    } else {
-      s = fma2(w1, d1, fma2(w0, d0, s));
-    }
-  }
-  // three edge terms as one summand (the six-neighbour path: two per node)
-  __device__ __forceinline__ void add_triple(f2_t w0, f2_t d0, f2_t w1, f2_t d1, f2_t w2, f2_t d2) {
-    if (COMP) {
-      const f2_t y = fma2(w2, d2, fma2(w1, d1, fma2(w0, d0, nc)));
-      const f2_t t = add2(s, y);
-      nc = sub2(y, sub2(t, s));
-      s = t;
-    } else {
-      s = fma2(w2, d2, fma2(w1, d1, fma2(w0, d0, s)));
-    }
-  }
-  __device__ __forceinline__ f2_t value() const { return COMP ? add2(s, nc) : s; }
-};
 
 // ------------------------------------------------------------- kernel
 
@@ -215,14 +71,9 @@ struct TiledArgs {
   int nstages;
   int *status;
   uint64_t timeout_ns;  // limit of every pipeline wait (the method's wait limit)
+  int32_t nnodes;       // nodes of the mesh (index checks)
+  uint32_t col_area;    // staged column offsets lie below this (index checks)
 };
-
-// Limit of the producer's drain after a failed wait.  The copies it waits for
-// were issued already and complete without any other warp, so this wait
-// does not depend on the (possibly tiny) pipeline limit.
-constexpr uint64_t kDrainLimitNs = 4000000000ull;
-// Pipeline wait limit when the method sets none.
-constexpr uint64_t kDefaultWaitNs = 2000000000ull;
 
 // Issue the copies of tile t into the stage at `stage` (one whole warp).
 __device__ __forceinline__ void issue_tile(const TiledArgs &a, const CUtensorMap *map, int t,
@@ -242,6 +93,25 @@ __device__ __forceinline__ void issue_tile(const TiledArgs &a, const CUtensorMap
   const uint32_t hbase = (n * a.row_bytes + 127u) & ~127u;
   const int32_t sa = a.rec16 ? n0 : (n0 & ~1), sb = a.rec16 ? n1 : ((n1 + 1) & ~1);
   const uint32_t sbytes = a.off_s ? (uint32_t)(sb - sa) * (a.rec16 ? 16u : 8u) : 0u;
+#ifdef NB_BOUNDS_CHECK
+  // a tile whose copies would leave their stage regions is not copied: it is
+  // published empty and NB_EINVAL is recorded
+  {
+    const uint32_t send = a.off_s ? a.off_s : a.off_h;
+    const bool bad = n1 <= n0 || n1 > a.nnodes || h1 < h0 || hbase + groups * a.gpitch > a.off_w ||
+                     a.off_w + wbytes > a.off_l || a.off_l + lbytes > a.off_r || a.off_r + rbytes > send ||
+                     (a.off_s && a.off_s + sbytes > a.off_h);
+    if (bad) {
+      if (lane == 0) {
+        atomicCAS(a.status, 0, (int)NB_EINVAL);
+        asm volatile("st.shared.v2.s32 [%0], {%1, %1};" ::"r"(stage + a.off_h), "r"(n0) : "memory");
+        mbar_expect_tx(bar, 0);
+      }
+      __syncwarp();
+      return;
+    }
+  }
+#endif
   if (lane == 0) {
     // header for the consumers, published by the arrive below
     asm volatile("st.shared.v2.s32 [%0], {%1, %2};" ::"r"(stage + a.off_h), "r"(n0), "r"(n1) : "memory");
@@ -265,251 +135,25 @@ __device__ __forceinline__ void issue_tile(const TiledArgs &a, const CUtensorMap
     // a short last group repeats its last node (the copy fills the group's slots)
     const int32_t *hp = a.halo + h0;
     const uint32_t k = 4u * g, last = H - 1u;
-    gather4_g2s(stage + hbase + g * a.gpitch, map, __ldg(hp + k), __ldg(hp + min(k + 1u, last)),
-                __ldg(hp + min(k + 2u, last)), __ldg(hp + min(k + 3u, last)), bar);
+    auto hid = [&](uint32_t q) { return (int32_t)NB_IDX(__ldg(hp + q), 0, a.nnodes, a.status); };
+    gather4_g2s(stage + hbase + g * a.gpitch, map, hid(k), hid(min(k + 1u, last)), hid(min(k + 2u, last)),
+                hid(min(k + 3u, last)), bar);
   }
 }
 
-// Shared-memory loads by 32-bit address (volatile: they must stay after the
-// mbarrier wait that makes the staged data visible).
-__device__ __forceinline__ float4 lds128(uint32_t a) {
-  float4 v;
-  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-               : "r"(a));
+// The view of one staged tile of the single-operator and fused passes.
+__device__ __forceinline__ TileView staged_view(const TiledArgs &a, uint32_t stage) {
+  TileView v;
+  v.n0 = lds_s32(stage + a.off_h);
+  v.n1 = lds_s32(stage + a.off_h + 4u);
+  v.rows = stage;
+  v.s = a.rec16 ? stage + a.off_s - 16u * (uint32_t)v.n0 : stage + a.off_s - 8u * (uint32_t)(v.n0 & ~1);
+  const int32_t ra = v.n0 & ~3;
+  v.r = stage + a.off_r - 4u * (uint32_t)ra;
+  const int32_t pa = lds_s32(v.r + 4u * (uint32_t)v.n0);
+  v.w = a.rec16 ? stage + a.off_w - 16u * (uint32_t)pa : stage + a.off_w - 8u * (uint32_t)(pa & ~1);
+  v.l = stage + a.off_l - 4u * (uint32_t)(pa & ~3);
   return v;
-}
-__device__ __forceinline__ float2 lds64(uint32_t a) {
-  float2 v;
-  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
-  return v;
-}
-// 16 bytes as two packed FP32x2 registers, 8 bytes as one (no repacking moves)
-__device__ __forceinline__ void lds2x64(uint32_t a, unsigned long long &lo, unsigned long long &hi) {
-  asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(lo), "=l"(hi) : "r"(a));
-}
-__device__ __forceinline__ unsigned long long lds_b64(uint32_t a) {
-  unsigned long long v;
-  asm volatile("ld.shared.b64 %0, [%1];" : "=l"(v) : "r"(a));
-  return v;
-}
-__device__ __forceinline__ uint32_t lds_u32(uint32_t a) {
-  uint32_t v;
-  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
-  return v;
-}
-__device__ __forceinline__ int32_t lds_s32(uint32_t a) {
-  int32_t v;
-  asm volatile("ld.shared.s32 %0, [%1];" : "=r"(v) : "r"(a));
-  return v;
-}
-
-// 32-bit shared addresses of one staged tile: entry p's weight is at
-// w + 8 p, its staged byte offset at l + 4 p, node i's row pointer at r + 4 i
-// (wrap-around arithmetic; the sums land inside the stage).
-struct TileView {
-  int32_t n0, n1;
-  uint32_t rows, w, l, r, s;
-  __device__ __forceinline__ TileView(const TiledArgs &a, int t, uint32_t stage) {
-    n0 = lds_s32(stage + a.off_h);
-    n1 = lds_s32(stage + a.off_h + 4u);
-    rows = stage;
-    s = a.rec16 ? stage + a.off_s - 16u * (uint32_t)n0 : stage + a.off_s - 8u * (uint32_t)(n0 & ~1);
-    const int32_t ra = n0 & ~3;
-    r = stage + a.off_r - 4u * (uint32_t)ra;
-    pa = lds_s32(r + 4u * (uint32_t)n0);
-    w = a.rec16 ? stage + a.off_w - 16u * (uint32_t)pa : stage + a.off_w - 8u * (uint32_t)(pa & ~1);
-    l = stage + a.off_l - 4u * (uint32_t)(pa & ~3);
-  }
-  int32_t pa;  // CSR index of the tile's first entry
-};
-
-// Consumer side.  A warp takes items [i0, i1) of tile t, one per lane,
-// stride 32.  All but a handful of nodes of an octahedral mesh have six
-// neighbours: for them the neighbour loop is fully unrolled, so every
-// accumulator and address stays in fixed registers and no loop bookkeeping
-// is issued; other degrees take a loop over neighbour pairs.  Staged data
-// is loaded straight into packed FP32x2 registers.
-//
-// div / curl.  A staged (u, v) column is a sequence of 16-byte units of two
-// levels each; item c of a node takes units c and c + G, so that every
-// shared-memory load of a warp reads consecutive 16-byte words.  FUSED
-// evaluates div and curl of the same wind in one pass: the staged columns,
-// offsets and differences are shared, each operator keeps its own weights
-// and accumulators, and each output gets exactly the arithmetic of its
-// single-operator pass.
-template <bool COMP, bool FUSED>
-__device__ __forceinline__ void divcurl_tile(const TiledArgs &a, int t, uint32_t stage, int part,
-                                             int nparts) {
-  const TileView v(a, t, stage);
-  const uint32_t items = (uint32_t)(v.n1 - v.n0) * a.G;
-  const uint32_t i0 = (uint32_t)(((uint64_t)items * part) / nparts);
-  const uint32_t i1 = (uint32_t)(((uint64_t)items * (part + 1)) / nparts);
-  const bool pole = t >= a.ntiles_main;
-  const int units = (a.nlev + 1) / 2;
-  const uint32_t rb = a.row_bytes;
-  const uint32_t g16 = 16u * (uint32_t)a.G;
-  for (uint32_t item = i0 + (threadIdx.x & 31); item < i1; item += 32) {
-    const uint32_t il = (uint32_t)(((uint64_t)item * a.g_magic) >> a.g_shift);
-    const uint32_t c = item - il * a.G;
-    const int u0 = (int)c, u1 = (int)c + a.G;
-    const bool has1 = u1 < units;
-    const int32_t node = v.n0 + (int32_t)il;
-    const int32_t p0 = lds_s32(v.r + 4u * (uint32_t)node), p1 = lds_s32(v.r + 4u * (uint32_t)node + 4u);
-    const uint32_t colA = v.rows + (uint32_t)u0 * 16u;
-    const uint32_t colB = colA + (has1 ? g16 : 0u);
-    float r[4], z[4];
-    if (!pole) {
-      f2_t i0p, i1p, i2p, i3p;
-      lds2x64(colA + il * rb, i0p, i1p);
-      lds2x64(colB + il * rb, i2p, i3p);
-      Kahan2<COMP> k0, k1, k2, k3, q0, q1, q2, q3;
-      // weights of entry e: single pass, 8-byte (w.x, w.y) at pw + 8 e; fused,
-      // 16-byte (div, curl) records at pw + 16 e
-      const uint32_t pw = v.w + (FUSED ? 16u : 8u) * (uint32_t)p0;
-      auto weights = [&](uint32_t e, f2_t &wd, f2_t &wc) {
-        if (FUSED) lds2x64(pw + 16u * e, wd, wc);
-        else wd = lds_b64(pw + 8u * e);
-      };
-      const uint32_t pl = v.l + 4u * (uint32_t)p0;
-      // differences of neighbour entry e: units (c, c + G) minus the node's own
-      auto diffs = [&](uint32_t e, f2_t (&d)[4]) {
-        const uint32_t off = lds_u32(pl + 4u * e);
-        f2_t x0, x1, y0, y1;
-        lds2x64(colA + off, x0, x1);
-        lds2x64(colB + off, y0, y1);
-        d[0] = sub2(x0, i0p);
-        d[1] = sub2(x1, i1p);
-        d[2] = sub2(y0, i2p);
-        d[3] = sub2(y1, i3p);
-      };
-      auto triple = [&](uint32_t e) {
-        f2_t d0[4], d1[4], d2[4];
-        diffs(e, d0);
-        diffs(e + 1u, d1);
-        diffs(e + 2u, d2);
-        f2_t w0, w1, w2, x0 = 0ull, x1 = 0ull, x2 = 0ull;
-        weights(e, w0, x0);
-        weights(e + 1u, w1, x1);
-        weights(e + 2u, w2, x2);
-        k0.add_triple(w0, d0[0], w1, d1[0], w2, d2[0]);
-        k1.add_triple(w0, d0[1], w1, d1[1], w2, d2[1]);
-        k2.add_triple(w0, d0[2], w1, d1[2], w2, d2[2]);
-        k3.add_triple(w0, d0[3], w1, d1[3], w2, d2[3]);
-        if (FUSED) {
-          q0.add_triple(x0, d0[0], x1, d1[0], x2, d2[0]);
-          q1.add_triple(x0, d0[1], x1, d1[1], x2, d2[1]);
-          q2.add_triple(x0, d0[2], x1, d1[2], x2, d2[2]);
-          q3.add_triple(x0, d0[3], x1, d1[3], x2, d2[3]);
-        }
-      };
-      auto pair = [&](uint32_t e) {
-        f2_t d0[4], d1[4];
-        diffs(e, d0);
-        diffs(e + 1u, d1);
-        f2_t w0, w1, x0 = 0ull, x1 = 0ull;
-        weights(e, w0, x0);
-        weights(e + 1u, w1, x1);
-        k0.add_pair(w0, d0[0], w1, d1[0]);
-        k1.add_pair(w0, d0[1], w1, d1[1]);
-        k2.add_pair(w0, d0[2], w1, d1[2]);
-        k3.add_pair(w0, d0[3], w1, d1[3]);
-        if (FUSED) {
-          q0.add_pair(x0, d0[0], x1, d1[0]);
-          q1.add_pair(x0, d0[1], x1, d1[1]);
-          q2.add_pair(x0, d0[2], x1, d1[2]);
-          q3.add_pair(x0, d0[3], x1, d1[3]);
-        }
-      };
-      auto single = [&](uint32_t e) {
-        f2_t d0[4];
-        diffs(e, d0);
-        f2_t w0, x0 = 0ull;
-        weights(e, w0, x0);
-        k0.add_prod(w0, d0[0]);
-        k1.add_prod(w0, d0[1]);
-        k2.add_prod(w0, d0[2]);
-        k3.add_prod(w0, d0[3]);
-        if (FUSED) {
-          q0.add_prod(x0, d0[0]);
-          q1.add_prod(x0, d0[1]);
-          q2.add_prod(x0, d0[2]);
-          q3.add_prod(x0, d0[3]);
-        }
-      };
-      const int deg = p1 - p0;
-      if (deg == 6) {
-        triple(0);
-        triple(3);
-      } else {
-        int e = 0;
-        for (; e + 1 < deg; e += 2) pair((uint32_t)e);
-        if (e < deg) single((uint32_t)e);
-      }
-      const f2_t self[4] = {i0p, i1p, i2p, i3p};
-      f2_t sw_div, sw_curl = 0ull;
-      if (FUSED) lds2x64(v.s + 16u * (uint32_t)node, sw_div, sw_curl);
-      else sw_div = lds_b64(v.s + 8u * (uint32_t)node);
-      {
-        const f2_t sw = sw_div;
-        const f2_t vals[4] = {k0.value(), k1.value(), k2.value(), k3.value()};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          float x, y;
-          upk(fma2(sw, self[k], vals[k]), x, y);
-          r[k] = __fadd_rn(x, y);
-        }
-      }
-      if (FUSED) {
-        const f2_t sw = sw_curl;
-        const f2_t vals[4] = {q0.value(), q1.value(), q2.value(), q3.value()};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          float x, y;
-          upk(fma2(sw, self[k], vals[k]), x, y);
-          z[k] = __fadd_rn(x, y);
-        }
-      }
-    } else {
-      const float4 A = lds128(colA + il * rb);
-      const float4 B = lds128(colB + il * rb);
-      const float iu[4] = {A.x, A.z, B.x, B.z}, iv[4] = {A.y, A.w, B.y, B.w};
-      double sacc[4] = {0, 0, 0, 0}, zacc[4] = {0, 0, 0, 0};
-      for (int32_t p = p0; p < p1; ++p) {
-        const double2 w = __ldg(a.w64 + p);
-        const double2 x = FUSED ? __ldg(a.w64b + p) : w;
-        const uint32_t r0 = lds_u32(v.l + 4u * (uint32_t)p);
-        const float4 C = lds128(colA + r0);
-        const float4 D = lds128(colB + r0);
-        const float ju[4] = {C.x, C.z, D.x, D.z}, jv[4] = {C.y, C.w, D.y, D.w};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const double du = (double)ju[k] - (double)iu[k], dv = (double)jv[k] - (double)iv[k];
-          sacc[k] = fma(w.y, dv, fma(w.x, du, sacc[k]));
-          if (FUSED) zacc[k] = fma(x.y, dv, fma(x.x, du, zacc[k]));
-        }
-      }
-      const double2 sw = __ldg(a.s64 + node);
-      const double2 sx = FUSED ? __ldg(a.s64b + node) : sw;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        r[k] = (float)fma(sw.y, (double)iv[k], fma(sw.x, (double)iu[k], sacc[k]));
-        if (FUSED) z[k] = (float)fma(sx.y, (double)iv[k], fma(sx.x, (double)iu[k], zacc[k]));
-      }
-    }
-    // levels 2 u0, 2 u0 + 1 from r[0..1], levels 2 u1, 2 u1 + 1 from r[2..3]
-    auto put = [&](float *oo, const float (&o)[4]) {
-      const int la0 = 2 * u0, la1 = 2 * u1;
-      if (la0 + 1 < a.nlev) __stcs(reinterpret_cast<float2 *>(oo + la0), make_float2(o[0], o[1]));
-      else oo[la0] = o[0];
-      if (has1) {
-        if (la1 + 1 < a.nlev) __stcs(reinterpret_cast<float2 *>(oo + la1), make_float2(o[2], o[3]));
-        else oo[la1] = o[2];
-      }
-    };
-    put(a.out + (int64_t)node * a.out_stride, r);
-    if (FUSED) put(a.out2 + (int64_t)node * a.out_stride, z);
-  }
 }
 
 // grad.  Item c of a node takes the 4-level unit c of its scalar column;
@@ -517,7 +161,7 @@ __device__ __forceinline__ void divcurl_tile(const TiledArgs &a, int t, uint32_t
 template <bool COMP>
 __device__ __forceinline__ void grad_tile(const TiledArgs &a, int t, uint32_t stage, int part,
                                           int nparts) {
-  const TileView v(a, t, stage);
+  const TileView v = staged_view(a, stage);
   const uint32_t items = (uint32_t)(v.n1 - v.n0) * a.G;
   const uint32_t i0 = (uint32_t)(((uint64_t)items * part) / nparts);
   const uint32_t i1 = (uint32_t)(((uint64_t)items * (part + 1)) / nparts);
@@ -534,72 +178,57 @@ __device__ __forceinline__ void grad_tile(const TiledArgs &a, int t, uint32_t st
     if (!pole) {
       f2_t fi01, fi23;
       lds2x64(col + il * rb, fi01, fi23);
-      Kahan2<COMP> ax01, ax23, ay01, ay23;
+      GroupSum<COMP> ax01, ax23, ay01, ay23;
       const uint32_t pw = v.w + 8u * (uint32_t)p0, pl = v.l + 4u * (uint32_t)p0;
-      auto pair = [&](uint32_t q) {
-        const float2 w0 = lds64(pw + 8u * q), w1 = lds64(pw + 8u * q + 8u);
-        const uint32_t r0 = lds_u32(pl + 4u * q), r1 = lds_u32(pl + 4u * q + 4u);
-        f2_t f001, f023, f101, f123;
-        lds2x64(col + r0, f001, f023);
-        lds2x64(col + r1, f101, f123);
-        const f2_t a01 = sub2(f001, fi01), a23 = sub2(f023, fi23);
-        const f2_t b01 = sub2(f101, fi01), b23 = sub2(f123, fi23);
-        const f2_t wx0 = pk(w0.x, w0.x), wy0 = pk(w0.y, w0.y);
-        const f2_t wx1 = pk(w1.x, w1.x), wy1 = pk(w1.y, w1.y);
-        ax01.add_pair(wx0, a01, wx1, b01);
-        ax23.add_pair(wx0, a23, wx1, b23);
-        ay01.add_pair(wy0, a01, wy1, b01);
-        ay23.add_pair(wy0, a23, wy1, b23);
-      };
-      auto triple = [&](uint32_t q) {
-        const float2 w0 = lds64(pw + 8u * q), w1 = lds64(pw + 8u * q + 8u), w2 = lds64(pw + 8u * q + 16u);
-        const uint32_t r0 = lds_u32(pl + 4u * q), r1 = lds_u32(pl + 4u * q + 4u), r2 = lds_u32(pl + 4u * q + 8u);
-        f2_t f001, f023, f101, f123, f201, f223;
-        lds2x64(col + r0, f001, f023);
-        lds2x64(col + r1, f101, f123);
-        lds2x64(col + r2, f201, f223);
-        const f2_t a01 = sub2(f001, fi01), a23 = sub2(f023, fi23);
-        const f2_t b01 = sub2(f101, fi01), b23 = sub2(f123, fi23);
-        const f2_t e01 = sub2(f201, fi01), e23 = sub2(f223, fi23);
-        const f2_t wx0 = pk(w0.x, w0.x), wy0 = pk(w0.y, w0.y);
-        const f2_t wx1 = pk(w1.x, w1.x), wy1 = pk(w1.y, w1.y);
-        const f2_t wx2 = pk(w2.x, w2.x), wy2 = pk(w2.y, w2.y);
-        ax01.add_triple(wx0, a01, wx1, b01, wx2, e01);
-        ax23.add_triple(wx0, a23, wx1, b23, wx2, e23);
-        ay01.add_triple(wy0, a01, wy1, b01, wy2, e01);
-        ay23.add_triple(wy0, a23, wy1, b23, wy2, e23);
-      };
-      auto single = [&](uint32_t q) {
+      auto nbr = [&](uint32_t q, bool first) {
         const float2 w = lds64(pw + 8u * q);
-        f2_t f001, f023;
-        lds2x64(col + lds_u32(pl + 4u * q), f001, f023);
-        const f2_t d01 = sub2(f001, fi01), d23 = sub2(f023, fi23);
+        f2_t f01, f23;
+        lds2x64(col + (uint32_t)NB_IDX(lds_u32(pl + 4u * q), 0, a.col_area, a.status), f01, f23);
+        const f2_t a01 = sub2(f01, fi01), a23 = sub2(f23, fi23);
         const f2_t wx = pk(w.x, w.x), wy = pk(w.y, w.y);
-        ax01.add_prod(wx, d01);
-        ax23.add_prod(wx, d23);
-        ay01.add_prod(wy, d01);
-        ay23.add_prod(wy, d23);
+        if (first) {
+          ax01.start(wx, a01), ax23.start(wx, a23), ay01.start(wy, a01), ay23.start(wy, a23);
+        } else {
+          ax01.term(wx, a01), ax23.term(wx, a23), ay01.term(wy, a01), ay23.term(wy, a23);
+        }
+      };
+      auto close = [&](int which) {  // 0: first group, 1: second of two, 2: later
+        GroupSum<COMP> *acc[4] = {&ax01, &ax23, &ay01, &ay23};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (which == 0) acc[j]->close_first();
+          else if (which == 1) acc[j]->close_second();
+          else acc[j]->close();
+        }
       };
       const int deg = p1 - p0;
       if (deg == 6) {
-        triple(0);
-        triple(3);
+        nbr(0, true), nbr(1, false), nbr(2, false);
+        close(0);
+        nbr(3, true), nbr(4, false), nbr(5, false);
+        close(1);
       } else {
         int q = 0;
-        for (; q + 1 < deg; q += 2) pair((uint32_t)q);
-        if (q < deg) single((uint32_t)q);
+        for (; q + 1 < deg; q += 2) {
+          nbr((uint32_t)q, true), nbr((uint32_t)q + 1, false);
+          close(q == 0 ? 0 : 2);
+        }
+        if (q < deg) {
+          nbr((uint32_t)q, true);
+          close(q == 0 ? 0 : 2);
+        }
       }
-      upk(ax01.value(), gx[0], gx[1]);
-      upk(ax23.value(), gx[2], gx[3]);
-      upk(ay01.value(), gy[0], gy[1]);
-      upk(ay23.value(), gy[2], gy[3]);
+      upk(ax01.finish(), gx[0], gx[1]);
+      upk(ax23.finish(), gx[2], gx[3]);
+      upk(ay01.finish(), gy[0], gy[1]);
+      upk(ay23.finish(), gy[2], gy[3]);
     } else {
       const float4 fi = lds128(col + il * rb);
       double sx[4] = {0, 0, 0, 0}, sy[4] = {0, 0, 0, 0};
       const float fiv[4] = {fi.x, fi.y, fi.z, fi.w};
       for (int32_t p = p0; p < p1; ++p) {
         const double2 w = __ldg(a.w64 + p);
-        const float4 fj = lds128(col + lds_u32(v.l + 4u * (uint32_t)p));
+        const float4 fj = lds128(col + (uint32_t)NB_IDX(lds_u32(v.l + 4u * (uint32_t)p), 0, a.col_area, a.status));
         const float fjv[4] = {fj.x, fj.y, fj.z, fj.w};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -629,9 +258,6 @@ __device__ __forceinline__ void grad_tile(const TiledArgs &a, int t, uint32_t st
   }
 }
 
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
 
 // Consumer warps per operator.  Fewer warps than the SM could hold: timed on
 // B300 at O1280 x 137 levels, 11-12 consumer warps beat 16 by 1-7 % (more
@@ -642,9 +268,18 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // `ahead` steps further along the CTA's walk, so that its stage copy reads
 // L2 instead of HBM (timed: 1-3 % per launch; 1 step for the single
 // operators, 2 for the fused pass).
+#ifndef NB_GRAD_WARPS
+#define NB_GRAD_WARPS 12
+#endif
+#ifndef NB_DIV_WARPS
+#define NB_DIV_WARPS 11
+#endif
+#ifndef NB_DIVCURL_WARPS
+#define NB_DIVCURL_WARPS 11
+#endif
 template <int OP>
 struct StagedShape {
-  static constexpr int warps = OP == 0 ? 12 : 11;
+  static constexpr int warps = OP == 0 ? NB_GRAD_WARPS : OP == 1 ? NB_DIV_WARPS : NB_DIVCURL_WARPS;
   static constexpr int threads = 32 * (warps + 1);
   static constexpr int ahead = OP == 2 ? 2 : 1;
 };
@@ -663,7 +298,7 @@ __device__ __forceinline__ int tile_at(const TiledArgs &a, int i) {
 // of this CTA's walk into it ("full" barrier, transaction count).  Each of
 // the W consumer warps waits for "full", computes its 1/W share of the
 // tile's items and releases the stage; no block-wide barrier is used.
-template <int OP, bool COMP>
+template <int OP, bool COMP, int KU>
 __global__ void __launch_bounds__(StagedShape<OP>::threads, 1)
     staged_f32(const TiledArgs a, const __grid_constant__ CUtensorMap map) {
   constexpr int W = StagedShape<OP>::warps;
@@ -721,8 +356,8 @@ __global__ void __launch_bounds__(StagedShape<OP>::threads, 1)
     }
     const uint32_t rows = stage0 + (uint32_t)s * a.stage_bytes;
     if (OP == 0) grad_tile<COMP>(a, t, rows, warp, W);
-    else if (OP == 1) divcurl_tile<COMP, false>(a, t, rows, warp, W);
-    else divcurl_tile<COMP, true>(a, t, rows, warp, W);
+    else if (OP == 1) divcurl_tile<COMP, false, KU>(a, staged_view(a, rows), t >= a.ntiles_main, a.row_bytes, warp, W);
+    else divcurl_tile<COMP, true, KU>(a, staged_view(a, rows), t >= a.ntiles_main, a.row_bytes, warp, W);
     __syncwarp();
     if (lane == 0) mbar_arrive(empty0 + 8 * s);
   }
@@ -736,6 +371,22 @@ static int plan_upload(TilePlan *tp, nb_method *m) {
   std::vector<uint32_t> loff;
   build_tile_plan_bytes(mesh, tp->area, tp->row_bytes, tp->copy_bytes, tp->nmax, tp->ecap, tp->pole_cap, node0, hptr,
                         halo, loff, tp->max_halo, tp->max_entries, tp->ntiles_main);
+  {
+    // every staged offset must decode to the column of its neighbour
+    const int64_t rb = tp->row_bytes, cb = tp->copy_bytes, gp = (4 * cb + 127) / 128 * 128;
+    auto slot = [&](int64_t p, int, int64_t n) -> int64_t {
+      const int64_t off = loff[p], hb = (n * rb + 127) / 128 * 128;
+      if (off < n * rb) return off % rb == 0 ? off / rb : -1;
+      if (off < hb) return -1;
+      const int64_t r = (off - hb) % gp;
+      return (r % cb == 0 && r / cb < 4) ? n + 4 * ((off - hb) / gp) + r / cb : -1;
+    };
+    std::string why;
+    if (!check_tile_plan(mesh, (int)node0.size() - 1, node0.data(), hptr.data(), halo.data(), slot, why)) {
+      set_error("staged kernel: invalid tile plan (" + why + ")");
+      return NB_EINVAL;
+    }
+  }
   loff.resize(loff.size() + 8, 0);  // slack for 16-byte bounding copies
   if (halo.empty()) halo.push_back(0);
   tp->ntiles = (int)node0.size() - 1;
@@ -783,11 +434,7 @@ static TilePlan *get_plan(nb_method *m, int64_t area, int64_t row_bytes, int64_t
 }
 
 // cuTensorMapEncodeTiled from the driver, looked up once.
-typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
-                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
-                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-static EncodeTiledFn encode_fn() {
+EncodeTiledFn encode_fn() {
   static std::once_flag once;
   static EncodeTiledFn fn = nullptr;
   std::call_once(once, [] {
@@ -806,24 +453,24 @@ static EncodeTiledFn encode_fn() {
 // x / d is below x / 2^k <= 1 / d for x < 2^32, so the floor is exact; for
 // x < 2^24 (at most 1024 nodes x 16384 groups per tile) and m < 2^33 the
 // product fits in 64 bits.
-static void magic_div(uint32_t d, uint64_t &magic, uint32_t &shift) {
+void magic_div(uint32_t d, uint64_t &magic, uint32_t &shift) {
   uint32_t s = 0;
   while ((1u << s) < d) ++s;
   shift = 32 + s;
   magic = ((1ull << shift) + d - 1) / d;
 }
 
-template <int OP, bool COMP>
+template <int OP, bool COMP, int KU>
 static int launch_staged_t(const TiledArgs &a, const CUtensorMap &map, int grid, size_t smem,
                            cudaStream_t st) {
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [&] {
-    attr_err = cudaFuncSetAttribute(staged_f32<OP, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    attr_err = cudaFuncSetAttribute(staged_f32<OP, COMP, KU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     227 * 1024);
   });
   NB_CUDA(attr_err);
-  staged_f32<OP, COMP><<<grid, StagedShape<OP>::threads, smem, st>>>(a, map);
+  staged_f32<OP, COMP, KU><<<grid, StagedShape<OP>::threads, smem, st>>>(a, map);
   count_launch(1);
   NB_CUDA(cudaGetLastError());
   return NB_OK;
@@ -831,9 +478,54 @@ static int launch_staged_t(const TiledArgs &a, const CUtensorMap &map, int grid,
 
 static int g_sm_count = 0;
 
+int sm_count(int *out) {
+  if (g_sm_count == 0) {
+    int dev = 0;
+    NB_CUDA(cudaGetDevice(&dev));
+    NB_CUDA(cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev));
+  }
+  *out = g_sm_count;
+  return NB_OK;
+}
+
+// Item shape of the div / curl consumers for a column of `units` 16-byte
+// units: KU units per item, G items per node.  units_req 2 or 3 fixes KU,
+// align_req 1 (0) asks for G rounded up to a multiple of 8 (not rounded).
+// Left to the library (0 / -1): the fused pass keeps KU = 2 with G not
+// rounded (timed on B300 at O1280 x 137: 3.88 ms against 3.92 ms with KU = 3
+// and G = 24; its two sets of sums need ~30 more registers a thread at
+// KU = 3); the single operators take the shape with the fewest shared-memory
+// wavefronts per node, (G / 32) (22 + 28 KU f): per warp-wide item ~22 for
+// its row pointers, offsets and weights, 28 per unit for its seven 16-byte
+// column loads, and f = 1.25 when quarter-warps can span two nodes (bank
+// conflict replays), else 1 (timed: 2.81 ms with KU = 3, G = 24, against
+// 2.97 ms with KU = 2, G = 35).
+void item_shape(int units_req, int align_req, int units, bool fused, int &KU, int &G) {
+  if (fused && units_req == 0 && align_req < 0) {
+    KU = 2;
+    G = (units + 1) / 2;
+    return;
+  }
+  double best = 1e30;
+  for (int ku = 2; ku <= 3; ++ku) {
+    if (units_req && units_req != ku) continue;
+    for (int al = 0; al <= 1; ++al) {
+      if (align_req >= 0 && align_req != al) continue;
+      const int g = al ? ((units + ku - 1) / ku + 7) / 8 * 8 : (units + ku - 1) / ku;
+      const double f = (g % 8 == 0) ? 1.0 : 1.25;
+      const double cost = g * (22.0 + 28.0 * ku * f);
+      if (cost < best) {
+        best = cost;
+        KU = ku;
+        G = g;
+      }
+    }
+  }
+}
+
 // Device address of the status word on the current device (looked up once
 // per device).
-static int status_word(int **out) {
+int status_word(int **out) {
   static std::mutex mu;
   static int *addr[64] = {};
   int dev = 0;
@@ -864,10 +556,13 @@ int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, 
   // short columns leave most staged items idle: the direct kernels do better
   if (!aligned || in->nlev < 16) return NB_OK;
   const uint32_t row_bytes = (uint32_t)(in->node_stride * 4);
-  const int G = (in->nlev + 3) / 4;
   const int nvar = in->nvar;
-  // each 4-level group must lie inside the staged column
-  if ((uint64_t)G * 16u * nvar > row_bytes) return NB_OK;
+  // items per node: grad, one 4-level unit per item; div / curl, KU 2-level
+  // units per item (item_shape)
+  int KU = 1, G = (in->nlev + 3) / 4;
+  if (nvar == 2) item_shape(m->item_units, m->item_align, (in->nlev + 1) / 2, fused, KU, G);
+  // each 16-byte unit must lie inside the staged column
+  if ((uint64_t)(nvar == 2 ? (in->nlev + 1) / 2 : G) * 16u > row_bytes) return NB_OK;
   const uint32_t copy_bytes = (uint32_t)(((int64_t)in->nlev * nvar * 4 + 15) / 16 * 16);
   // halo columns are gathered as tensor rows of 4-byte (scalar) or 8-byte
   // (vector) elements; a box row holds at most 256 elements
@@ -957,6 +652,8 @@ int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, 
   a.status = nullptr;
   if (const int rc = status_word(&a.status)) return rc;
   a.timeout_ns = m->wait_limit_ns >= 0 ? (uint64_t)m->wait_limit_ns : kDefaultWaitNs;
+  a.nnodes = (int32_t)in->nnodes;
+  a.col_area = area;
   const size_t smem = (size_t)nstages * a.stage_bytes + 16 * (size_t)nstages;
   if (smem > 227 * 1024) {
     set_error("staged kernel: nstages * stage size exceeds 227 KB of shared memory");
@@ -965,10 +662,15 @@ int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, 
   const int grid = std::min(tp->ntiles, g_sm_count);
   *handled = true;
   const bool comp = comp_mode < 0 ? m->compensated != 0 : comp_mode != 0;
-  if (g) return comp ? launch_staged_t<0, true>(a, map, grid, smem, st) : launch_staged_t<0, false>(a, map, grid, smem, st);
-  if (fused)
-    return comp ? launch_staged_t<2, true>(a, map, grid, smem, st) : launch_staged_t<2, false>(a, map, grid, smem, st);
-  return comp ? launch_staged_t<1, true>(a, map, grid, smem, st) : launch_staged_t<1, false>(a, map, grid, smem, st);
+  if (g) return comp ? launch_staged_t<0, true, 1>(a, map, grid, smem, st) : launch_staged_t<0, false, 1>(a, map, grid, smem, st);
+  if (fused) {
+    if (KU == 3)
+      return comp ? launch_staged_t<2, true, 3>(a, map, grid, smem, st) : launch_staged_t<2, false, 3>(a, map, grid, smem, st);
+    return comp ? launch_staged_t<2, true, 2>(a, map, grid, smem, st) : launch_staged_t<2, false, 2>(a, map, grid, smem, st);
+  }
+  if (KU == 3)
+    return comp ? launch_staged_t<1, true, 3>(a, map, grid, smem, st) : launch_staged_t<1, false, 3>(a, map, grid, smem, st);
+  return comp ? launch_staged_t<1, true, 2>(a, map, grid, smem, st) : launch_staged_t<1, false, 2>(a, map, grid, smem, st);
 }
 
 int device_status(int clear, int *code) {

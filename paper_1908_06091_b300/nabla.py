@@ -24,13 +24,16 @@ import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "libnabla_b300.so")
+# NB_LIBRARY=debug loads the bounds-checked build (build.py, variant "debug")
+LIB_PATH = os.path.join(_HERE, "_lib", "libnabla_b300_debug.so" if os.environ.get("NB_LIBRARY") == "debug"
+                        else "libnabla_b300.so")
 
 NB_OK, NB_EINVAL, NB_ESHAPE, NB_EDTYPE, NB_EOOM, NB_ECUDA, NB_ETIMEOUT, NB_EBUDGET = range(8)
 NB_F32, NB_F64 = 0, 1
 OP_GRAD, OP_DIV, OP_CURL, OP_LAP = 0, 1, 2, 3
 OPS = {"grad": OP_GRAD, "div": OP_DIV, "curl": OP_CURL, "lap": OP_LAP}
 KERNEL_AUTO, KERNEL_DIRECT, KERNEL_TILED, KERNEL_EDGE = 0, 1, 2, 3
+LAP_TWO_PASS, LAP_FUSED = 0, 1
 EARTH_RADIUS_M = 6.37122e6
 
 
@@ -98,6 +101,8 @@ SIGNATURES = {
     "nb_mesh_triangles": [_P, _P],
     "nb_mesh_edges": [_P, _P],
     "nb_mesh_cap_begin": [_P, _I64P],
+    "nb_mesh_lap_plan": [_P, _I] + [ctypes.POINTER(ctypes.c_int32)] * 4,
+    "nb_check_tile_plan": [_P, ctypes.c_int32, _P, _P, _P, _P],
     "nb_mesh_csr": [_P, _P, _P],
     "nb_mesh_tile_plan": [_P, _I, _I, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                           _I64P, _P, _P, _P, _P],
@@ -109,6 +114,8 @@ SIGNATURES = {
     "nb_method_set_compensated": [_P, _I],
     "nb_method_set_staging": [_P, _I, _I],
     "nb_method_set_wait_limit": [_P, ctypes.c_int64],
+    "nb_method_set_item_shape": [_P, _I, _I],
+    "nb_method_set_laplacian_route": [_P, _I],
     "nb_fs_nodecolumns": [_P, _I, _I, ctypes.POINTER(_P)],
     "nb_fs_release": [_P],
     "nb_fs_level_stride": [_P, _I64P],
@@ -127,6 +134,7 @@ SIGNATURES = {
     "nb_nabla_apply_host": [_P, _I, _P, _P, _FP, _FP, _FP, _P],
     "nb_set_allocator": [ctypes.POINTER(nb_allocator)],
     "nb_launch_count": [_I64P],
+    "nb_probe_fp64_rate": [ctypes.c_int64, _P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
     "nb_device_status": [_I, ctypes.POINTER(ctypes.c_int32)],
     "nb_batch_create": [_P, _I, ctypes.POINTER(_P)],
     "nb_batch_release": [_P],
@@ -179,6 +187,14 @@ def launch_count() -> int:
     c = ctypes.c_int64()
     check(lib().nb_launch_count(ctypes.byref(c)))
     return c.value
+
+
+def probe_fp64_rate(iters: int = 40000, stream=None):
+    """(TFLOP/s, ms) of the device's FP64 FMA-chain probe (nb_probe_fp64_rate)."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    check(lib().nb_probe_fp64_rate(int(iters), ctypes.c_void_p(_stream(stream)), ctypes.byref(tf),
+                                   ctypes.byref(ms)))
+    return tf.value, ms.value
 
 
 def device_status(clear: bool = False) -> int:
@@ -342,6 +358,13 @@ class Mesh(_Handle):
         check(lib().nb_mesh_csr(self._h, rp.ctypes.data, nb.ctypes.data))
         return rp, nb
 
+    def lap_plan(self, nlev: int):
+        """(tiles, main tiles, max g-nodes, fits) of the single-pass
+        Laplacian's plan for FP32 columns of nlev levels (host only)."""
+        v = [ctypes.c_int32() for _ in range(4)]
+        check(lib().nb_mesh_lap_plan(self._h, int(nlev), *[ctypes.byref(x) for x in v]))
+        return tuple(x.value for x in v)
+
     def tile_plan(self, rcap: int, nmax: int = 256):
         """(node0, halo_ptr, halo, lnbr, ntiles_main) of the staged kernels' plan."""
         nt, nm, nh = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
@@ -355,6 +378,16 @@ class Mesh(_Handle):
                                       ctypes.byref(nh), node0.ctypes.data, hptr.ctypes.data,
                                       halo.ctypes.data, lnbr.ctypes.data))
         return node0, hptr, halo[:nh.value], lnbr, nm.value
+
+    def check_tile_plan(self, node0, halo_ptr, halo, lnbr) -> None:
+        """Raise NablaError unless the plan (format of tile_plan) is valid
+        (nb_check_tile_plan)."""
+        n0 = np.ascontiguousarray(node0, dtype=np.int32)
+        hp = np.ascontiguousarray(halo_ptr, dtype=np.int32)
+        h = np.ascontiguousarray(halo if len(halo) else np.zeros(1), dtype=np.int32)
+        ln = np.ascontiguousarray(lnbr, dtype=np.uint16)
+        check(lib().nb_check_tile_plan(self._h, len(n0) - 1, n0.ctypes.data, hp.ctypes.data, h.ctypes.data,
+                                       ln.ctypes.data))
 
 
 class Method(_Handle):
@@ -385,6 +418,16 @@ class Method(_Handle):
 
     def set_compensated(self, on: bool) -> None:
         check(lib().nb_method_set_compensated(self._h, 1 if on else 0))
+
+    def set_laplacian_route(self, route: int) -> None:
+        """LAP_TWO_PASS (default) or LAP_FUSED (single-pass Laplacian for
+        the FP32 staged path); see nb_method_set_laplacian_route."""
+        check(lib().nb_method_set_laplacian_route(self._h, int(route)))
+
+    def set_item_shape(self, units: int = 0, aligned: int = -1) -> None:
+        """Item shape of the staged div / curl kernels (0 / -1: chosen by
+        the library); see nb_method_set_item_shape."""
+        check(lib().nb_method_set_item_shape(self._h, int(units), int(aligned)))
 
     def set_wait_limit(self, limit_ns: int = -1) -> None:
         """Limit of the staged kernels' pipeline waits in ns (-1 = default

@@ -212,3 +212,44 @@ def test_last_error_is_per_thread():
     assert seen["grid"][0] == nabla.NB_EINVAL and seen["mesh"][0] == nabla.NB_EINVAL
     assert seen["grid"][1] and seen["mesh"][1]
     assert seen["grid"][1] != seen["mesh"][1], seen
+
+
+@pytest.mark.parametrize("grid", ["O32", "O96", "F16", "PL"])
+def test_fused_laplacian_plans_fit_their_layout(grid):
+    """The single-pass Laplacian's planner grows tiles with incrementally
+    counted rings; the library then recounts every tile's rings exactly and
+    refuses a plan in which one does not fit the kernel's shared memory.
+    Every plan it builds must pass that check, with pole-row tiles last."""
+    pl = [20, 27, 33, 40, 44, 47, 47, 44, 40, 33, 27, 20]
+    g = {"O32": lambda: nabla.Grid(32), "O96": lambda: nabla.Grid(96), "F16": lambda: nabla.Grid.regular(16),
+         "PL": lambda: nabla.Grid.reduced(pl)}[grid]()
+    m = nabla.Mesh(g, 1)
+    for nlev in (16, 37, 91, 137, 300):
+        ntiles, nmain, max_gnodes, fits = m.lap_plan(nlev)
+        assert fits == 1, (grid, nlev)
+        assert 0 < nmain < ntiles <= m.V
+        assert max_gnodes >= 2
+    with pytest.raises(nabla.NablaError):
+        m.lap_plan(8)
+
+
+def test_corrupted_tile_plans_are_refused_on_the_host():
+    """The plan check the library runs before uploading a plan: a valid plan
+    passes; a halo node out of range, a neighbour mapped to the wrong staged
+    row, and tiles out of order are each refused with NB_EINVAL (no GPU)."""
+    m = nabla.Mesh(nabla.Grid(24), 1)
+    node0, hptr, halo, lnbr, _ = m.tile_plan(rcap=160, nmax=64)
+    m.check_tile_plan(node0, hptr, halo, lnbr)
+    bad_halo = halo.copy()
+    bad_halo[len(bad_halo) // 2] = m.V + 5
+    bad_rows = lnbr.copy()
+    rp, _nbr = m.csr()
+    p = int(rp[len(rp) // 2])
+    bad_rows[p] = (int(bad_rows[p]) + 1) % 60000
+    bad_order = node0.copy()
+    bad_order[3], bad_order[4] = bad_order[4], bad_order[3]
+    for args, what in (((node0, hptr, bad_halo, lnbr), "halo"), ((node0, hptr, halo, bad_rows), "staged"),
+                       ((bad_order, hptr, halo, lnbr), "order")):
+        with pytest.raises(nabla.NablaError) as ei:
+            m.check_tile_plan(*args)
+        assert ei.value.code == nabla.NB_EINVAL, what
