@@ -151,14 +151,14 @@ class Clocks:
 def measured_traffic(op, V, L):
     """DRAM bytes of one launch of `op` from the ncu capture recorded in
     profiles/dram_traffic.json (per node-level, scaled to V x L), or None when
-    the staged kernel source has changed since that capture."""
+    the staged kernels' sources have changed since that capture."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as fh:
             d = json.load(fh)
-        with open(os.path.join(ROOT, d["kernel_source"]), "rb") as fh:
-            if hashlib.sha256(fh.read()).hexdigest() != d["kernel_source_sha256"]:
-                return None
+        blob = b"".join(open(os.path.join(ROOT, f), "rb").read() for f in d["kernel_sources"])
+        if hashlib.sha256(blob).hexdigest() != d["kernel_sources_sha256"]:
+            return None
         return int(d["dram_bytes_per_node_level"][op] * V * L)
     except Exception:
         return None

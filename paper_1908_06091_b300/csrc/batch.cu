@@ -584,9 +584,36 @@ static int staged_or_direct(nb_method *m, int op, const nb_field &in, const nb_f
   return launch_direct(m, op, &in, &out, st);
 }
 
-// Launch the phases directly on a stream (used for capture and for tuning).
-static int batch_launch(nb_batch *bt, cudaStream_t st) {
+// Branches of the batch's launch graph: the staged-route items are spread
+// over the main stream and kBatchBranches - 1 side streams, forked from and
+// joined back to the main stream with events, so that a small item's launch
+// (fewer tiles than SMs) runs beside others and each launch's ramp and tail
+// overlap its neighbours'.  No CTA of these kernels waits on another, so
+// they complete in any overlap.
+constexpr int kBatchBranches = 4;
+
+// One staged-route item (both passes of a Laplacian) on stream st.
+static int staged_item(nb_batch *bt, size_t k, cudaStream_t st) {
+  const auto &s = bt->src[k];
+  if (s.op == NB_OP_LAP) {
+    nb_field tmp = s.in;
+    tmp.data = bt->scratch[k];
+    tmp.nvar = 2;
+    tmp.node_stride = 2 * (int64_t)((s.in.nlev + 3) / 4) * 4;
+    tmp.lev_stride = 2;
+    int rc = staged_or_direct(s.method, NB_OP_GRAD, s.in, tmp, bt->comp, st);
+    if (rc == NB_OK) rc = staged_or_direct(s.method, NB_OP_DIV, tmp, s.out, bt->comp, st);
+    return rc;
+  }
+  return staged_or_direct(s.method, s.op, s.in, s.out, bt->comp, st);
+}
+
+// Launch the phases on stream st and its side streams (used for capture and
+// for tuning): the persistent phases on st, the staged-route items spread
+// over st and the side streams, largest first onto the least-loaded branch.
+static int batch_launch(nb_batch *bt, cudaStream_t st, cudaStream_t *side = nullptr, int nside = 0) {
   NB_CUDA(cudaMemsetAsync(bt->d_counter, 0, 2 * sizeof(unsigned long long), st));
+  double load[kBatchBranches] = {};
   for (int p = 0; p < 2; ++p) {
     if (bt->nunits[p] == 0) continue;
     batch_kernel<<<bt->grid, kBatchThreads, 0, st>>>(bt->d_items[p], bt->nitems[p], bt->nunits[p],
@@ -594,24 +621,50 @@ static int batch_launch(nb_batch *bt, cudaStream_t st) {
     count_launch(1);
     NB_CUDA(cudaGetLastError());
   }
-  for (size_t k = 0; k < bt->src.size(); ++k) {
-    if (!staged_route(bt->shape[k])) continue;
+  for (size_t k = 0; k < bt->src.size(); ++k)
+    if (!staged_route(bt->shape[k])) load[0] += (double)bt->src[k].in.nnodes * bt->src[k].in.nlev;
+  std::vector<size_t> order;
+  for (size_t k = 0; k < bt->src.size(); ++k)
+    if (staged_route(bt->shape[k])) order.push_back(k);
+  auto work = [&](size_t k) {
     const auto &s = bt->src[k];
-    int rc;
-    if (s.op == NB_OP_LAP) {
-      nb_field tmp = s.in;
-      tmp.data = bt->scratch[k];
-      tmp.nvar = 2;
-      tmp.node_stride = 2 * (int64_t)((s.in.nlev + 3) / 4) * 4;
-      tmp.lev_stride = 2;
-      rc = staged_or_direct(s.method, NB_OP_GRAD, s.in, tmp, bt->comp, st);
-      if (rc == NB_OK) rc = staged_or_direct(s.method, NB_OP_DIV, tmp, s.out, bt->comp, st);
-    } else {
-      rc = staged_or_direct(s.method, s.op, s.in, s.out, bt->comp, st);
-    }
-    if (rc != NB_OK) return rc;
+    return (double)s.in.nnodes * s.in.nlev * (s.op == NB_OP_LAP ? 2.0 : 1.0);
+  };
+  std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return work(x) > work(y); });
+  const int nb = 1 + std::min(nside, kBatchBranches - 1);
+  cudaStream_t lanes[kBatchBranches] = {st};
+  for (int b = 1; b < nb; ++b) lanes[b] = side[b - 1];
+  cudaEvent_t ev[2 * kBatchBranches] = {};
+  int nev = 0;
+  int rc = NB_OK;
+  if (nb > 1) {  // fork: the side streams follow st
+    cudaEvent_t fork = nullptr;
+    NB_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    ev[nev++] = fork;
+    if (cudaEventRecord(fork, st) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "batch fork");
+    for (int b = 1; b < nb && rc == NB_OK; ++b)
+      if (cudaStreamWaitEvent(lanes[b], fork, 0) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "batch fork");
   }
-  return NB_OK;
+  for (size_t k : order) {
+    if (rc != NB_OK) break;
+    int b = 0;
+    for (int c = 1; c < nb; ++c)
+      if (load[c] < load[b]) b = c;
+    load[b] += work(k);
+    rc = staged_item(bt, k, lanes[b]);
+  }
+  for (int b = 1; b < nb; ++b) {  // join: st waits for every side stream
+    cudaEvent_t join = nullptr;
+    if (cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess) {
+      if (rc == NB_OK) rc = cuda_fail(cudaGetLastError(), "batch join");
+      continue;
+    }
+    ev[nev++] = join;
+    if (cudaEventRecord(join, lanes[b]) != cudaSuccess || cudaStreamWaitEvent(st, join, 0) != cudaSuccess)
+      if (rc == NB_OK) rc = cuda_fail(cudaGetLastError(), "batch join");
+  }
+  for (int e = 0; e < nev; ++e) cudaEventDestroy(ev[e]);
+  return rc;
 }
 
 static void drop_graph(nb_batch *bt) {
@@ -623,25 +676,32 @@ static void drop_graph(nb_batch *bt) {
 
 static int batch_capture(nb_batch *bt) {
   drop_graph(bt);
-  cudaStream_t cs;
+  cudaStream_t cs, side[kBatchBranches - 1] = {};
   NB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  int nside = 0;
+  for (; nside < kBatchBranches - 1; ++nside)
+    if (cudaStreamCreateWithFlags(&side[nside], cudaStreamNonBlocking) != cudaSuccess) break;
+  auto destroy = [&] {
+    cudaStreamDestroy(cs);
+    for (int b = 0; b < nside; ++b) cudaStreamDestroy(side[b]);
+  };
   // one eager run first: staged launches build their tile plans (host and
   // device allocations) on first use, which a capture must not contain
-  int rc = batch_launch(bt, cs);
+  int rc = batch_launch(bt, cs, side, nside);
   if (rc == NB_OK && cudaStreamSynchronize(cs) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "batch warm-up");
   if (rc != NB_OK) {
-    cudaStreamDestroy(cs);
+    destroy();
     return rc;
   }
   if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-    cudaStreamDestroy(cs);
+    destroy();
     set_error("nb_batch: stream capture failed to start");
     return NB_ECUDA;
   }
-  rc = batch_launch(bt, cs);
+  rc = batch_launch(bt, cs, side, nside);
   cudaGraph_t g = nullptr;
   const cudaError_t e = cudaStreamEndCapture(cs, &g);
-  cudaStreamDestroy(cs);
+  destroy();
   if (rc != NB_OK) {
     if (g) cudaGraphDestroy(g);
     return rc;

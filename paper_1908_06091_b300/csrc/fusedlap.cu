@@ -408,6 +408,19 @@ __global__ void lap_records_kernel(int64_t n, const int32_t *__restrict__ p, con
   rec[i] = make_float4(w.x, w.y, __uint_as_float(foff[i]), __int_as_float(q));
 }
 
+// Structural check of a single-pass Laplacian plan before it is used: the
+// tiles, their rings and the own nodes' g-buffer offsets (each must decode to
+// the g slot of its neighbour).
+static bool check_lap_plan(const nb_mesh *mesh, const LapLayout &L, const LapPlanHost &h, std::string &why) {
+  const int64_t gp = L.g_pitch;
+  auto slot = [&](int64_t p, int t, int64_t n) -> int64_t {
+    const int64_t off = h.goff[p];
+    return (off % gp == 0 && off / gp < n + h.r1_count[t]) ? off / gp : -1;
+  };
+  return check_tile_plan(mesh, (int)h.node0.size() - 1, h.node0.data(), h.halo_ptr.data(), h.halo.data(), slot,
+                         why);
+}
+
 static int lap_plan_upload(LapPlan *lp, nb_method *m, const LapLayout &L, int nmax, int pole_cap) {
   LapPlanHost h;
   build_lap_plan(m->mesh, L, nmax, pole_cap, h);
@@ -416,14 +429,8 @@ static int lap_plan_upload(LapPlan *lp, nb_method *m, const LapLayout &L, int nm
     return NB_EINVAL;
   }
   {
-    // own nodes' g-buffer offsets must decode to their neighbours' g slots
-    const int64_t gp = L.g_pitch;
-    auto slot = [&](int64_t p, int t, int64_t n) -> int64_t {
-      const int64_t off = h.goff[p];
-      return (off % gp == 0 && off / gp < n + h.r1_count[t]) ? off / gp : -1;
-    };
     std::string why;
-    if (!check_tile_plan(m->mesh, lp->ntiles, h.node0.data(), h.halo_ptr.data(), h.halo.data(), slot, why)) {
+    if (!check_lap_plan(m->mesh, L, h, why)) {
       set_error("fused Laplacian: invalid tile plan (" + why + ")");
       return NB_EINVAL;
     }
@@ -625,7 +632,8 @@ int lap_plan_info(const nb_mesh *mesh, int nlev, int32_t *ntiles, int32_t *ntile
   *ntiles = (int32_t)h.node0.size() - 1;
   *ntiles_main = h.ntiles_main;
   *max_gnodes = h.max_gnodes;
-  *fits = h.fits ? 1 : 0;
+  std::string why;
+  *fits = (h.fits && check_lap_plan(mesh, L, h, why)) ? 1 : 0;
   return NB_OK;
 }
 

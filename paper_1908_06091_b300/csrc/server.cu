@@ -78,7 +78,7 @@ template <class T>
 __global__ void __launch_bounds__(kSynthThreads) synth_fields_kernel(const float *__restrict__ basis, int nvar,
                                                                      int64_t V, int nlev, int64_t stride,
                                                                      const float *__restrict__ wts, T *out) {
-  extern __shared__ float sm[];
+  extern __shared__ __align__(16) float sm[];
   const int lb = (int)(stride / nvar);           // padded levels of the column block
   float *wT = sm;                                // [8][lb]
   float *bs = sm + 8 * lb;                       // [kSynthNodes][8][nvar]
@@ -99,16 +99,32 @@ __global__ void __launch_bounds__(kSynthThreads) synth_fields_kernel(const float
 #pragma unroll
     for (int b = 0; b < 8; ++b) w[b] = wT[b * lb + k];
     for (int il = warp; il < nn; il += nwarps) {
-      const float *bi = bs + il * 8 * nvar;
+      // the node's basis values: 16-byte broadcast loads (bs and each node's
+      // 8 x nvar floats start on 32 bytes)
+      const float4 *bi = reinterpret_cast<const float4 *>(bs + il * 8 * nvar);
       float acc0 = 0.f, acc1 = 0.f;
+      if (nvar == 1) {
+        const float4 p = bi[0], q = bi[1];
+        const float v[8] = {p.x, p.y, p.z, p.w, q.x, q.y, q.z, q.w};
 #pragma unroll
-      for (int b = 0; b < 8; ++b) {
-        acc0 = __fmaf_rn(w[b], bi[b * nvar], acc0);
-        if (nvar == 2) acc1 = __fmaf_rn(w[b], bi[b * 2 + 1], acc1);
+        for (int b = 0; b < 8; ++b) acc0 = __fmaf_rn(w[b], v[b], acc0);
+      } else {
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          const float4 p = bi[h];  // (u, v) of bases 2h and 2h + 1
+          acc0 = __fmaf_rn(w[2 * h], p.x, acc0);
+          acc1 = __fmaf_rn(w[2 * h], p.y, acc1);
+          acc0 = __fmaf_rn(w[2 * h + 1], p.z, acc0);
+          acc1 = __fmaf_rn(w[2 * h + 1], p.w, acc1);
+        }
       }
       T *o = out + (n0 + il) * stride + (int64_t)k * nvar;
-      o[0] = (T)acc0;
-      if (nvar == 2) o[1] = (T)acc1;
+      if (nvar == 2) {
+        if constexpr (sizeof(T) == 4) *reinterpret_cast<float2 *>(o) = make_float2(acc0, acc1);
+        else *reinterpret_cast<double2 *>(o) = make_double2((double)acc0, (double)acc1);
+      } else {
+        o[0] = (T)acc0;
+      }
     }
   }
 }
