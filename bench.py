@@ -57,6 +57,9 @@ def parse():
     p.add_argument("--batch-fields", type=int, default=64, help="0 skips the batched section")
     p.add_argument("--serve-seconds", type=float, default=2.0, help="0 skips the serving section")
     p.add_argument("--serve-rate", type=float, default=2000.0)
+    p.add_argument("--no-serve-baseline", action="store_true", help="skip the sequential FP64 serving baseline")
+    p.add_argument("--serve-streams", type=int, default=8)
+    p.add_argument("--serve-inflight", type=int, default=32)
     p.add_argument("--stages", type=int, default=0)
     p.add_argument("--stage-kb", type=int, default=0)
     return p.parse_args()
@@ -607,14 +610,15 @@ def bench_served(a, nabla, synth):
                 "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
                 "mean_ms": round(float(lat.mean()), 3), "peak_budget_GB": round(st["peak_used"] / 1e9, 2)}
 
-    ours = run(nabla.NB_F32, 8, 32)
+    ns, nf = a.serve_streams, a.serve_inflight
+    ours = run(nabla.NB_F32, ns, nf)
     # the same trace at a fifth of the rate (first fifth of the requests):
     # latency below saturation
-    light = run(nabla.NB_F32, 8, 32, count=max(1, n // 5), stretch=5.0)
-    base = run(nabla.NB_F64, 1, 1)
+    light = run(nabla.NB_F32, ns, nf, count=max(1, n // 5), stretch=5.0)
+    base = None if a.no_serve_baseline else run(nabla.NB_F64, 1, 1)
     return {"workload": f"Poisson {a.serve_rate:.0f} req/s for {a.serve_seconds:.0f} s (seeded), op in "
                         "{grad,div,curl,lap}, O80/O160/O320/O640, levels {1,37,91,137}, 1-8 fields, "
-                        "60 GB budget, 8 streams, 32 in flight, FP32 compensated",
+                        f"60 GB budget, {ns} streams, {nf} in flight, FP32 compensated",
             "continuous_batching_fp32": ours, "continuous_batching_fp32_fifth_rate": light,
             "sequential_plain_fp64": base}
 

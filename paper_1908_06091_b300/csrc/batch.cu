@@ -590,7 +590,10 @@ static int staged_or_direct(nb_method *m, int op, const nb_field &in, const nb_f
 // (fewer tiles than SMs) runs beside others and each launch's ramp and tail
 // overlap its neighbours'.  No CTA of these kernels waits on another, so
 // they complete in any overlap.
-constexpr int kBatchBranches = 4;
+#ifndef NB_BATCH_BRANCHES
+#define NB_BATCH_BRANCHES 4
+#endif
+constexpr int kBatchBranches = NB_BATCH_BRANCHES;
 
 // One staged-route item (both passes of a Laplacian) on stream st.
 static int staged_item(nb_batch *bt, size_t k, cudaStream_t st) {
