@@ -120,7 +120,6 @@ __device__ __forceinline__ f2_t mul2(f2_t a, f2_t b) {
   return d;
 }
 
-
 // Compensated per-node sum of edge terms, two independent lanes at once (a
 // packed FP32x2 register).  In the difference form every term w (x_j - x_i)
 // is of the size of the result, so terms are summed in groups by FMA chains
