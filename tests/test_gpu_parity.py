@@ -319,3 +319,32 @@ def test_edge_variant_equals_direct_kernels_bitwise(nlev, pad, dtype):
         ref = run_op(meth, fs, op, x)
         meth.set_kernel(nabla.KERNEL_AUTO)
         assert torch.equal(got[:, lv], ref[:, lv]), (op, nlev, pad)
+
+
+def test_o32_one_level_fp64_with_the_solid_body_wind():
+    """The first configuration as stated: O32, one level, FP64, a seeded
+    spherical-harmonic scalar (degree <= 10) and the solid-body wind
+    u = 20 m/s cos(lat), v = 0, all four operators against the oracle.  The
+    discrete divergence of solid-body rotation is near zero (a truncation
+    residue), so it is gated by its absolute difference from the oracle,
+    scaled by the curl's magnitude (~2U/R)."""
+    from paper_1908_06091_b300 import synth
+    N = 32
+    g, m, meth = product(N)
+    om = oracle_mesh(N)
+    perm = m.permutation()
+    f, _ = inputs(om, 1, 10, torch.float64)
+    uv = synth.solid_body_wind(om.lat)
+    uv = np.asarray(uv, dtype=np.float64).reshape(om.V, 1, 2)
+    fs = nabla.NodeColumns(meth, 1, torch.float64)
+    fd, uvd = to_device(fs, f, perm, 1), to_device(fs, uv, perm, 2)
+    for op, x, xin in (("grad", f, fd), ("lap", f, fd)):
+        ref = oracle_op(om, op, x)
+        assert rel_l2(to_grid(run_op(meth, fs, op, xin), perm), ref) <= 1e-12, op
+    z_ref = oracle_op(om, "curl", uv)
+    z = to_grid(run_op(meth, fs, "curl", uvd), perm)
+    assert rel_l2(z, z_ref) <= 1e-12
+    d_ref = oracle_op(om, "div", uv)
+    d = to_grid(run_op(meth, fs, "div", uvd), perm)
+    assert np.abs(d - d_ref).max() <= 1e-12 * np.abs(z_ref).max()
+    assert np.abs(d_ref).max() < 1e-2 * np.abs(z_ref).max()  # the divergence is a small residue
