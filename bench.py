@@ -60,6 +60,8 @@ def parse():
     p.add_argument("--no-serve-baseline", action="store_true", help="skip the sequential FP64 serving baseline")
     p.add_argument("--serve-streams", type=int, default=8)
     p.add_argument("--serve-inflight", type=int, default=32)
+    p.add_argument("--lap-route", default="two_pass", choices=["two_pass", "fused"],
+                   help="Laplacian of the step: two passes (default) or the single-pass kernel")
     p.add_argument("--stages", type=int, default=0)
     p.add_argument("--stage-kb", type=int, default=0)
     return p.parse_args()
@@ -175,6 +177,8 @@ def algorithmic_bytes(op, V, E, L, elem):
         return V * L * elem * (1 + 2) + (V + 1) * 4 + P * (4 + 2 * elem)
     if op == "divcurl":  # one wind in, two scalars out, both weight sets
         return V * L * elem * (2 + 2) + (V + 1) * 4 + P * (4 + 4 * elem) + V * 4 * elem
+    if op == "gradlap_fused":  # f in, g and lap out; gradient and divergence weights
+        return V * L * elem * (1 + 2 + 1) + (V + 1) * 4 + 2 * P * (4 + 2 * elem) + V * 2 * elem
     # div / curl: vector in, scalar out, plus per-node self weights
     return V * L * elem * (2 + 1) + (V + 1) * 4 + P * (4 + 2 * elem) + V * 2 * elem
 
@@ -201,23 +205,30 @@ def make_inputs(nabla, synth, grid, mesh, method, nlev, lmax, dtype, device):
     return fs, f, uv
 
 
-def run_step(nabla, method, f, uv, outs, scratch, stream, ev=None):
+def run_step(nabla, method, f, uv, outs, scratch, stream, ev=None, fused=False):
     """One step of the hot path: g = grad(f); lap(f) = div(g), the Laplacian's
     second pass on the gradient just computed (the two launches of
     nb_nabla_gradlap, issued separately so that each is timed); div(uv) and
-    curl(uv) in one fused pass.  ev[0..3] bracket the three launches."""
+    curl(uv) in one fused pass.  ev[0..3] bracket the three launches.  With
+    fused, g and lap(f) come from one single-pass nb_nabla_gradlap launch
+    (the method's Laplacian route set to NB_LAP_FUSED) and ev[0..2] bracket
+    the two launches."""
     g, d, z, l = outs
-    if ev is not None:
-        ev[0].record(stream)
-    nabla.apply(method, "grad", f, g, stream=stream)
-    if ev is not None:
-        ev[1].record(stream)
-    nabla.apply(method, "div", g, l, stream=stream)
-    if ev is not None:
-        ev[2].record(stream)
+
+    def rec(i):
+        if ev is not None:
+            ev[i].record(stream)
+    rec(0)
+    if fused:
+        nabla.gradlap(method, f, g, l, stream=stream)
+        rec(1)
+    else:
+        nabla.apply(method, "grad", f, g, stream=stream)
+        rec(1)
+        nabla.apply(method, "div", g, l, stream=stream)
+        rec(2)
     nabla.divcurl(method, uv, d, z, stream=stream)
-    if ev is not None:
-        ev[3].record(stream)
+    rec(2 if fused else 3)
 
 
 def bench_ours(a):
@@ -243,6 +254,9 @@ def bench_ours(a):
     method.set_kernel(a.variant, a.tile)
     if a.stages:
         method.set_staging(a.stages, a.stage_kb)
+    fused = a.lap_route == "fused"
+    method.set_laplacian_route(nabla.LAP_FUSED if fused else nabla.LAP_TWO_PASS)
+    parts = ("gradlap", "divcurl") if fused else PARTS
     setup_s = time.time() - t0
     V, E, L = mesh.V, mesh.E, a.nlev
     fs, f, uv = make_inputs(nabla, synth, grid, mesh, method, L, a.lmax, torch.float32, device)
@@ -252,7 +266,7 @@ def bench_ours(a):
     stream = torch.cuda.Stream(device=device)
     with torch.cuda.stream(stream):
         for _ in range(max(a.warmup, 3)):
-            run_step(nabla, method, f, uv, outs, scratch, stream)
+            run_step(nabla, method, f, uv, outs, scratch, stream, fused=fused)
     stream.synchronize()
 
     # timed region: K steps, per-op CUDA events on the launching stream
@@ -265,7 +279,7 @@ def bench_ours(a):
         start.record(stream)
         with torch.cuda.stream(stream):
             for k in range(a.steps):
-                run_step(nabla, method, f, uv, outs, scratch, stream, evs[k])
+                run_step(nabla, method, f, uv, outs, scratch, stream, evs[k], fused=fused)
         stop.record(stream)
         stream.synchronize()
     barrier()
@@ -273,23 +287,23 @@ def bench_ours(a):
     ms_total = reduce_max(start.elapsed_time(stop), world, device)
     ms_step = ms_total / a.steps
     per_op_ms = {op: statistics.median(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(a.steps))
-                 for i, op in enumerate(PARTS)}
+                 for i, op in enumerate(parts)}
     nl = V * L
     value = world * 4 * nl * a.steps / (ms_total * 1e-3) / 1e9
     hbm, peak_kind = peaks()
     elem = 4
     # kernels of a step, one launch each: gradient, divergence (the
     # Laplacian's second pass), fused div+curl
-    kern = {"grad": "grad", "lap_from_grad": "div", "divcurl": "divcurl"}
-    kern_ms = {kern[p]: per_op_ms[p] for p in PARTS}
+    kern = {"grad": "grad", "lap_from_grad": "div", "divcurl": "divcurl", "gradlap": "gradlap_fused"}
+    kern_ms = {kern[p]: per_op_ms[p] for p in parts}
     dom = max(kern_ms, key=kern_ms.get)
     algo = algorithmic_bytes(dom, V, E, L, elem)
     achieved = algo / (kern_ms[dom] * 1e-3) / 1e9
     per_op = {}
-    for op in PARTS:
+    for op in parts:
         b = algorithmic_bytes(kern[op], V, E, L, elem)
         per_op[op] = {"ms": round(per_op_ms[op], 4),
-                      "gnl_s": round((2 if op == "divcurl" else 1) * nl / per_op_ms[op] / 1e6, 1),
+                      "gnl_s": round((2 if op in ("divcurl", "gradlap") else 1) * nl / per_op_ms[op] / 1e6, 1),
                       "algo_GBs": round(b / per_op_ms[op] / 1e6, 1),
                       "frac_hbm": round(b / per_op_ms[op] / 1e6 / hbm, 3)}
     # a level sample of this run's own inputs and outputs (grid order, host),
@@ -458,7 +472,9 @@ def bench_ours(a):
         "data": "synthetic: seeded spherical-harmonic fields (degree<=40), levels mixed from 8 bases",
         "config": {"workload": f"O{a.grid}x{L} grad+div+curl+lap FP32, compensated accumulation, FP64 geometry",
                    "grid": f"O{a.grid}", "nodes": V, "edges": E, "levels": L, "level_stride": fs.lp,
-                   "ops_per_step": list(OPS), "step": "grad(f); lap(f) as the divergence of that gradient; div(uv) and curl(uv) in one fused pass",
+                   "ops_per_step": list(OPS), "step": ("grad(f) and lap(f) in one single-pass kernel; " if fused else
+                            "grad(f); lap(f) as the divergence of that gradient; ")
+                           + "div(uv) and curl(uv) in one fused pass",
                    "l2": "inputs larger than L2 (no flush)",
                    "parallelism": f"replicas x{world} (independent fields per GPU)",
                    "setup_s": round(setup_s, 2)},
