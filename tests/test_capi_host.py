@@ -253,3 +253,24 @@ def test_corrupted_tile_plans_are_refused_on_the_host():
         with pytest.raises(nabla.NablaError) as ei:
             m.check_tile_plan(*args)
         assert ei.value.code == nabla.NB_EINVAL, what
+
+
+def test_new_control_calls_check_their_arguments_on_the_host():
+    """The failure-injection, probe, plan-check and kernel-control calls reject
+    NULL or out-of-range arguments with NB_EINVAL before any device work."""
+    L = nabla.lib()
+    assert L.nb_server_inject_failure(None, 1, 0) == nabla.NB_EINVAL
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    assert L.nb_probe_fp64_rate(0, None, ctypes.byref(tf), ctypes.byref(ms)) == nabla.NB_EINVAL
+    assert L.nb_probe_fp64_rate(1000, None, None, ctypes.byref(ms)) == nabla.NB_EINVAL
+    assert L.nb_method_set_wait_limit(None, 0) == nabla.NB_EINVAL
+    assert L.nb_method_set_item_shape(None, 0, -1) == nabla.NB_EINVAL
+    assert L.nb_method_set_laplacian_route(None, 0) == nabla.NB_EINVAL
+    assert L.nb_check_tile_plan(None, 1, None, None, None, None) == nabla.NB_EINVAL
+    m = nabla.Mesh(nabla.Grid(16), 1)
+    node0, hptr, halo, lnbr, _ = m.tile_plan(rcap=160, nmax=64)
+    empty = np.zeros(1, dtype=np.int32)
+    # zero tiles do not cover a mesh with nodes
+    assert L.nb_check_tile_plan(m.handle, 0, empty.ctypes.data, empty.ctypes.data, empty.ctypes.data,
+                                lnbr.ctypes.data) == nabla.NB_EINVAL
+    assert b"cover" in L.nb_last_error() or b"tiles" in L.nb_last_error()
