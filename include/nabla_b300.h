@@ -516,12 +516,13 @@ int nb_server_input(nb_server *server, uint64_t ticket, void *host_in, int64_t b
  * afterwards whose seed is `seed` has its alloc_index-th device allocation
  * refused, as a pool with no memory left would refuse it (index 0 is the
  * request's mixing weights, then per column block of its fields the input,
- * the output and, for a Laplacian, the scratch field).  Such a request ends
- * with status NB_EOOM once the work it had already enqueued has run, and
- * frees what it holds and its share of the budget; requests in flight beside
- * it are not touched.  alloc_index = -1 removes the injection for `seed`.
- * Host-side only: no device fault is involved.  (No counterpart in the
- * paper.)  Errors: NB_EINVAL. */
+ * the output and, for a Laplacian, the scratch field).  Such a request is
+ * retired at once with status NB_EOOM and returns its share of the budget;
+ * the work it had already enqueued still runs on its stream, and its device
+ * memory goes back to the pool in stream order after that work.  Requests in
+ * flight beside it are not touched.  alloc_index = -1 removes the injection
+ * for `seed`.  Host-side only: no device fault is involved.  (No counterpart
+ * in the paper.)  Errors: NB_EINVAL. */
 int nb_server_inject_failure(nb_server *server, uint64_t seed, int32_t alloc_index);
 
 /* Budget in use, its peak, queued and in-flight request counts. */
