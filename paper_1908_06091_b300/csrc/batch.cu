@@ -568,6 +568,9 @@ static int batch_build_tables(nb_batch *bt) {
                          cudaMemcpyHostToDevice));
     }
   }
+  log_msg(1, "batch: %zu items; persistent route %d + %d items in %lld + %lld units; staged route %d launches",
+          bt->src.size(), bt->nitems[0], bt->nitems[1], (long long)bt->nunits[0], (long long)bt->nunits[1],
+          bt->staged_launches);
   return NB_OK;
 }
 

@@ -9,6 +9,9 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <cstdio>
+#include <cstdarg>
+#include <chrono>
 #include <mutex>
 #include <new>
 #include <stdexcept>
@@ -21,6 +24,29 @@ namespace nb {
 
 static thread_local std::string t_last_error;
 void set_error(const std::string &msg) { t_last_error = msg; }
+
+// NB_DEBUG=1 (or 2) logs the library's setup steps to stderr: mesh and method
+// builds, tile plans, kernel shapes; 2 adds one line per operator launch.
+// Read once per process.
+int log_level() {
+  static const int level = [] {
+    const char *v = std::getenv("NB_DEBUG");
+    return v ? std::max(0, std::atoi(v)) : 0;
+  }();
+  return level;
+}
+
+void log_msg(int level, const char *fmt, ...) {
+  if (log_level() < level) return;
+  static std::mutex mu;
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  std::lock_guard<std::mutex> lk(mu);
+  std::fprintf(stderr, "[nabla_b300] %s\n", buf);
+}
 
 static std::mutex g_alloc_mu;
 static DevAlloc g_alloc;
@@ -252,7 +278,11 @@ int nb_mesh_create(const nb_grid *g, int reorder, nb_mesh **out) {
   NB_REQUIRE(g && out, NB_EINVAL, "nb_mesh_create: NULL argument");
   NB_REQUIRE(reorder == 0 || reorder == 1, NB_EINVAL, "nb_mesh_create: reorder must be 0 or 1");
   NB_GUARD_BEGIN
+  const auto t0 = std::chrono::steady_clock::now();
   *out = nb::build_mesh(const_cast<nb_grid *>(g), reorder);
+  nb::log_msg(1, "mesh: %lld nodes, %lld edges, %lld triangles, %s order, built in %.3f s", (long long)(*out)->V,
+              (long long)(*out)->E, (long long)(*out)->F, reorder ? "Hilbert" : "grid",
+              std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
   return NB_OK;
   NB_GUARD_END
 }
@@ -394,6 +424,8 @@ int nb_method_create(const nb_mesh *mesh, double radius_m, nb_method **out) {
     nb::release(m);
     return st;
   }
+  nb::log_msg(1, "method: R = %.6g m, dual area / (4 pi R^2) - 1 = %.3g, %.1f MB on device %d", m->R,
+              m->area / (4.0 * 3.14159265358979323846 * m->R * m->R) - 1.0, m->device_bytes / 1e6, m->device);
   *out = m;
   return NB_OK;
   NB_GUARD_END

@@ -436,6 +436,9 @@ static int lap_plan_upload(LapPlan *lp, nb_method *m, const LapLayout &L, int nm
     }
   }
   lp->ntiles = (int)h.node0.size() - 1;
+  log_msg(1, "single-pass Laplacian plan: %d tiles (%d pole-row), at most %d g-nodes and %d records a tile, "
+          "%zu ring columns in all", lp->ntiles, lp->ntiles - h.ntiles_main, h.max_gnodes, h.max_recs,
+          h.halo.size());
   lp->ntiles_main = h.ntiles_main;
   lp->max_gnodes = h.max_gnodes;
   h.gn.resize(h.gn.size() + 8, 0);        // slack for 16-byte bounding copies
@@ -614,6 +617,8 @@ int launch_fused_lap(nb_method *m, const nb_field *f, const nb_field *lap, const
     return NB_EINVAL;
   }
   const int grid = std::min(lp->ntiles, sms);
+  log_msg(2, "single-pass Laplacian launch: %d levels, %d tiles, grid %d, %zu B shared%s", f->nlev, lp->ntiles,
+          grid, smem, g ? ", gradient written" : "");
   *handled = true;
   const bool comp = m->compensated != 0;
   if (KU == 3) return comp ? launch_lap_t<true, 3>(a, map, grid, smem, st) : launch_lap_t<false, 3>(a, map, grid, smem, st);

@@ -17,6 +17,9 @@
 namespace nb {
 
 void set_error(const std::string &msg);
+// stderr logging when NB_DEBUG >= level (capi.cu)
+int log_level();
+void log_msg(int level, const char *fmt, ...);
 
 // Source of library-owned device memory: the caller's nb_allocator, or the
 // CUDA runtime when user.alloc is NULL (capi.cu).

@@ -361,6 +361,8 @@ static void worker_loop(nb_server *s) {
       const int rc = launch_request(s, q);
       lk.lock();
       if (rc != NB_OK) {
+        log_msg(1, "server: request %llu (op %d, O%d, %d levels, %d fields) failed with status %d",
+                (unsigned long long)q->ticket, q->r.op, q->r.N, q->r.nlev, q->r.nfields, rc);
         q->status = rc;
         if (!q->ev) {  // nothing to wait for: retire now
           const double t_done = s->now();

@@ -390,6 +390,9 @@ static int plan_upload(TilePlan *tp, nb_method *m) {
   loff.resize(loff.size() + 8, 0);  // slack for 16-byte bounding copies
   if (halo.empty()) halo.push_back(0);
   tp->ntiles = (int)node0.size() - 1;
+  log_msg(1, "staged plan: %d tiles (%d pole-row), column pitch %lld B, stage area %lld B, largest halo %d, "
+          "%zu halo columns in all", tp->ntiles, tp->ntiles - tp->ntiles_main, (long long)tp->row_bytes,
+          (long long)tp->area, tp->max_halo, halo.size());
   auto up = [&](void **dst, const void *src, size_t bytes) -> int {
     const size_t nb = std::max<size_t>(bytes, 16);
     const int st = dev_alloc(m->alloc, dst, nb, "tile plan upload");
@@ -660,6 +663,8 @@ int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, 
     return NB_EINVAL;
   }
   const int grid = std::min(tp->ntiles, g_sm_count);
+  log_msg(2, "staged launch: op %d%s, %d levels x %d vars, %d units per item, %d items per node, %d tiles, "
+          "grid %d, %zu B shared", op, fused ? " (div+curl)" : "", in->nlev, nvar, KU, G, tp->ntiles, grid, smem);
   *handled = true;
   const bool comp = comp_mode < 0 ? m->compensated != 0 : comp_mode != 0;
   if (g) return comp ? launch_staged_t<0, true, 1>(a, map, grid, smem, st) : launch_staged_t<0, false, 1>(a, map, grid, smem, st);

@@ -274,3 +274,21 @@ def test_new_control_calls_check_their_arguments_on_the_host():
     assert L.nb_check_tile_plan(m.handle, 0, empty.ctypes.data, empty.ctypes.data, empty.ctypes.data,
                                 lnbr.ctypes.data) == nabla.NB_EINVAL
     assert b"cover" in L.nb_last_error() or b"tiles" in L.nb_last_error()
+
+
+def test_nb_debug_logs_setup_steps_to_stderr():
+    """NB_DEBUG=1 makes the library log its setup steps (here a mesh build)
+    to stderr; unset, it prints nothing."""
+    import subprocess
+    import sys
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_1908_06091_b300 import nabla\n"
+            "nabla.Mesh(nabla.Grid(16), 1)\n") % ROOT
+    env = dict(os.environ)
+    env.pop("NB_DEBUG", None)
+    quiet = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=120)
+    env["NB_DEBUG"] = "1"
+    loud = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=120)
+    assert quiet.returncode == 0 and loud.returncode == 0
+    assert "[nabla_b300]" not in quiet.stderr
+    assert "[nabla_b300] mesh: 1600 nodes, 4794 edges, 3196 triangles" in loud.stderr
