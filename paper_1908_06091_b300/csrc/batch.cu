@@ -615,20 +615,29 @@ static int staged_item(nb_batch *bt, size_t k, cudaStream_t st) {
 }
 
 // Launch the phases on stream st and its side streams (used for capture and
-// for tuning): the persistent phases on st, the staged-route items spread
-// over st and the side streams, largest first onto the least-loaded branch
-// (st's load counts the persistent items).  Errors after the fork still
-// join every branch, so a capture ends with no branch left open.
+// for tuning): the persistent phases on st, then the staged-route items
+// spread over st and the side streams, largest first onto the least-loaded
+// branch (st's load counts the persistent items).  Errors after the fork
+// still join every branch, so a capture ends with no branch left open.
 static int batch_launch(nb_batch *bt, cudaStream_t st, cudaStream_t *side = nullptr, int nside = 0) {
   const int nb = 1 + std::min(nside, kBatchBranches - 1);
   cudaStream_t lanes[kBatchBranches] = {st};
   for (int b = 1; b < nb; ++b) lanes[b] = side[b - 1];
   cudaEvent_t ev[2 * kBatchBranches] = {};
   int nev = 0;
+  // the persistent phases first, on st alone: run beside the large staged
+  // launches they compete for SMs (timed: 4.74 against 4.63 ms on the
+  // 64-field batch)
+  NB_CUDA(cudaMemsetAsync(bt->d_counter, 0, 2 * sizeof(unsigned long long), st));
+  for (int p = 0; p < 2; ++p) {
+    if (bt->nunits[p] == 0) continue;
+    batch_kernel<<<bt->grid, kBatchThreads, 0, st>>>(bt->d_items[p], bt->nitems[p], bt->nunits[p],
+                                                     bt->d_counter + p, bt->comp);
+    count_launch(1);
+    NB_CUDA(cudaGetLastError());
+  }
   int rc = NB_OK;
-  if (nb > 1) {
-    // fork first: the side streams start at once, beside the persistent
-    // phases that follow on st
+  if (nb > 1) {  // fork: the side streams follow st
     cudaEvent_t fork = nullptr;
     NB_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
     ev[nev++] = fork;
@@ -637,16 +646,6 @@ static int batch_launch(nb_batch *bt, cudaStream_t st, cudaStream_t *side = null
       if (cudaStreamWaitEvent(lanes[b], fork, 0) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "batch fork");
   }
   double load[kBatchBranches] = {};
-  if (rc == NB_OK && cudaMemsetAsync(bt->d_counter, 0, 2 * sizeof(unsigned long long), st) != cudaSuccess)
-    rc = cuda_fail(cudaGetLastError(), "batch counter reset");
-  for (int p = 0; p < 2 && rc == NB_OK; ++p) {
-    if (bt->nunits[p] == 0) continue;
-    batch_kernel<<<bt->grid, kBatchThreads, 0, st>>>(bt->d_items[p], bt->nitems[p], bt->nunits[p],
-                                                     bt->d_counter + p, bt->comp);
-    count_launch(1);
-    const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) rc = cuda_fail(e, "batch_kernel launch");
-  }
   for (size_t k = 0; k < bt->src.size(); ++k)
     if (!staged_route(bt->shape[k])) load[0] += (double)bt->src[k].in.nnodes * bt->src[k].in.nlev;
   std::vector<size_t> order;

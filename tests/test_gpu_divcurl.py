@@ -137,3 +137,29 @@ def test_operator_calls_capture_into_a_cuda_graph_after_first_use():
     assert all(torch.equal(a, b) for a, b in zip(eager, outs))
     assert torch.equal(outs[1], outs[4])  # gradlap's Laplacian == nb_nabla_laplacian
     assert nabla.device_status() == 0
+
+
+@pytest.mark.parametrize("N,nlev", [(32, 137), (48, 91), (24, 37), (16, 16)])
+def test_item_shapes_give_identical_results(N, nlev):
+    """The staged div / curl kernels give the same bits for every item shape
+    (2 or 3 units per item, items per node rounded to a multiple of 8 or
+    not): each level's arithmetic does not depend on the shape."""
+    g, m, meth = product(N)
+    om = oracle_mesh(N)
+    _, uv = inputs(om, nlev, 10, torch.float32)
+    fs = nabla.NodeColumns(meth, nlev, torch.float32)
+    uvd = to_device(fs, uv, m.permutation(), 2)
+    ref = None
+    try:
+        for units, aligned in ((2, 0), (2, 1), (3, 0), (3, 1), (0, -1)):
+            meth.set_item_shape(units, aligned)
+            d, z = _fused(meth, fs, uvd)
+            d1 = run_op(meth, fs, "div", uvd)
+            got = (d[:, :nlev].clone(), z[:, :nlev].clone(), d1[:, :nlev].clone())
+            if ref is None:
+                ref = got
+            assert all(torch.equal(a, b) for a, b in zip(got, ref)), (units, aligned)
+    finally:
+        meth.set_item_shape(0, -1)
+    with pytest.raises(nabla.NablaError):
+        meth.set_item_shape(4, 0)
