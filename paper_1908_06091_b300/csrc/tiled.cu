@@ -75,12 +75,39 @@ struct TiledArgs {
   uint32_t col_area;    // staged column offsets lie below this (index checks)
 };
 
-// Issue the copies of tile t into the stage at `stage` (one whole warp).
-__device__ __forceinline__ void issue_tile(const TiledArgs &a, const CUtensorMap *map, int t,
+// What the producer reads from global memory to issue a tile's copies: its
+// node and halo ranges, its CSR range, and this lane's first group of four
+// halo nodes.  Loaded one iteration ahead, while the producer waits for the
+// stage to be released, so that a release is followed at once by the copies.
+struct TilePrep {
+  int32_t n0, n1, h0, h1, pa, pb;
+  int32_t y[4];  // halo nodes of group `lane` (when the tile has that group)
+};
+
+__device__ __forceinline__ TilePrep prepare_tile(const TiledArgs &a, int t, int lane) {
+  TilePrep p;
+  p.n0 = __ldg(a.tile_node0 + t);
+  p.n1 = __ldg(a.tile_node0 + t + 1);
+  p.h0 = __ldg(a.halo_ptr + t);
+  p.h1 = __ldg(a.halo_ptr + t + 1);
+  p.pa = __ldg(a.row_ptr + p.n0);
+  p.pb = __ldg(a.row_ptr + p.n1);
+  const uint32_t H = (uint32_t)(p.h1 - p.h0);
+  if ((uint32_t)lane < ((H + 3u) >> 2)) {
+    // a short last group repeats its last node (the copy fills the group's slots)
+    const int32_t *hp = a.halo + p.h0;
+    const uint32_t k = 4u * (uint32_t)lane, last = H - 1u;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) p.y[q] = (int32_t)NB_IDX(__ldg(hp + min(k + (uint32_t)q, last)), 0, a.nnodes, a.status);
+  }
+  return p;
+}
+
+// Issue the copies of a prepared tile into the stage at `stage` (one whole
+// warp).
+__device__ __forceinline__ void issue_tile(const TiledArgs &a, const CUtensorMap *map, const TilePrep &p,
                                            uint32_t stage, uint32_t bar, int lane) {
-  const int32_t n0 = __ldg(a.tile_node0 + t), n1 = __ldg(a.tile_node0 + t + 1);
-  const int32_t h0 = __ldg(a.halo_ptr + t), h1 = __ldg(a.halo_ptr + t + 1);
-  const int32_t pa = __ldg(a.row_ptr + n0), pb = __ldg(a.row_ptr + n1);
+  const int32_t n0 = p.n0, n1 = p.n1, h0 = p.h0, h1 = p.h1, pa = p.pa, pb = p.pb;
   const uint32_t n = (uint32_t)(n1 - n0), H = (uint32_t)(h1 - h0);
   // 8-byte weights are copied from an even entry; 16-byte records as they are
   const int32_t wa = a.rec16 ? pa : (pa & ~1), wb = a.rec16 ? pb : ((pb + 1) & ~1);
@@ -131,8 +158,10 @@ __device__ __forceinline__ void issue_tile(const TiledArgs &a, const CUtensorMap
     if (a.rec16) bulk_g2s(stage + a.off_s, a.s4 + sa, sbytes, bar);
     else bulk_g2s(stage + a.off_s, a.s32 + sa, sbytes, bar);
   }
-  for (uint32_t g = lane; g < groups; g += 32) {
-    // a short last group repeats its last node (the copy fills the group's slots)
+  if ((uint32_t)lane < groups)
+    gather4_g2s(stage + hbase + (uint32_t)lane * a.gpitch, map, p.y[0], p.y[1], p.y[2], p.y[3], bar);
+  for (uint32_t g = (uint32_t)lane + 32u; g < groups; g += 32) {
+    // groups past the 32nd (rare): halo nodes loaded here
     const int32_t *hp = a.halo + h0;
     const uint32_t k = 4u * g, last = H - 1u;
     auto hid = [&](uint32_t q) { return (int32_t)NB_IDX(__ldg(hp + q), 0, a.nnodes, a.status); };
@@ -318,17 +347,21 @@ __global__ void __launch_bounds__(StagedShape<OP>::threads, 1)
   __syncthreads();
   const int G = gridDim.x;
   if (warp == W) {
-    // producer
+    // producer: tile i+G's global metadata is loaded before waiting for the
+    // stage tile i goes to
     int k = 0;
     bool failed = false;
+    TilePrep next{};
+    if ((int)blockIdx.x < a.ntiles) next = prepare_tile(a, tile_at(a, blockIdx.x), lane);
     for (int i = blockIdx.x; i < a.ntiles; i += G, ++k) {
-      const int t = tile_at(a, i);
+      const TilePrep cur = next;
+      if (i + G < a.ntiles) next = prepare_tile(a, tile_at(a, i + G), lane);
       const int s = k % NS;
       if (k >= NS && !mbar_wait_bounded(empty0 + 8 * s, (uint32_t)(k / NS - 1) & 1u, a.timeout_ns)) {
         failed = true;
         break;
       }
-      issue_tile(a, &map, t, stage0 + s * a.stage_bytes, full0 + 8 * s, lane);
+      issue_tile(a, &map, cur, stage0 + s * a.stage_bytes, full0 + 8 * s, lane);
       // L2 prefetch of the column block of a later tile of this walk
       constexpr int D = StagedShape<OP>::ahead;
       if (lane == 0 && i + D * G < a.ntiles) {
