@@ -73,14 +73,40 @@ struct LapArgs {
 constexpr int kLapWarps = 12;
 constexpr int kLapThreads = 32 * (kLapWarps + 1);
 
-__device__ __forceinline__ void issue_lap_tile(const LapArgs &a, const CUtensorMap *map, int t, uint32_t stage,
-                                               uint32_t bar, int lane) {
-  const int32_t n0 = __ldg(a.tile_node0 + t), n1 = __ldg(a.tile_node0 + t + 1);
-  const int32_t h0 = __ldg(a.halo_ptr + t), h1 = __ldg(a.halo_ptr + t + 1);
-  const int32_t g0 = __ldg(a.gn_ptr + t), g1 = __ldg(a.gn_ptr + t + 1);
-  const int32_t q0 = __ldg(a.rec_ptr + t), q1 = __ldg(a.rec_ptr + t + 1);
-  const int32_t pa = __ldg(a.row_ptr + n0), pb = __ldg(a.row_ptr + n1);
-  const int32_t H1 = __ldg(a.r1_count + t);
+// A tile's global metadata and this lane's first group of four ring nodes,
+// loaded one iteration ahead while the producer waits for the stage.
+struct LapPrep {
+  int32_t n0, n1, h0, h1, g0, g1, q0, q1, pa, pb, H1;
+  int32_t y[4];
+};
+
+__device__ __forceinline__ LapPrep prepare_lap_tile(const LapArgs &a, int t, int lane) {
+  LapPrep p;
+  p.n0 = __ldg(a.tile_node0 + t);
+  p.n1 = __ldg(a.tile_node0 + t + 1);
+  p.h0 = __ldg(a.halo_ptr + t);
+  p.h1 = __ldg(a.halo_ptr + t + 1);
+  p.g0 = __ldg(a.gn_ptr + t);
+  p.g1 = __ldg(a.gn_ptr + t + 1);
+  p.q0 = __ldg(a.rec_ptr + t);
+  p.q1 = __ldg(a.rec_ptr + t + 1);
+  p.pa = __ldg(a.row_ptr + p.n0);
+  p.pb = __ldg(a.row_ptr + p.n1);
+  p.H1 = __ldg(a.r1_count + t);
+  const uint32_t H = (uint32_t)(p.h1 - p.h0);
+  if ((uint32_t)lane < ((H + 3u) >> 2)) {
+    const int32_t *hp = a.halo + p.h0;
+    const uint32_t k = 4u * (uint32_t)lane, last = H - 1u;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) p.y[q] = (int32_t)NB_IDX(__ldg(hp + min(k + (uint32_t)q, last)), 0, a.nnodes, a.status);
+  }
+  return p;
+}
+
+__device__ __forceinline__ void issue_lap_tile(const LapArgs &a, const CUtensorMap *map, const LapPrep &p,
+                                               uint32_t stage, uint32_t bar, int lane) {
+  const int32_t n0 = p.n0, n1 = p.n1, h0 = p.h0, h1 = p.h1, g0 = p.g0, g1 = p.g1, q0 = p.q0, q1 = p.q1;
+  const int32_t pa = p.pa, pb = p.pb, H1 = p.H1;
   const uint32_t n = (uint32_t)(n1 - n0), H = (uint32_t)(h1 - h0);
   // 16-byte bounding ranges of the metadata arrays
   const int32_t ga = g0 & ~3, gb = (g1 + 3) & ~3;
@@ -129,7 +155,9 @@ __device__ __forceinline__ void issue_lap_tile(const LapArgs &a, const CUtensorM
   if (lane == 4) bulk_g2s(stage + a.off_go, a.goff + la, gob, bar);
   if (lane == 5) bulk_g2s(stage + a.off_rp, a.row_ptr + ra, rpb, bar);
   if (lane == 6) bulk_g2s(stage + a.off_sd, a.sd32 + sa, sdb, bar);
-  for (uint32_t g = lane; g < groups; g += 32) {
+  if ((uint32_t)lane < groups)
+    gather4_g2s(stage + hbase + (uint32_t)lane * a.gpitch, map, p.y[0], p.y[1], p.y[2], p.y[3], bar);
+  for (uint32_t g = (uint32_t)lane + 32u; g < groups; g += 32) {
     const int32_t *hp = a.halo + h0;
     const uint32_t k = 4u * g, last = H - 1u;
     auto hid = [&](uint32_t q) { return (int32_t)NB_IDX(__ldg(hp + q), 0, a.nnodes, a.status); };
@@ -295,14 +323,17 @@ __global__ void __launch_bounds__(kLapThreads, 1)
   if (warp == W) {
     int k = 0;
     bool failed = false;
+    LapPrep next{};
+    if ((int)blockIdx.x < a.ntiles) next = prepare_lap_tile(a, lap_tile_at(a, blockIdx.x), lane);
     for (int i = blockIdx.x; i < a.ntiles; i += GR, ++k) {
-      const int t = lap_tile_at(a, i);
+      const LapPrep cur = next;
+      if (i + GR < a.ntiles) next = prepare_lap_tile(a, lap_tile_at(a, i + GR), lane);
       const int s = k % NS;
       if (k >= NS && !mbar_wait_bounded(emptyb + 8 * s, (uint32_t)(k / NS - 1) & 1u, a.timeout_ns)) {
         failed = true;
         break;
       }
-      issue_lap_tile(a, &map, t, stage0 + s * a.stage_bytes, fullb + 8 * s, lane);
+      issue_lap_tile(a, &map, cur, stage0 + s * a.stage_bytes, fullb + 8 * s, lane);
       if (lane == 0 && i + GR < a.ntiles) {
         const int tp = lap_tile_at(a, i + GR);
         const int32_t p0 = __ldg(a.tile_node0 + tp), p1 = __ldg(a.tile_node0 + tp + 1);
