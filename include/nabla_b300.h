@@ -186,8 +186,23 @@ int nb_mesh_triangles(const nb_mesh *mesh, int32_t *tri);
 int nb_mesh_edges(const nb_mesh *mesh, int32_t *edge);
 
 /* Node -> neighbour CSR in functionspace numbering (host): row_ptr[V+1],
- * nbr[2E], neighbours of each node ascending. */
+ * nbr[2E].  Each node's neighbours are ascending, except in the rows of
+ * paired nodes (nb_mesh_node_pairs), which start with the two neighbours
+ * the pair shares, ascending, then the partner, then the other three
+ * ascending.  Every operator sums a node's edge terms in this row order. */
 int nb_mesh_csr(const nb_mesh *mesh, int64_t *row_ptr, int32_t *nbr);
+
+/* Node pairs of the FP32 staged kernels (host): mate[V] is the
+ * partner of each paired node, -1 for an unpaired one.  A pair is two
+ * adjacent six-neighbour nodes outside the pole rows, at most 16 places
+ * apart in functionspace order, with exactly two common neighbours,
+ * matched greedily along the node order.  When both nodes of a pair are
+ * own nodes of one staged tile, one consumer thread evaluates both from
+ * the 10 columns they span instead of 14 (the shared neighbours and the
+ * partner's own column are read once); results are the same bits as the
+ * single-node evaluation (nb_method_set_node_pairs).
+ * mate: caller-owned host int32[V].  Errors: NB_EINVAL. */
+int nb_mesh_node_pairs(const nb_mesh *mesh, int32_t *mate);
 
 /* Tile plan of the shared-memory staged kernels (host, for inspection):
  * tiles of consecutive nodes, grown while own nodes + halo nodes <= rcap and
@@ -588,6 +603,17 @@ int nb_method_set_laplacian_route(nb_method *method, int route);
  * per level count.  Results do not depend on the shape (each level's
  * arithmetic is the same).  For tuning and tests; errors: NB_EINVAL. */
 int nb_method_set_item_shape(nb_method *method, int units, int aligned);
+
+/* Node pairs in the staged FP32 kernels (grad, div, curl, fused div+curl).
+ * With pairs, one consumer thread evaluates both nodes of a pair
+ * (nb_mesh_node_pairs) whose nodes are own nodes of the same staged tile,
+ * reading the 10 columns they span once instead of 14 times; without,
+ * every node alone.  Both give the same bits (each node's terms are summed
+ * in its row order either way).  mode = 1: pairs in every staged pass;
+ * 0: in none; -1 (the default): in all but the fused div+curl pass, whose
+ * two sets of sums leave too few registers for a second node.  For tuning
+ * and tests; errors: NB_EINVAL. */
+int nb_method_set_node_pairs(nb_method *method, int mode);
 
 /* Limit of every wait inside the staged kernels' copy pipeline (a warp
  * waiting for a stage's copies to land, or for the consumer warps to release

@@ -325,6 +325,12 @@ int nb_mesh_csr(const nb_mesh *m, int64_t *row_ptr, int32_t *nbr) {
   return NB_OK;
 }
 
+int nb_mesh_node_pairs(const nb_mesh *m, int32_t *mate) {
+  NB_REQUIRE(m && mate, NB_EINVAL, "nb_mesh_node_pairs: NULL argument");
+  std::memcpy(mate, m->mate.data(), sizeof(int32_t) * m->V);
+  return NB_OK;
+}
+
 int nb_mesh_tile_plan(const nb_mesh *m, int rcap, int nmax, int32_t *ntiles, int32_t *ntiles_main,
                       int64_t *nhalo, int32_t *node0, int32_t *halo_ptr, int32_t *halo,
                       uint16_t *lnbr) {
@@ -492,6 +498,14 @@ int nb_method_set_item_shape(nb_method *m, int units, int aligned) {
   NB_REQUIRE(aligned >= -1 && aligned <= 1, NB_EINVAL, "nb_method_set_item_shape: aligned must be -1, 0 or 1");
   m->item_units = units;
   m->item_align = aligned;
+  return NB_OK;
+}
+
+int nb_method_set_node_pairs(nb_method *m, int mode) {
+  NB_REQUIRE(m, NB_EINVAL, "nb_method_set_node_pairs: NULL method");
+  NB_REQUIRE(mode >= -1 && mode <= 1, NB_EINVAL, "nb_method_set_node_pairs: mode must be -1, 0 or 1");
+  m->node_pairs = mode;
+  nb::log_msg(1, "method: node pairs %s", mode > 0 ? "on" : mode == 0 ? "off" : "on except in the fused pass");
   return NB_OK;
 }
 

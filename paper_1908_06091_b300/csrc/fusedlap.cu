@@ -378,7 +378,9 @@ __global__ void __launch_bounds__(kLapThreads, 1)
     v.w = stage + a.off_wd - 8u * (uint32_t)(pa & ~1);
     v.l = stage + a.off_go - 4u * (uint32_t)(pa & ~3);
     v.s = stage + a.off_sd - 8u * (uint32_t)(n0 & ~1);
-    divcurl_tile<COMP, false, KU>(a, v, t >= a.ntiles_main, a.g_pitch, warp, W);
+    v.p = 0u;  // every node alone
+    v.npairs = 0;
+    divcurl_tile<COMP, false, KU, false>(a, v, t >= a.ntiles_main, a.g_pitch, warp, W);
     __syncwarp();
     if (lane == 0) {
       mbar_arrive(emptyb + 8 * s);
@@ -610,7 +612,7 @@ int launch_fused_lap(nb_method *m, const nb_field *f, const nb_field *lap, const
   a.out_stride = lap->node_stride;
   a.nlev = f->nlev;
   int KU = 2, G = 0;
-  item_shape(m->item_units, m->item_align, (f->nlev + 1) / 2, false, KU, G);
+  item_shape(m->item_units, m->item_align, (f->nlev + 1) / 2, KU, G);
   a.G = G;
   magic_div((uint32_t)G, a.g_magic, a.g_shift);
   a.Gg = z.Gg;

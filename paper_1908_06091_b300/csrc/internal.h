@@ -75,7 +75,8 @@ struct nb_mesh : nb::RefCounted {
   std::vector<double> xyz;           // [V][3] unit position, new order
   std::vector<double> lat, lon;      // per node, new order
   std::vector<int32_t> tri;          // [F][3] CCW, new numbering
-  // node -> neighbour CSR, neighbours ascending
+  // node -> neighbour CSR, neighbours ascending except in the rows of
+  // paired nodes: (shared A, shared B, partner, the other three ascending)
   std::vector<int64_t> row_ptr;      // V+1
   std::vector<int32_t> nbr;          // 2E neighbour node
   std::vector<int32_t> nbr_edge;     // 2E edge id
@@ -83,6 +84,7 @@ struct nb_mesh : nb::RefCounted {
   std::vector<int32_t> nbr_right;    // 2E triangle right of (i -> j)
   std::vector<int32_t> edge;         // [E][2] a < b
   std::vector<int32_t> edge_tri;     // [E][2] (left, right) of a -> b
+  std::vector<int32_t> mate;         // [V] partner of a paired node, -1 if unpaired (pair_nodes)
   ~nb_mesh() override { nb::release(grid); }
 };
 
@@ -103,6 +105,13 @@ struct TilePlan {
   int32_t *d_halo_ptr = nullptr;     // ntiles+1
   int32_t *d_halo = nullptr;         // halo node ids
   uint32_t *d_loff = nullptr;        // 2E (+4): stage byte offset of each CSR neighbour
+  // node pairs: tile t's slots d_slots[d_slot_ptr[t] .. d_slot_ptr[t + 1])
+  // (padded to a multiple of 4), own node li | partner lj << 16, the first
+  // d_npairs[t] of them pairs, then single nodes (li | li << 16)
+  int32_t *d_slot_ptr = nullptr;     // ntiles+1
+  int32_t *d_npairs = nullptr;       // ntiles
+  uint32_t *d_slots = nullptr;
+  int64_t paired_nodes = 0;          // own nodes that fall in a pair slot
 };
 
 // Device side of a single-pass Laplacian plan (fusedlap.cu).
@@ -150,6 +159,7 @@ struct nb_method : nb::RefCounted {
   int64_t wait_limit_ns = -1;  // staged kernels' pipeline wait limit (-1 = default)
   int item_units = 0;   // staged div / curl: 2-level units per item (0 = chosen per column)
   int item_align = -1;  // staged div / curl: items per node a multiple of 8 (1), not (0), chosen (-1)
+  int node_pairs = -1;  // staged kernels: node pairs always (1), never (0), all but the fused pass (-1)
   std::mutex plan_mu;
   std::map<std::tuple<int64_t, int64_t, int64_t, int, int, int>, std::unique_ptr<TilePlan>> plans;
   std::map<std::tuple<int64_t, int64_t, int64_t, int64_t, int64_t, int, int>, std::unique_ptr<LapPlan>> lap_plans;
@@ -221,6 +231,8 @@ void build_lap_plan(const nb_mesh *m, const LapLayout &layout, int nmax, int pol
 bool check_tile_plan(const nb_mesh *m, int ntiles, const int32_t *node0, const int32_t *halo_ptr,
                      const int32_t *halo, const std::function<int64_t(int64_t, int, int64_t)> &slot,
                      std::string &why);
+bool check_slot_lists(const nb_mesh *m, int ntiles, const int32_t *node0, const int32_t *slot_ptr,
+                      const int32_t *npairs, const uint32_t *slots, std::string &why);
 
 // device side (nabla_kernels.cu)
 int method_upload(nb_method *m);            // returns NB_* status

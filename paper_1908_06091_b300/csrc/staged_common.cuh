@@ -88,37 +88,19 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
   }
 }
 
-// packed FP32x2 arithmetic (two lanes per register pair, IEEE round-to-nearest)
-typedef unsigned long long f2_t;
-__device__ __forceinline__ f2_t pk(float a, float b) {
-  f2_t r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-  return r;
-}
+// Packed FP32x2 arithmetic: two independent FP32 lanes per value, each
+// operation IEEE round-to-nearest (the CUDA float2 intrinsics of sm_100 and
+// later; a difference is the sum with the negated operand, which is exact).
+typedef float2 f2_t;
+__device__ __forceinline__ f2_t pk(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ void upk(f2_t r, float &a, float &b) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+  a = r.x;
+  b = r.y;
 }
-__device__ __forceinline__ f2_t fma2(f2_t a, f2_t b, f2_t c) {
-  f2_t d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-__device__ __forceinline__ f2_t add2(f2_t a, f2_t b) {
-  f2_t d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2_t sub2(f2_t a, f2_t b) {
-  f2_t d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-
-__device__ __forceinline__ f2_t mul2(f2_t a, f2_t b) {
-  f2_t d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
+__device__ __forceinline__ f2_t fma2(f2_t a, f2_t b, f2_t c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ f2_t add2(f2_t a, f2_t b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2_t sub2(f2_t a, f2_t b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ f2_t mul2(f2_t a, f2_t b) { return __fmul2_rn(a, b); }
 
 // Compensated per-node sum of edge terms, two independent lanes at once (a
 // packed FP32x2 register).  In the difference form every term w (x_j - x_i)
@@ -137,7 +119,7 @@ struct GroupSum {
   __device__ __forceinline__ void term(f2_t w, f2_t d) { y = fma2(w, d, y); }
   __device__ __forceinline__ void close_first() {
     s = y;
-    e = 0ull;
+    e = make_float2(0.f, 0.f);
   }
   __device__ __forceinline__ void close() {
     const f2_t t = add2(s, y);
@@ -179,13 +161,13 @@ __device__ __forceinline__ float2 lds64(uint32_t a) {
   asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
   return v;
 }
-// 16 bytes as two packed FP32x2 registers, 8 bytes as one (no repacking moves)
-__device__ __forceinline__ void lds2x64(uint32_t a, unsigned long long &lo, unsigned long long &hi) {
-  asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(lo), "=l"(hi) : "r"(a));
+// 16 bytes as two packed FP32x2 values, 8 bytes as one
+__device__ __forceinline__ void lds2x64(uint32_t a, f2_t &lo, f2_t &hi) {
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(lo.x), "=f"(lo.y), "=f"(hi.x), "=f"(hi.y) : "r"(a));
 }
-__device__ __forceinline__ unsigned long long lds_b64(uint32_t a) {
-  unsigned long long v;
-  asm volatile("ld.shared.b64 %0, [%1];" : "=l"(v) : "r"(a));
+__device__ __forceinline__ f2_t lds_b64(uint32_t a) {
+  f2_t v;
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
   return v;
 }
 __device__ __forceinline__ uint32_t lds_u32(uint32_t a) {
@@ -221,6 +203,10 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 struct TileView {
   int32_t n0, n1;
   uint32_t rows, w, l, r, s;
+  // slot list (div / curl, 0 = none): slot q = own node li | node lj << 16;
+  // the first npairs slots are node pairs (li, lj), the rest single nodes
+  uint32_t p;
+  int32_t npairs;
 };
 
 // Consumer side.  A warp takes items [i0, i1) of tile t, one per lane,
@@ -231,8 +217,8 @@ struct TileView {
 // packed FP32x2 registers.
 //
 // div / curl.  A staged (u, v) column is a sequence of 16-byte units of two
-// levels each.  Item c of a node takes the KU units c, c + G, c + 2G, ...
-// (G items per node).  With G a multiple of 8 and warp shares starting on
+// levels each.  Item c of a slot takes the KU units c, c + G, c + 2G, ...
+// (G items per slot).  With G a multiple of 8 and warp shares starting on
 // multiples of 8 items, the 8 lanes of every quarter-warp read 8 consecutive
 // units of one column, 128 contiguous bytes: no shared-memory bank
 // conflicts.  More units per item spread each item's row pointers, offsets
@@ -241,25 +227,96 @@ struct TileView {
 // differences are shared, each operator keeps its own weights and sums, and
 // each output gets exactly the arithmetic of its single-operator pass.
 //
+// Slots.  Without a slot list a slot is one own node, in node order.  With
+// one, the first npairs slots are node pairs (i, j): adjacent six-neighbour
+// nodes whose rows both start with their two shared neighbours A, B and
+// then the partner.  A pair item reads the columns of i, j, A and B once,
+// forms the first group of both nodes (A, B and the partner, whose
+// difference x_i - x_j is the exact negation of x_j - x_i), then each
+// node's other three neighbours: 10 column reads for two nodes instead of
+// 14, and each node's sum takes the same terms in the same order as on the
+// single-node path, so the bits are the same.
+//
 // A supplies G, g_magic, g_shift, nlev, the FP64 weights of the pole path
 // (w64, w64b, s64, s64b), the outputs (out, out2, out_stride), and for the
 // bounds-checked build status and col_area (staged column offsets lie below
-// it); v locates
-// the tile's columns (own node k at v.rows + k rb) and staged metadata; pole
-// tiles run in FP64.
-template <bool COMP, bool FUSED, int KU, class A>
+// it); v locates the tile's columns (own node k at v.rows + k rb), staged
+// metadata and slot list; pole tiles run in FP64 (they hold no pairs).
+// PAIRS = false compiles the consumer without the slot list and pair path.
+template <bool COMP, bool FUSED, int KU, bool PAIRS, class A>
 __device__ __forceinline__ void divcurl_tile(const A &a, const TileView &v, bool pole, uint32_t rb, int part,
                                              int nparts) {
+  const uint32_t n = (uint32_t)(v.n1 - v.n0);
+  const uint32_t npairs = (PAIRS && v.p) ? (uint32_t)v.npairs : 0u;
   uint32_t i0, i1;
-  warp_share((uint32_t)(v.n1 - v.n0) * (uint32_t)a.G, part, nparts, i0, i1);
+  warp_share((n - npairs) * (uint32_t)a.G, part, nparts, i0, i1);
   const uint32_t units = (uint32_t)(a.nlev + 1) >> 1;
   const uint32_t G = (uint32_t)a.G;
+  const uint32_t rs = FUSED ? 16u : 8u;  // bytes of a weight record (and of a self-weight record)
+  // weights of staged record `at`: div, and curl when fused
+  auto weights = [&](uint32_t at, f2_t &wd, f2_t &wc) {
+    if (FUSED) lds2x64(at, wd, wc);
+    else {
+      wd = lds_b64(at);
+      wc = make_float2(0.f, 0.f);
+    }
+  };
+  auto column = [&](uint32_t at) {
+    return v.rows + (uint32_t)NB_IDX(lds_u32(at), 0, a.col_area, a.status);
+  };
+  // unit k holds levels 2u, 2u + 1 (u = c + k G)
+  auto put = [&](float *oo, const float (&o)[2 * KU], uint32_t c, const bool (&has)[KU]) {
+#pragma unroll
+    for (int k = 0; k < KU; ++k) {
+      if (!has[k]) continue;
+      const int la = 2 * (int)(c + (uint32_t)k * G);
+      if (la + 1 < a.nlev) __stcs(reinterpret_cast<float2 *>(oo + la), make_float2(o[2 * k], o[2 * k + 1]));
+      else oo[la] = o[2 * k];
+    }
+  };
+  // self terms (su, sv) . (u_i, v_i) of `node`, then the (u, v) halves
+  auto finish_node = [&](int32_t node, const f2_t (&x)[KU][2], const GroupSum<COMP> (&sd)[KU][2],
+                         const GroupSum<COMP> (&sc)[KU][2], float (&r)[2 * KU], float (&z)[2 * KU]) {
+    f2_t sw_div, sw_curl;
+    weights(v.s + rs * (uint32_t)node, sw_div, sw_curl);
+#pragma unroll
+    for (int k = 0; k < KU; ++k)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float x0, y0;
+        upk(sd[k][h].finish(sw_div, x[k][h]), x0, y0);
+        r[2 * k + h] = __fadd_rn(x0, y0);
+        if (FUSED) {
+          upk(sc[k][h].finish(sw_curl, x[k][h]), x0, y0);
+          z[2 * k + h] = __fadd_rn(x0, y0);
+        }
+      }
+  };
+  auto close_all = [&](GroupSum<COMP> (&sd)[KU][2], GroupSum<COMP> (&sc)[KU][2], int which) {
+#pragma unroll
+    for (int k = 0; k < KU; ++k)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (which == 0) sd[k][h].close_first();
+        else if (which == 1) sd[k][h].close_second();
+        else sd[k][h].close();
+        if (FUSED) {
+          if (which == 0) sc[k][h].close_first();
+          else if (which == 1) sc[k][h].close_second();
+          else sc[k][h].close();
+        }
+      }
+  };
   for (uint32_t item = i0 + (threadIdx.x & 31); item < i1; item += 32) {
-    const uint32_t il = (uint32_t)(((uint64_t)item * a.g_magic) >> a.g_shift);
-    const uint32_t c = item - il * G;
+    const uint32_t q = (uint32_t)(((uint64_t)item * a.g_magic) >> a.g_shift);
+    const uint32_t c = item - q * G;
     if (c >= units) continue;  // G * KU may exceed the column's units
-    const int32_t node = v.n0 + (int32_t)il;
-    const int32_t p0 = lds_s32(v.r + 4u * (uint32_t)node), p1 = lds_s32(v.r + 4u * (uint32_t)node + 4u);
+    uint32_t il = q, jl = 0;
+    if (PAIRS && v.p) {
+      const uint32_t sl = lds_u32(v.p + 4u * q);
+      il = (uint32_t)NB_IDX(sl & 0xffffu, 0, n, a.status);
+      jl = (uint32_t)NB_IDX(sl >> 16, 0, n, a.status);
+    }
     // byte offset of each unit in a column; a unit past the column reads
     // unit c again and is not stored
     uint32_t uo[KU];
@@ -270,7 +327,131 @@ __device__ __forceinline__ void divcurl_tile(const A &a, const TileView &v, bool
       has[k] = u < units;
       uo[k] = 16u * (has[k] ? u : c);
     }
+    const int32_t node = v.n0 + (int32_t)il;
     const uint32_t own = v.rows + il * rb;
+    // terms of the staged neighbour column `col` for a node with own values x
+    auto accumulate = [&](GroupSum<COMP> (&sd)[KU][2], GroupSum<COMP> (&sc)[KU][2], const f2_t (&x)[KU][2],
+                          uint32_t col, f2_t wd, f2_t wc, bool first) {
+#pragma unroll
+      for (int k = 0; k < KU; ++k) {
+        f2_t n0, n1;
+        lds2x64(col + uo[k], n0, n1);
+        const f2_t d0 = sub2(n0, x[k][0]), d1 = sub2(n1, x[k][1]);
+        if (first) {
+          sd[k][0].start(wd, d0);
+          sd[k][1].start(wd, d1);
+          if (FUSED) {
+            sc[k][0].start(wc, d0);
+            sc[k][1].start(wc, d1);
+          }
+        } else {
+          sd[k][0].term(wd, d0);
+          sd[k][1].term(wd, d1);
+          if (FUSED) {
+            sc[k][0].term(wc, d0);
+            sc[k][1].term(wc, d1);
+          }
+        }
+      }
+    };
+    if (PAIRS && q < npairs) {
+      // node pair (il, jl): rows (A, B, partner, three others)
+      const int32_t nodej = v.n0 + (int32_t)jl;
+      const uint32_t pi = (uint32_t)lds_s32(v.r + 4u * (uint32_t)node);
+      const uint32_t pj = (uint32_t)lds_s32(v.r + 4u * (uint32_t)nodej);
+      const uint32_t ownj = v.rows + jl * rb;
+      f2_t xi[KU][2], xj[KU][2];
+#pragma unroll
+      for (int k = 0; k < KU; ++k) {
+        lds2x64(own + uo[k], xi[k][0], xi[k][1]);
+        lds2x64(ownj + uo[k], xj[k][0], xj[k][1]);
+      }
+      GroupSum<COMP> sdi[KU][2], sci[KU][2], sdj[KU][2], scj[KU][2];
+      const uint32_t wi = v.w + rs * pi, wj = v.w + rs * pj;
+      const uint32_t li = v.l + 4u * pi, lj = v.l + 4u * pj;
+      // first group of both nodes: the shared neighbours A and B ...
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const uint32_t col = column(li + 4u * e);
+        f2_t wdi, wci, wdj, wcj;
+        weights(wi + rs * e, wdi, wci);
+        weights(wj + rs * e, wdj, wcj);
+#pragma unroll
+        for (int k = 0; k < KU; ++k) {
+          f2_t n0, n1;
+          lds2x64(col + uo[k], n0, n1);
+          const f2_t n[2] = {n0, n1};
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const f2_t di = sub2(n[h], xi[k][h]), dj = sub2(n[h], xj[k][h]);
+            if (e == 0) {
+              sdi[k][h].start(wdi, di);
+              sdj[k][h].start(wdj, dj);
+              if (FUSED) {
+                sci[k][h].start(wci, di);
+                scj[k][h].start(wcj, dj);
+              }
+            } else {
+              sdi[k][h].term(wdi, di);
+              sdj[k][h].term(wdj, dj);
+              if (FUSED) {
+                sci[k][h].term(wci, di);
+                scj[k][h].term(wcj, dj);
+              }
+            }
+          }
+        }
+      }
+      // ... and the partner
+      {
+        f2_t wdi, wci, wdj, wcj;
+        weights(wi + 2u * rs, wdi, wci);
+        weights(wj + 2u * rs, wdj, wcj);
+#pragma unroll
+        for (int k = 0; k < KU; ++k)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const f2_t d = sub2(xj[k][h], xi[k][h]), nd = make_float2(-d.x, -d.y);
+            sdi[k][h].term(wdi, d);
+            sdj[k][h].term(wdj, nd);
+            if (FUSED) {
+              sci[k][h].term(wci, d);
+              scj[k][h].term(wcj, nd);
+            }
+          }
+      }
+      close_all(sdi, sci, 0);
+      close_all(sdj, scj, 0);
+      // second group of node i, then of node j
+#pragma unroll
+      for (int e = 3; e < 6; ++e) {
+        f2_t wd, wc;
+        weights(wi + rs * e, wd, wc);
+        accumulate(sdi, sci, xi, column(li + 4u * e), wd, wc, e == 3);
+      }
+      close_all(sdi, sci, 1);
+      {
+        float r[2 * KU], z[2 * KU];
+        finish_node(node, xi, sdi, sci, r, z);
+        put(a.out + (int64_t)node * a.out_stride, r, c, has);
+        if (FUSED) put(a.out2 + (int64_t)node * a.out_stride, z, c, has);
+      }
+#pragma unroll
+      for (int e = 3; e < 6; ++e) {
+        f2_t wd, wc;
+        weights(wj + rs * e, wd, wc);
+        accumulate(sdj, scj, xj, column(lj + 4u * e), wd, wc, e == 3);
+      }
+      close_all(sdj, scj, 1);
+      {
+        float r[2 * KU], z[2 * KU];
+        finish_node(nodej, xj, sdj, scj, r, z);
+        put(a.out + (int64_t)nodej * a.out_stride, r, c, has);
+        if (FUSED) put(a.out2 + (int64_t)nodej * a.out_stride, z, c, has);
+      }
+      continue;
+    }
+    const int32_t p0 = lds_s32(v.r + 4u * (uint32_t)node), p1 = lds_s32(v.r + 4u * (uint32_t)node + 4u);
     float r[2 * KU], z[2 * KU];
     if (!pole) {
       f2_t x[KU][2];  // own (u, v) at levels 2u and 2u + 1 of each unit
@@ -279,84 +460,33 @@ __device__ __forceinline__ void divcurl_tile(const A &a, const TileView &v, bool
       GroupSum<COMP> sd[KU][2], sc[KU][2];
       // weights of entry e: single pass, 8-byte (w.x, w.y) at pw + 8 e; fused,
       // 16-byte (div, curl) records at pw + 16 e
-      const uint32_t pw = v.w + (FUSED ? 16u : 8u) * (uint32_t)p0;
+      const uint32_t pw = v.w + rs * (uint32_t)p0;
       const uint32_t pl = v.l + 4u * (uint32_t)p0;
       // neighbour entry e: its units minus the node's own, times the weights
       auto nbr = [&](uint32_t e, bool first) {
-        const uint32_t col = v.rows + (uint32_t)NB_IDX(lds_u32(pl + 4u * e), 0, a.col_area, a.status);
-        f2_t wd, wc = 0ull;
-        if (FUSED) lds2x64(pw + 16u * e, wd, wc);
-        else wd = lds_b64(pw + 8u * e);
-#pragma unroll
-        for (int k = 0; k < KU; ++k) {
-          f2_t n0, n1;
-          lds2x64(col + uo[k], n0, n1);
-          const f2_t d0 = sub2(n0, x[k][0]), d1 = sub2(n1, x[k][1]);
-          if (first) {
-            sd[k][0].start(wd, d0);
-            sd[k][1].start(wd, d1);
-            if (FUSED) {
-              sc[k][0].start(wc, d0);
-              sc[k][1].start(wc, d1);
-            }
-          } else {
-            sd[k][0].term(wd, d0);
-            sd[k][1].term(wd, d1);
-            if (FUSED) {
-              sc[k][0].term(wc, d0);
-              sc[k][1].term(wc, d1);
-            }
-          }
-        }
-      };
-      auto close = [&](int which) {  // 0: first group, 1: second of two, 2: later
-#pragma unroll
-        for (int k = 0; k < KU; ++k)
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            if (which == 0) sd[k][h].close_first();
-            else if (which == 1) sd[k][h].close_second();
-            else sd[k][h].close();
-            if (FUSED) {
-              if (which == 0) sc[k][h].close_first();
-              else if (which == 1) sc[k][h].close_second();
-              else sc[k][h].close();
-            }
-          }
+        const uint32_t col = column(pl + 4u * e);
+        f2_t wd, wc;
+        weights(pw + rs * e, wd, wc);
+        accumulate(sd, sc, x, col, wd, wc, first);
       };
       const int deg = p1 - p0;
       if (deg == 6) {
         nbr(0, true), nbr(1, false), nbr(2, false);
-        close(0);
+        close_all(sd, sc, 0);
         nbr(3, true), nbr(4, false), nbr(5, false);
-        close(1);
+        close_all(sd, sc, 1);
       } else {
         int e = 0;
         for (; e + 1 < deg; e += 2) {
           nbr((uint32_t)e, true), nbr((uint32_t)e + 1, false);
-          close(e == 0 ? 0 : 2);
+          close_all(sd, sc, e == 0 ? 0 : 2);
         }
         if (e < deg) {
           nbr((uint32_t)e, true);
-          close(e == 0 ? 0 : 2);
+          close_all(sd, sc, e == 0 ? 0 : 2);
         }
       }
-      // self terms (su, sv) . (u_i, v_i), then the (u, v) halves
-      f2_t sw_div, sw_curl = 0ull;
-      if (FUSED) lds2x64(v.s + 16u * (uint32_t)node, sw_div, sw_curl);
-      else sw_div = lds_b64(v.s + 8u * (uint32_t)node);
-#pragma unroll
-      for (int k = 0; k < KU; ++k)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          float x0, y0;
-          upk(sd[k][h].finish(sw_div, x[k][h]), x0, y0);
-          r[2 * k + h] = __fadd_rn(x0, y0);
-          if (FUSED) {
-            upk(sc[k][h].finish(sw_curl, x[k][h]), x0, y0);
-            z[2 * k + h] = __fadd_rn(x0, y0);
-          }
-        }
+      finish_node(node, x, sd, sc, r, z);
     } else {
       float iu[2 * KU], iv[2 * KU];
 #pragma unroll
@@ -369,8 +499,8 @@ __device__ __forceinline__ void divcurl_tile(const A &a, const TileView &v, bool
       for (int j = 0; j < 2 * KU; ++j) sacc[j] = zacc[j] = 0.0;
       for (int32_t p = p0; p < p1; ++p) {
         const double2 w = __ldg(a.w64 + p);
-        const double2 q = FUSED ? __ldg(a.w64b + p) : w;
-        const uint32_t col = v.rows + (uint32_t)NB_IDX(lds_u32(v.l + 4u * (uint32_t)p), 0, a.col_area, a.status);
+        const double2 qw = FUSED ? __ldg(a.w64b + p) : w;
+        const uint32_t col = column(v.l + 4u * (uint32_t)p);
 #pragma unroll
         for (int k = 0; k < KU; ++k) {
           const float4 C = lds128(col + uo[k]);
@@ -380,7 +510,7 @@ __device__ __forceinline__ void divcurl_tile(const A &a, const TileView &v, bool
             const double du = (double)ju[h] - (double)iu[2 * k + h];
             const double dv = (double)jv[h] - (double)iv[2 * k + h];
             sacc[2 * k + h] = fma(w.y, dv, fma(w.x, du, sacc[2 * k + h]));
-            if (FUSED) zacc[2 * k + h] = fma(q.y, dv, fma(q.x, du, zacc[2 * k + h]));
+            if (FUSED) zacc[2 * k + h] = fma(qw.y, dv, fma(qw.x, du, zacc[2 * k + h]));
           }
         }
       }
@@ -392,18 +522,8 @@ __device__ __forceinline__ void divcurl_tile(const A &a, const TileView &v, bool
         if (FUSED) z[j] = (float)fma(sx.y, (double)iv[j], fma(sx.x, (double)iu[j], zacc[j]));
       }
     }
-    // unit k holds levels 2u, 2u + 1 (u = c + k G)
-    auto put = [&](float *oo, const float (&o)[2 * KU]) {
-#pragma unroll
-      for (int k = 0; k < KU; ++k) {
-        if (!has[k]) continue;
-        const int la = 2 * (int)(c + (uint32_t)k * G);
-        if (la + 1 < a.nlev) __stcs(reinterpret_cast<float2 *>(oo + la), make_float2(o[2 * k], o[2 * k + 1]));
-        else oo[la] = o[2 * k];
-      }
-    };
-    put(a.out + (int64_t)node * a.out_stride, r);
-    if (FUSED) put(a.out2 + (int64_t)node * a.out_stride, z);
+    put(a.out + (int64_t)node * a.out_stride, r, c, has);
+    if (FUSED) put(a.out2 + (int64_t)node * a.out_stride, z, c, has);
   }
 }
 
@@ -417,6 +537,6 @@ EncodeTiledFn encode_fn();  // cuTensorMapEncodeTiled from the driver (NULL if m
 void magic_div(uint32_t d, uint64_t &magic, uint32_t &shift);
 int sm_count(int *out);
 // item shape of the div / curl consumers (KU units per item, G items per node)
-void item_shape(int units_req, int align_req, int units, bool fused, int &KU, int &G);
+void item_shape(int units_req, int align_req, int units, int &KU, int &G);
 
 }  // namespace nb

@@ -73,6 +73,12 @@ struct TiledArgs {
   uint64_t timeout_ns;  // limit of every pipeline wait (the method's wait limit)
   int32_t nnodes;       // nodes of the mesh (index checks)
   uint32_t col_area;    // staged column offsets lie below this (index checks)
+  // node pairs (div / curl): tile t's slot list is slots[slot_ptr[t] ..
+  // slot_ptr[t + 1]), its first npairs[t] slots pairs; off_p = 0: no pairs
+  const int32_t *slot_ptr;
+  const int32_t *npairs;
+  const uint32_t *slots;
+  uint32_t off_p;       // stage offset of the slot list
 };
 
 // What the producer reads from global memory to issue a tile's copies: its
@@ -81,6 +87,7 @@ struct TiledArgs {
 // stage to be released, so that a release is followed at once by the copies.
 struct TilePrep {
   int32_t n0, n1, h0, h1, pa, pb;
+  int32_t qa, qb, np;  // slot list range and pair count (node pairs only)
   int32_t y[4];  // halo nodes of group `lane` (when the tile has that group)
 };
 
@@ -92,6 +99,12 @@ __device__ __forceinline__ TilePrep prepare_tile(const TiledArgs &a, int t, int 
   p.h1 = __ldg(a.halo_ptr + t + 1);
   p.pa = __ldg(a.row_ptr + p.n0);
   p.pb = __ldg(a.row_ptr + p.n1);
+  p.qa = p.qb = p.np = 0;
+  if (a.off_p) {
+    p.qa = __ldg(a.slot_ptr + t);
+    p.qb = __ldg(a.slot_ptr + t + 1);
+    p.np = __ldg(a.npairs + t);
+  }
   const uint32_t H = (uint32_t)(p.h1 - p.h0);
   if ((uint32_t)lane < ((H + 3u) >> 2)) {
     // a short last group repeats its last node (the copy fills the group's slots)
@@ -120,18 +133,21 @@ __device__ __forceinline__ void issue_tile(const TiledArgs &a, const CUtensorMap
   const uint32_t hbase = (n * a.row_bytes + 127u) & ~127u;
   const int32_t sa = a.rec16 ? n0 : (n0 & ~1), sb = a.rec16 ? n1 : ((n1 + 1) & ~1);
   const uint32_t sbytes = a.off_s ? (uint32_t)(sb - sa) * (a.rec16 ? 16u : 8u) : 0u;
+  const uint32_t pbytes = (uint32_t)(p.qb - p.qa) * 4u;  // a multiple of 16 (lists padded to 4 slots)
 #ifdef NB_BOUNDS_CHECK
   // a tile whose copies would leave their stage regions is not copied: it is
   // published empty and NB_EINVAL is recorded
   {
-    const uint32_t send = a.off_s ? a.off_s : a.off_h;
+    const uint32_t send = a.off_s ? a.off_s : a.off_p ? a.off_p : a.off_h;
+    const uint32_t pend = a.off_p ? a.off_p : a.off_h;
     const bool bad = n1 <= n0 || n1 > a.nnodes || h1 < h0 || hbase + groups * a.gpitch > a.off_w ||
                      a.off_w + wbytes > a.off_l || a.off_l + lbytes > a.off_r || a.off_r + rbytes > send ||
-                     (a.off_s && a.off_s + sbytes > a.off_h);
+                     (a.off_s && a.off_s + sbytes > pend) || (a.off_p && a.off_p + pbytes > a.off_h) ||
+                     p.np < 0 || 2 * p.np > (int32_t)n || (a.off_p && 4u * (n - (uint32_t)p.np) > pbytes);
     if (bad) {
       if (lane == 0) {
         atomicCAS(a.status, 0, (int)NB_EINVAL);
-        asm volatile("st.shared.v2.s32 [%0], {%1, %1};" ::"r"(stage + a.off_h), "r"(n0) : "memory");
+        asm volatile("st.shared.v4.s32 [%0], {%1, %1, %2, %2};" ::"r"(stage + a.off_h), "r"(n0), "r"(0) : "memory");
         mbar_expect_tx(bar, 0);
       }
       __syncwarp();
@@ -141,11 +157,13 @@ __device__ __forceinline__ void issue_tile(const TiledArgs &a, const CUtensorMap
 #endif
   if (lane == 0) {
     // header for the consumers, published by the arrive below
-    asm volatile("st.shared.v2.s32 [%0], {%1, %2};" ::"r"(stage + a.off_h), "r"(n0), "r"(n1) : "memory");
+    asm volatile("st.shared.v4.s32 [%0], {%1, %2, %3, %4};" ::"r"(stage + a.off_h), "r"(n0), "r"(n1), "r"(p.np),
+                 "r"(0)
+                 : "memory");
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   if (lane == 0)
-    mbar_expect_tx(bar, body + wbytes + lbytes + rbytes + sbytes + groups * 4u * a.copy_bytes);
+    mbar_expect_tx(bar, body + wbytes + lbytes + rbytes + sbytes + pbytes + groups * 4u * a.copy_bytes);
   __syncwarp();
   if (lane == 0) bulk_g2s(stage, a.in + (int64_t)n0 * a.in_stride * 4, body, bar);
   if (lane == 1) {
@@ -158,6 +176,7 @@ __device__ __forceinline__ void issue_tile(const TiledArgs &a, const CUtensorMap
     if (a.rec16) bulk_g2s(stage + a.off_s, a.s4 + sa, sbytes, bar);
     else bulk_g2s(stage + a.off_s, a.s32 + sa, sbytes, bar);
   }
+  if (lane == 5 && pbytes) bulk_g2s(stage + a.off_p, a.slots + p.qa, pbytes, bar);
   if ((uint32_t)lane < groups)
     gather4_g2s(stage + hbase + (uint32_t)lane * a.gpitch, map, p.y[0], p.y[1], p.y[2], p.y[3], bar);
   for (uint32_t g = (uint32_t)lane + 32u; g < groups; g += 32) {
@@ -182,96 +201,50 @@ __device__ __forceinline__ TileView staged_view(const TiledArgs &a, uint32_t sta
   const int32_t pa = lds_s32(v.r + 4u * (uint32_t)v.n0);
   v.w = a.rec16 ? stage + a.off_w - 16u * (uint32_t)pa : stage + a.off_w - 8u * (uint32_t)(pa & ~1);
   v.l = stage + a.off_l - 4u * (uint32_t)(pa & ~3);
+  v.p = a.off_p ? stage + a.off_p : 0u;
+  v.npairs = lds_s32(stage + a.off_h + 8u);
   return v;
 }
 
-// grad.  Item c of a node takes the 4-level unit c of its scalar column;
-// each weight is broadcast to both lanes of a packed register.
-template <bool COMP>
+// grad.  Item c of a slot takes the 4-level unit c of its scalar column;
+// each weight is broadcast to both lanes of a packed register.  A node pair
+// slot (see divcurl_tile) evaluates both nodes from 10 staged columns: the
+// shared neighbours A and B and the partner first, then each node's other
+// three, every node's terms in its row order as on the single-node path.
+// PAIRS = false compiles it without the slot list and pair path.
+template <bool COMP, bool PAIRS>
 __device__ __forceinline__ void grad_tile(const TiledArgs &a, int t, uint32_t stage, int part,
                                           int nparts) {
   const TileView v = staged_view(a, stage);
-  const uint32_t items = (uint32_t)(v.n1 - v.n0) * a.G;
+  const uint32_t n = (uint32_t)(v.n1 - v.n0);
+  const uint32_t npairs = (PAIRS && v.p) ? (uint32_t)v.npairs : 0u;
+  const uint32_t items = (n - npairs) * a.G;
   const uint32_t i0 = (uint32_t)(((uint64_t)items * part) / nparts);
   const uint32_t i1 = (uint32_t)(((uint64_t)items * (part + 1)) / nparts);
   const bool pole = t >= a.ntiles_main;
   const uint32_t rb = a.row_bytes;
-  for (uint32_t item = i0 + (threadIdx.x & 31); item < i1; item += 32) {
-    const uint32_t il = (uint32_t)(((uint64_t)item * a.g_magic) >> a.g_shift);
-    const uint32_t c = item - il * a.G;
-    const int l0 = 4 * (int)c;
-    const int32_t node = v.n0 + (int32_t)il;
-    const int32_t p0 = lds_s32(v.r + 4u * (uint32_t)node), p1 = lds_s32(v.r + 4u * (uint32_t)node + 4u);
-    const uint32_t col = v.rows + c * 16u;
-    float gx[4], gy[4];
-    if (!pole) {
-      f2_t fi01, fi23;
-      lds2x64(col + il * rb, fi01, fi23);
-      GroupSum<COMP> ax01, ax23, ay01, ay23;
-      const uint32_t pw = v.w + 8u * (uint32_t)p0, pl = v.l + 4u * (uint32_t)p0;
-      auto nbr = [&](uint32_t q, bool first) {
-        const float2 w = lds64(pw + 8u * q);
-        f2_t f01, f23;
-        lds2x64(col + (uint32_t)NB_IDX(lds_u32(pl + 4u * q), 0, a.col_area, a.status), f01, f23);
-        const f2_t a01 = sub2(f01, fi01), a23 = sub2(f23, fi23);
-        const f2_t wx = pk(w.x, w.x), wy = pk(w.y, w.y);
-        if (first) {
-          ax01.start(wx, a01), ax23.start(wx, a23), ay01.start(wy, a01), ay23.start(wy, a23);
-        } else {
-          ax01.term(wx, a01), ax23.term(wx, a23), ay01.term(wy, a01), ay23.term(wy, a23);
-        }
-      };
-      auto close = [&](int which) {  // 0: first group, 1: second of two, 2: later
-        GroupSum<COMP> *acc[4] = {&ax01, &ax23, &ay01, &ay23};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          if (which == 0) acc[j]->close_first();
-          else if (which == 1) acc[j]->close_second();
-          else acc[j]->close();
-        }
-      };
-      const int deg = p1 - p0;
-      if (deg == 6) {
-        nbr(0, true), nbr(1, false), nbr(2, false);
-        close(0);
-        nbr(3, true), nbr(4, false), nbr(5, false);
-        close(1);
-      } else {
-        int q = 0;
-        for (; q + 1 < deg; q += 2) {
-          nbr((uint32_t)q, true), nbr((uint32_t)q + 1, false);
-          close(q == 0 ? 0 : 2);
-        }
-        if (q < deg) {
-          nbr((uint32_t)q, true);
-          close(q == 0 ? 0 : 2);
-        }
-      }
-      upk(ax01.finish(), gx[0], gx[1]);
-      upk(ax23.finish(), gx[2], gx[3]);
-      upk(ay01.finish(), gy[0], gy[1]);
-      upk(ay23.finish(), gy[2], gy[3]);
+  struct Acc {
+    GroupSum<COMP> x01, x23, y01, y23;
+  };
+  // terms w (f_j - f_i) of one neighbour, four levels
+  auto term = [](Acc &s, float2 w, f2_t d01, f2_t d23, bool first) {
+    const f2_t wx = pk(w.x, w.x), wy = pk(w.y, w.y);
+    if (first) {
+      s.x01.start(wx, d01), s.x23.start(wx, d23), s.y01.start(wy, d01), s.y23.start(wy, d23);
     } else {
-      const float4 fi = lds128(col + il * rb);
-      double sx[4] = {0, 0, 0, 0}, sy[4] = {0, 0, 0, 0};
-      const float fiv[4] = {fi.x, fi.y, fi.z, fi.w};
-      for (int32_t p = p0; p < p1; ++p) {
-        const double2 w = __ldg(a.w64 + p);
-        const float4 fj = lds128(col + (uint32_t)NB_IDX(lds_u32(v.l + 4u * (uint32_t)p), 0, a.col_area, a.status));
-        const float fjv[4] = {fj.x, fj.y, fj.z, fj.w};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const double d = (double)fjv[k] - (double)fiv[k];
-          sx[k] = fma(w.x, d, sx[k]);
-          sy[k] = fma(w.y, d, sy[k]);
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        gx[k] = (float)sx[k];
-        gy[k] = (float)sy[k];
-      }
+      s.x01.term(wx, d01), s.x23.term(wx, d23), s.y01.term(wy, d01), s.y23.term(wy, d23);
     }
+  };
+  auto close = [](Acc &s, int which) {  // 0: first group, 1: second of two, 2: later
+    GroupSum<COMP> *acc[4] = {&s.x01, &s.x23, &s.y01, &s.y23};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (which == 0) acc[j]->close_first();
+      else if (which == 1) acc[j]->close_second();
+      else acc[j]->close();
+    }
+  };
+  auto store = [&](int32_t node, int l0, const float (&gx)[4], const float (&gy)[4]) {
     float *go = a.out + (int64_t)node * a.out_stride + 2 * l0;
     if (l0 + 4 <= a.nlev) {
       __stcs(reinterpret_cast<float4 *>(go), make_float4(gx[0], gy[0], gx[1], gy[1]));
@@ -283,6 +256,123 @@ __device__ __forceinline__ void grad_tile(const TiledArgs &a, int t, uint32_t st
           go[2 * k] = gx[k];
           go[2 * k + 1] = gy[k];
         }
+    }
+  };
+  auto finish = [&](int32_t node, int l0, const Acc &s) {
+    float gx[4], gy[4];
+    upk(s.x01.finish(), gx[0], gx[1]);
+    upk(s.x23.finish(), gx[2], gx[3]);
+    upk(s.y01.finish(), gy[0], gy[1]);
+    upk(s.y23.finish(), gy[2], gy[3]);
+    store(node, l0, gx, gy);
+  };
+  for (uint32_t item = i0 + (threadIdx.x & 31); item < i1; item += 32) {
+    const uint32_t q = (uint32_t)(((uint64_t)item * a.g_magic) >> a.g_shift);
+    const uint32_t c = item - q * a.G;
+    const int l0 = 4 * (int)c;
+    uint32_t il = q, jl = 0;
+    if (PAIRS && v.p) {
+      const uint32_t sl = lds_u32(v.p + 4u * q);
+      il = (uint32_t)NB_IDX(sl & 0xffffu, 0, n, a.status);
+      jl = (uint32_t)NB_IDX(sl >> 16, 0, n, a.status);
+    }
+    const int32_t node = v.n0 + (int32_t)il;
+    const uint32_t col = v.rows + c * 16u;
+    auto column = [&](uint32_t at) { return col + (uint32_t)NB_IDX(lds_u32(at), 0, a.col_area, a.status); };
+    if (PAIRS && q < npairs) {
+      // node pair (il, jl): rows (A, B, partner, three others)
+      const int32_t nodej = v.n0 + (int32_t)jl;
+      const uint32_t pi = (uint32_t)lds_s32(v.r + 4u * (uint32_t)node);
+      const uint32_t pj = (uint32_t)lds_s32(v.r + 4u * (uint32_t)nodej);
+      f2_t xi01, xi23, xj01, xj23;
+      lds2x64(col + il * rb, xi01, xi23);
+      lds2x64(col + jl * rb, xj01, xj23);
+      Acc si, sj;
+      const uint32_t wi = v.w + 8u * pi, wj = v.w + 8u * pj, li = v.l + 4u * pi, lj = v.l + 4u * pj;
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        f2_t f01, f23;
+        lds2x64(column(li + 4u * e), f01, f23);
+        term(si, lds64(wi + 8u * e), sub2(f01, xi01), sub2(f23, xi23), e == 0);
+        term(sj, lds64(wj + 8u * e), sub2(f01, xj01), sub2(f23, xj23), e == 0);
+      }
+      {
+        const f2_t d01 = sub2(xj01, xi01), d23 = sub2(xj23, xi23);
+        term(si, lds64(wi + 16u), d01, d23, false);
+        term(sj, lds64(wj + 16u), make_float2(-d01.x, -d01.y), make_float2(-d23.x, -d23.y), false);
+      }
+      close(si, 0);
+      close(sj, 0);
+#pragma unroll
+      for (int e = 3; e < 6; ++e) {
+        f2_t f01, f23;
+        lds2x64(column(li + 4u * e), f01, f23);
+        term(si, lds64(wi + 8u * e), sub2(f01, xi01), sub2(f23, xi23), e == 3);
+      }
+      close(si, 1);
+      finish(node, l0, si);
+#pragma unroll
+      for (int e = 3; e < 6; ++e) {
+        f2_t f01, f23;
+        lds2x64(column(lj + 4u * e), f01, f23);
+        term(sj, lds64(wj + 8u * e), sub2(f01, xj01), sub2(f23, xj23), e == 3);
+      }
+      close(sj, 1);
+      finish(nodej, l0, sj);
+      continue;
+    }
+    const int32_t p0 = lds_s32(v.r + 4u * (uint32_t)node), p1 = lds_s32(v.r + 4u * (uint32_t)node + 4u);
+    if (!pole) {
+      f2_t fi01, fi23;
+      lds2x64(col + il * rb, fi01, fi23);
+      Acc s;
+      const uint32_t pw = v.w + 8u * (uint32_t)p0, pl = v.l + 4u * (uint32_t)p0;
+      auto nbr = [&](uint32_t e, bool first) {
+        const float2 w = lds64(pw + 8u * e);
+        f2_t f01, f23;
+        lds2x64(column(pl + 4u * e), f01, f23);
+        term(s, w, sub2(f01, fi01), sub2(f23, fi23), first);
+      };
+      const int deg = p1 - p0;
+      if (deg == 6) {
+        nbr(0, true), nbr(1, false), nbr(2, false);
+        close(s, 0);
+        nbr(3, true), nbr(4, false), nbr(5, false);
+        close(s, 1);
+      } else {
+        int e = 0;
+        for (; e + 1 < deg; e += 2) {
+          nbr((uint32_t)e, true), nbr((uint32_t)e + 1, false);
+          close(s, e == 0 ? 0 : 2);
+        }
+        if (e < deg) {
+          nbr((uint32_t)e, true);
+          close(s, e == 0 ? 0 : 2);
+        }
+      }
+      finish(node, l0, s);
+    } else {
+      const float4 fi = lds128(col + il * rb);
+      double sx[4] = {0, 0, 0, 0}, sy[4] = {0, 0, 0, 0};
+      const float fiv[4] = {fi.x, fi.y, fi.z, fi.w};
+      for (int32_t p = p0; p < p1; ++p) {
+        const double2 w = __ldg(a.w64 + p);
+        const float4 fj = lds128(column(v.l + 4u * (uint32_t)p));
+        const float fjv[4] = {fj.x, fj.y, fj.z, fj.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const double d = (double)fjv[k] - (double)fiv[k];
+          sx[k] = fma(w.x, d, sx[k]);
+          sy[k] = fma(w.y, d, sy[k]);
+        }
+      }
+      float gx[4], gy[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        gx[k] = (float)sx[k];
+        gy[k] = (float)sy[k];
+      }
+      store(node, l0, gx, gy);
     }
   }
 }
@@ -327,7 +417,7 @@ __device__ __forceinline__ int tile_at(const TiledArgs &a, int i) {
 // of this CTA's walk into it ("full" barrier, transaction count).  Each of
 // the W consumer warps waits for "full", computes its 1/W share of the
 // tile's items and releases the stage; no block-wide barrier is used.
-template <int OP, bool COMP, int KU>
+template <int OP, bool COMP, int KU, bool PAIRS>
 __global__ void __launch_bounds__(StagedShape<OP>::threads, 1)
     staged_f32(const TiledArgs a, const __grid_constant__ CUtensorMap map) {
   constexpr int W = StagedShape<OP>::warps;
@@ -388,9 +478,10 @@ __global__ void __launch_bounds__(StagedShape<OP>::threads, 1)
       break;
     }
     const uint32_t rows = stage0 + (uint32_t)s * a.stage_bytes;
-    if (OP == 0) grad_tile<COMP>(a, t, rows, warp, W);
-    else if (OP == 1) divcurl_tile<COMP, false, KU>(a, staged_view(a, rows), t >= a.ntiles_main, a.row_bytes, warp, W);
-    else divcurl_tile<COMP, true, KU>(a, staged_view(a, rows), t >= a.ntiles_main, a.row_bytes, warp, W);
+    if (OP == 0) grad_tile<COMP, PAIRS>(a, t, rows, warp, W);
+    else if (OP == 1)
+      divcurl_tile<COMP, false, KU, PAIRS>(a, staged_view(a, rows), t >= a.ntiles_main, a.row_bytes, warp, W);
+    else divcurl_tile<COMP, true, KU, PAIRS>(a, staged_view(a, rows), t >= a.ntiles_main, a.row_bytes, warp, W);
     __syncwarp();
     if (lane == 0) mbar_arrive(empty0 + 8 * s);
   }
@@ -423,6 +514,34 @@ static int plan_upload(TilePlan *tp, nb_method *m) {
   loff.resize(loff.size() + 8, 0);  // slack for 16-byte bounding copies
   if (halo.empty()) halo.push_back(0);
   tp->ntiles = (int)node0.size() - 1;
+  // slot lists: the tile's node pairs (both nodes own nodes of the tile),
+  // then its other nodes, each list padded to a multiple of 4 slots
+  std::vector<int32_t> sptr(tp->ntiles + 1, 0), npairs(tp->ntiles, 0);
+  std::vector<uint32_t> slots;
+  slots.reserve(mesh->V + 4 * (size_t)tp->ntiles);
+  for (int t = 0; t < tp->ntiles; ++t) {
+    const int32_t a = node0[t], b = node0[t + 1];
+    sptr[t] = (int32_t)slots.size();
+    for (int32_t k = a; k < b; ++k) {
+      const int32_t j = mesh->mate[k];
+      if (j > k && j < b) slots.push_back((uint32_t)(k - a) | (uint32_t)(j - a) << 16);
+    }
+    npairs[t] = (int32_t)slots.size() - sptr[t];
+    tp->paired_nodes += 2 * npairs[t];
+    for (int32_t k = a; k < b; ++k) {
+      const int32_t j = mesh->mate[k];
+      if (!(j >= a && j < b)) slots.push_back((uint32_t)(k - a) * 0x10001u);
+    }
+    while (slots.size() % 4) slots.push_back(0);
+  }
+  sptr[tp->ntiles] = (int32_t)slots.size();
+  {
+    std::string why;
+    if (!check_slot_lists(mesh, tp->ntiles, node0.data(), sptr.data(), npairs.data(), slots.data(), why)) {
+      set_error("staged kernel: invalid slot list (" + why + ")");
+      return NB_EINVAL;
+    }
+  }
   log_msg(1, "staged plan: %d tiles (%d pole-row), column pitch %lld B, stage area %lld B, largest halo %d, "
           "%zu halo columns in all", tp->ntiles, tp->ntiles - tp->ntiles_main, (long long)tp->row_bytes,
           (long long)tp->area, tp->max_halo, halo.size());
@@ -440,6 +559,10 @@ static int plan_upload(TilePlan *tp, nb_method *m) {
   if ((st = up((void **)&tp->d_halo_ptr, hptr.data(), hptr.size() * 4))) return st;
   if ((st = up((void **)&tp->d_halo, halo.data(), halo.size() * 4))) return st;
   if ((st = up((void **)&tp->d_loff, loff.data(), loff.size() * 4))) return st;
+  if ((st = up((void **)&tp->d_slot_ptr, sptr.data(), sptr.size() * 4))) return st;
+  if ((st = up((void **)&tp->d_npairs, npairs.data(), npairs.size() * 4))) return st;
+  if ((st = up((void **)&tp->d_slots, slots.data(), slots.size() * 4))) return st;
+  log_msg(1, "staged plan: %lld of %lld nodes in pair slots", (long long)tp->paired_nodes, (long long)mesh->V);
   return NB_OK;
 }
 
@@ -496,20 +619,30 @@ void magic_div(uint32_t d, uint64_t &magic, uint32_t &shift) {
   magic = ((1ull << shift) + d - 1) / d;
 }
 
-template <int OP, bool COMP, int KU>
+template <int OP, bool COMP, int KU, bool PAIRS>
 static int launch_staged_t(const TiledArgs &a, const CUtensorMap &map, int grid, size_t smem,
                            cudaStream_t st) {
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [&] {
-    attr_err = cudaFuncSetAttribute(staged_f32<OP, COMP, KU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    attr_err = cudaFuncSetAttribute(staged_f32<OP, COMP, KU, PAIRS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     227 * 1024);
   });
   NB_CUDA(attr_err);
-  staged_f32<OP, COMP, KU><<<grid, StagedShape<OP>::threads, smem, st>>>(a, map);
+  staged_f32<OP, COMP, KU, PAIRS><<<grid, StagedShape<OP>::threads, smem, st>>>(a, map);
   count_launch(1);
   NB_CUDA(cudaGetLastError());
   return NB_OK;
+}
+
+template <int OP, int KU>
+static int launch_staged_sel(bool comp, bool pairs, const TiledArgs &a, const CUtensorMap &map, int grid,
+                             size_t smem, cudaStream_t st) {
+  if (comp)
+    return pairs ? launch_staged_t<OP, true, KU, true>(a, map, grid, smem, st)
+                 : launch_staged_t<OP, true, KU, false>(a, map, grid, smem, st);
+  return pairs ? launch_staged_t<OP, false, KU, true>(a, map, grid, smem, st)
+               : launch_staged_t<OP, false, KU, false>(a, map, grid, smem, st);
 }
 
 static int g_sm_count = 0;
@@ -527,21 +660,14 @@ int sm_count(int *out) {
 // Item shape of the div / curl consumers for a column of `units` 16-byte
 // units: KU units per item, G items per node.  units_req 2 or 3 fixes KU,
 // align_req 1 (0) asks for G rounded up to a multiple of 8 (not rounded).
-// Left to the library (0 / -1): the fused pass keeps KU = 2 with G not
-// rounded (timed on B300 at O1280 x 137: 3.88 ms against 3.92 ms with KU = 3
-// and G = 24; its two sets of sums need ~30 more registers a thread at
-// KU = 3); the single operators take the shape with the fewest shared-memory
-// wavefronts per node, (G / 32) (22 + 28 KU f): per warp-wide item ~22 for
-// its row pointers, offsets and weights, 28 per unit for its seven 16-byte
-// column loads, and f = 1.25 when quarter-warps can span two nodes (bank
-// conflict replays), else 1 (timed: 2.81 ms with KU = 3, G = 24, against
-// 2.97 ms with KU = 2, G = 35).
-void item_shape(int units_req, int align_req, int units, bool fused, int &KU, int &G) {
-  if (fused && units_req == 0 && align_req < 0) {
-    KU = 2;
-    G = (units + 1) / 2;
-    return;
-  }
+// Left to the library (0 / -1), the shape with the fewest shared-memory
+// wavefronts per node is taken, (G / 32) (22 + 28 KU f): per warp-wide item
+// ~22 for its row pointers, offsets and weights, 28 per unit for its seven
+// 16-byte column loads, and f = 1.25 when quarter-warps can span two nodes
+// (bank-conflict replays), else 1.  At 137 levels that is KU = 3, G = 24,
+// timed on B300 at O1280 x 137: div 2.60 against 2.82 ms with KU = 2,
+// G = 35, and div+curl 3.67 against 3.69 ms.
+void item_shape(int units_req, int align_req, int units, int &KU, int &G) {
   double best = 1e30;
   for (int ku = 2; ku <= 3; ++ku) {
     if (units_req && units_req != ku) continue;
@@ -596,7 +722,7 @@ int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, 
   // items per node: grad, one 4-level unit per item; div / curl, KU 2-level
   // units per item (item_shape)
   int KU = 1, G = (in->nlev + 3) / 4;
-  if (nvar == 2) item_shape(m->item_units, m->item_align, (in->nlev + 1) / 2, fused, KU, G);
+  if (nvar == 2) item_shape(m->item_units, m->item_align, (in->nlev + 1) / 2, KU, G);
   // each 16-byte unit must lie inside the staged column
   if ((uint64_t)(nvar == 2 ? (in->nlev + 1) / 2 : G) * 16u > row_bytes) return NB_OK;
   const uint32_t copy_bytes = (uint32_t)(((int64_t)in->nlev * nvar * 4 + 15) / 16 * 16);
@@ -622,7 +748,15 @@ int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, 
   const uint32_t wsz = up16((uint32_t)(ecap + 2) * rec), lsz = up16((uint32_t)(ecap + 8) * 4u),
                  rsz = up16((uint32_t)(nmax + 8) * 4u);
   const uint32_t ssz = op == NB_OP_GRAD ? 0u : up16((uint32_t)(nmax + 2) * rec), hsz = 16u;
-  const uint32_t meta = wsz + lsz + rsz + ssz + hsz;
+  // slot list of the node pairs: at most nmax slots plus padding.  By
+  // default (-1) every pass but the fused div+curl evaluates node pairs:
+  // timed at O1280 x 137, pairs took grad from 2.14 to 2.03 ms and div from
+  // 2.67 to 2.39 ms, while the fused pass, whose two sets of sums leave
+  // fewer registers for a second node (157-168 a thread), ran 3.78 ms with
+  // pairs against 3.66 ms without.
+  const bool pairs = m->node_pairs > 0 || (m->node_pairs < 0 && !fused);
+  const uint32_t psz = pairs ? up16((uint32_t)(nmax + 4) * 4u) : 0u;
+  const uint32_t meta = wsz + lsz + rsz + ssz + psz + hsz;
   if (stage_target <= meta + 4096u) return NB_OK;
   const uint32_t area = ((stage_target - meta) / 128u) * 128u;
   if (area < 24u * row_bytes) return NB_OK;  // columns too tall to stage a useful tile
@@ -682,7 +816,11 @@ int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, 
   a.off_l = a.off_w + wsz;
   a.off_r = a.off_l + lsz;
   a.off_s = ssz ? a.off_r + rsz : 0u;
-  a.off_h = a.off_r + rsz + ssz;
+  a.off_p = psz ? a.off_r + rsz + ssz : 0u;
+  a.off_h = a.off_r + rsz + ssz + psz;
+  a.slot_ptr = tp->d_slot_ptr;
+  a.npairs = tp->d_npairs;
+  a.slots = tp->d_slots;
   a.stage_bytes = (a.off_h + hsz + 127u) & ~127u;
   a.nstages = nstages;
   a.status = nullptr;
@@ -696,19 +834,17 @@ int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, 
     return NB_EINVAL;
   }
   const int grid = std::min(tp->ntiles, g_sm_count);
-  log_msg(2, "staged launch: op %d%s, %d levels x %d vars, %d units per item, %d items per node, %d tiles, "
-          "grid %d, %zu B shared", op, fused ? " (div+curl)" : "", in->nlev, nvar, KU, G, tp->ntiles, grid, smem);
+  log_msg(2, "staged launch: op %d%s, %d levels x %d vars, %d units per item, %d items per slot, %d tiles, "
+          "grid %d, %zu B shared, node pairs %s", op, fused ? " (div+curl)" : "", in->nlev, nvar, KU, G, tp->ntiles,
+          grid, smem, pairs ? "on" : "off");
   *handled = true;
   const bool comp = comp_mode < 0 ? m->compensated != 0 : comp_mode != 0;
-  if (g) return comp ? launch_staged_t<0, true, 1>(a, map, grid, smem, st) : launch_staged_t<0, false, 1>(a, map, grid, smem, st);
-  if (fused) {
-    if (KU == 3)
-      return comp ? launch_staged_t<2, true, 3>(a, map, grid, smem, st) : launch_staged_t<2, false, 3>(a, map, grid, smem, st);
-    return comp ? launch_staged_t<2, true, 2>(a, map, grid, smem, st) : launch_staged_t<2, false, 2>(a, map, grid, smem, st);
-  }
-  if (KU == 3)
-    return comp ? launch_staged_t<1, true, 3>(a, map, grid, smem, st) : launch_staged_t<1, false, 3>(a, map, grid, smem, st);
-  return comp ? launch_staged_t<1, true, 2>(a, map, grid, smem, st) : launch_staged_t<1, false, 2>(a, map, grid, smem, st);
+  if (g) return launch_staged_sel<0, 1>(comp, pairs, a, map, grid, smem, st);
+  if (fused)
+    return KU == 3 ? launch_staged_sel<2, 3>(comp, pairs, a, map, grid, smem, st)
+                   : launch_staged_sel<2, 2>(comp, pairs, a, map, grid, smem, st);
+  return KU == 3 ? launch_staged_sel<1, 3>(comp, pairs, a, map, grid, smem, st)
+                 : launch_staged_sel<1, 2>(comp, pairs, a, map, grid, smem, st);
 }
 
 int device_status(int clear, int *code) {

@@ -104,6 +104,7 @@ SIGNATURES = {
     "nb_mesh_lap_plan": [_P, _I] + [ctypes.POINTER(ctypes.c_int32)] * 4,
     "nb_check_tile_plan": [_P, ctypes.c_int32, _P, _P, _P, _P],
     "nb_mesh_csr": [_P, _P, _P],
+    "nb_mesh_node_pairs": [_P, _P],
     "nb_mesh_tile_plan": [_P, _I, _I, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                           _I64P, _P, _P, _P, _P],
     "nb_method_create": [_P, ctypes.c_double, ctypes.POINTER(_P)],
@@ -115,6 +116,7 @@ SIGNATURES = {
     "nb_method_set_staging": [_P, _I, _I],
     "nb_method_set_wait_limit": [_P, ctypes.c_int64],
     "nb_method_set_item_shape": [_P, _I, _I],
+    "nb_method_set_node_pairs": [_P, _I],
     "nb_method_set_laplacian_route": [_P, _I],
     "nb_fs_nodecolumns": [_P, _I, _I, ctypes.POINTER(_P)],
     "nb_fs_release": [_P],
@@ -358,6 +360,12 @@ class Mesh(_Handle):
         check(lib().nb_mesh_csr(self._h, rp.ctypes.data, nb.ctypes.data))
         return rp, nb
 
+    def node_pairs(self) -> np.ndarray:
+        """Partner of every paired node (-1: unpaired), functionspace order."""
+        mate = np.zeros(self.V, dtype=np.int32)
+        check(lib().nb_mesh_node_pairs(self._h, mate.ctypes.data))
+        return mate
+
     def lap_plan(self, nlev: int):
         """(tiles, main tiles, max g-nodes, fits) of the single-pass
         Laplacian's plan for FP32 columns of nlev levels (host only)."""
@@ -428,6 +436,12 @@ class Method(_Handle):
         """Item shape of the staged div / curl kernels (0 / -1: chosen by
         the library); see nb_method_set_item_shape."""
         check(lib().nb_method_set_item_shape(self._h, int(units), int(aligned)))
+
+    def set_node_pairs(self, mode: int = -1) -> None:
+        """Node pairs in the staged kernels: 1 in every pass, 0 in none, -1
+        (the default) in all but the fused div+curl pass; see
+        nb_method_set_node_pairs."""
+        check(lib().nb_method_set_node_pairs(self._h, int(mode)))
 
     def set_wait_limit(self, limit_ns: int = -1) -> None:
         """Limit of the staged kernels' pipeline waits in ns (-1 = default

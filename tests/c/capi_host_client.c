@@ -53,13 +53,24 @@ int main(int argc, char **argv) {
   int64_t *row_ptr = (int64_t *)malloc(sizeof(int64_t) * (size_t)(V + 1));
   int32_t *nbr = (int32_t *)malloc(sizeof(int32_t) * (size_t)(2 * ne));
   nb_mesh_csr(mesh, row_ptr, nbr);
+  int32_t *mate = (int32_t *)malloc(sizeof(int32_t) * (size_t)V);
+  check(nb_mesh_node_pairs(mesh, mate) == NB_OK, "node pairs queried");
   int csr_ok = row_ptr[0] == 0 && row_ptr[V] == 2 * ne;
-  for (int64_t i = 0; i < V && csr_ok; ++i)
-    for (int64_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) {
+  int64_t npaired = 0;
+  for (int64_t i = 0; i < V && csr_ok; ++i) {
+    const int64_t p0 = row_ptr[i];
+    /* a paired row: shared A < B, the partner, then the other three ascending */
+    const int paired = mate[i] >= 0;
+    npaired += paired;
+    if (paired) csr_ok &= row_ptr[i + 1] - p0 == 6 && nbr[p0 + 2] == mate[i] && mate[mate[i]] == i;
+    for (int64_t p = p0; p < row_ptr[i + 1]; ++p) {
       csr_ok &= nbr[p] >= 0 && nbr[p] < V && nbr[p] != i;
-      if (p > row_ptr[i]) csr_ok &= nbr[p] > nbr[p - 1];
+      if (p > p0 && !(paired && (p == p0 + 2 || p == p0 + 3))) csr_ok &= nbr[p] > nbr[p - 1];
     }
-  check(csr_ok, "CSR: neighbours in range, ascending, no self loops");
+  }
+  check(csr_ok, "CSR: neighbours in range, ascending (paired rows: shared pair, partner, rest), no self loops");
+  check(npaired > V / 2, "most nodes are paired");
+  free(mate);
 
   int32_t *perm = (int32_t *)malloc(sizeof(int32_t) * (size_t)V);
   char *seen = (char *)calloc((size_t)V, 1);

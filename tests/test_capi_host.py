@@ -265,6 +265,8 @@ def test_new_control_calls_check_their_arguments_on_the_host():
     assert L.nb_probe_fp64_rate(1000, None, None, ctypes.byref(ms)) == nabla.NB_EINVAL
     assert L.nb_method_set_wait_limit(None, 0) == nabla.NB_EINVAL
     assert L.nb_method_set_item_shape(None, 0, -1) == nabla.NB_EINVAL
+    assert L.nb_method_set_node_pairs(None, -1) == nabla.NB_EINVAL
+    assert L.nb_mesh_node_pairs(None, None) == nabla.NB_EINVAL
     assert L.nb_method_set_laplacian_route(None, 0) == nabla.NB_EINVAL
     assert L.nb_check_tile_plan(None, 1, None, None, None, None) == nabla.NB_EINVAL
     m = nabla.Mesh(nabla.Grid(16), 1)
@@ -292,3 +294,45 @@ def test_nb_debug_logs_setup_steps_to_stderr():
     assert quiet.returncode == 0 and loud.returncode == 0
     assert "[nabla_b300]" not in quiet.stderr
     assert "[nabla_b300] mesh: 1600 nodes, 4794 edges, 3196 triangles" in loud.stderr
+
+
+@pytest.mark.parametrize("N,reorder", [(24, 1), (48, 1), (32, 0)])
+def test_node_pairs_are_adjacent_six_neighbour_nodes_with_reordered_rows(N, reorder):
+    """Node pairs (nb_mesh_node_pairs) are mutual, adjacent six-neighbour
+    nodes outside the pole rows at most 16 places apart, with exactly two
+    common neighbours; each paired row starts with those two (ascending),
+    then the partner, then the rest ascending; unpaired rows are ascending.
+    Neighbour sets are checked against the triangles, independently of the
+    CSR."""
+    m = nabla.Mesh(nabla.Grid(N), reorder)
+    rp, nbr = m.csr()
+    mate = m.node_pairs()
+    tri = m.triangles()
+    adj = [set() for _ in range(m.V)]
+    for a, b, c in tri:
+        adj[a] |= {b, c}
+        adj[b] |= {a, c}
+        adj[c] |= {a, b}
+    idx = np.flatnonzero(mate >= 0)
+    assert len(idx) > 0.85 * m.V
+    assert np.array_equal(mate[mate[idx]], idx)
+    assert np.all(idx < m.cap_begin) and np.all(np.abs(mate[idx] - idx) <= 16)
+    for i in range(m.V):
+        row = nbr[rp[i]:rp[i + 1]].tolist()
+        assert set(row) == adj[i] and len(row) == len(adj[i])
+        j = int(mate[i])
+        if j < 0:
+            assert row == sorted(row)
+            continue
+        common = sorted(adj[i] & adj[j])
+        assert len(row) == 6 and len(adj[j]) == 6 and len(common) == 2
+        assert row[:2] == common and row[2] == j and row[3:] == sorted(row[3:])
+    # greedy along the node order: no unpaired six-neighbour node has an
+    # unpaired neighbour it could have been matched with
+    free = set(np.flatnonzero(mate < 0).tolist())
+    for i in free:
+        if i >= m.cap_begin or len(adj[i]) != 6:
+            continue
+        for j in adj[i]:
+            if j in free and j < m.cap_begin and abs(j - i) <= 16 and len(adj[j]) == 6:
+                assert len(adj[i] & adj[j]) != 2, (i, j)

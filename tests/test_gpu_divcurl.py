@@ -163,3 +163,55 @@ def test_item_shapes_give_identical_results(N, nlev):
         meth.set_item_shape(0, -1)
     with pytest.raises(nabla.NablaError):
         meth.set_item_shape(4, 0)
+
+
+@pytest.mark.parametrize("N,nlev", [(32, 137), (48, 91), (24, 37), (16, 16)])
+def test_node_pairs_give_identical_results(N, nlev):
+    """Evaluating both nodes of a node pair in one consumer thread (the
+    default) gives the same bits as evaluating every node alone, for the
+    single div and curl passes and the fused pass and for each item shape:
+    each node's terms are summed in its row order either way (mode 1: pairs
+    in every pass, 0: none, -1: all but the fused pass)."""
+    g, m, meth = product(N)
+    assert (m.node_pairs() >= 0).mean() > 0.8
+    om = oracle_mesh(N)
+    _, uv = inputs(om, nlev, 11, torch.float32)
+    fs = nabla.NodeColumns(meth, nlev, torch.float32)
+    uvd = to_device(fs, uv, m.permutation(), 2)
+    ref = None
+    try:
+        for pairs in (0, 1, -1):
+            meth.set_node_pairs(pairs)
+            for units, aligned in ((2, 0), (3, 1)):
+                meth.set_item_shape(units, aligned)
+                d, z = _fused(meth, fs, uvd)
+                d1, z1 = run_op(meth, fs, "div", uvd), run_op(meth, fs, "curl", uvd)
+                got = [t[:, :nlev].clone() for t in (d, z, d1, z1)]
+                if ref is None:
+                    ref = got
+                assert all(torch.equal(a, b) for a, b in zip(got, ref)), (pairs, units, aligned)
+    finally:
+        meth.set_node_pairs(-1)
+        meth.set_item_shape(0, -1)
+    with pytest.raises(nabla.NablaError):
+        lib = nabla.lib()
+        nabla.check(lib.nb_method_set_node_pairs(meth.handle, 2))
+
+
+@pytest.mark.parametrize("N,nlev", [(32, 137), (24, 37), (16, 16)])
+def test_node_pairs_give_identical_gradients_and_laplacians(N, nlev):
+    """The staged gradient (and the Laplacian built on it) gives the same
+    bits with node pairs on and off."""
+    g, m, meth = product(N)
+    om = oracle_mesh(N)
+    f, _ = inputs(om, nlev, 12, torch.float32)
+    fs = nabla.NodeColumns(meth, nlev, torch.float32)
+    fd = to_device(fs, f, m.permutation(), 1)
+    got = {}
+    try:
+        for pairs in (0, 1):
+            meth.set_node_pairs(pairs)
+            got[pairs] = [run_op(meth, fs, op, fd)[:, :nlev].clone() for op in ("grad", "lap")]
+    finally:
+        meth.set_node_pairs(-1)
+    assert all(torch.equal(a, b) for a, b in zip(got[0], got[1]))
