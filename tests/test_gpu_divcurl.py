@@ -215,3 +215,34 @@ def test_node_pairs_give_identical_gradients_and_laplacians(N, nlev):
     finally:
         meth.set_node_pairs(-1)
     assert all(torch.equal(a, b) for a, b in zip(got[0], got[1]))
+
+
+@pytest.mark.parametrize("tile_nodes", [8, 13, 1024])
+def test_node_pairs_across_tile_boundaries(tile_nodes):
+    """Small tiles cut many node pairs, whose nodes then take single slots
+    in their tiles; large tiles hold long slot lists.  Every staged pass
+    still gives the same bits with pairs in every pass (1) and in none (0)."""
+    N, nlev = 32, 37
+    g, m, meth = product(N)
+    om = oracle_mesh(N)
+    f, uv = inputs(om, nlev, 13, torch.float32)
+    fs = nabla.NodeColumns(meth, nlev, torch.float32)
+    perm = m.permutation()
+    fd, uvd = to_device(fs, f, perm, 1), to_device(fs, uv, perm, 2)
+    got = {}
+    try:
+        meth.set_kernel(nabla.KERNEL_TILED, tile_nodes)
+        for pairs in (0, 1):
+            meth.set_node_pairs(pairs)
+            d, z = _fused(meth, fs, uvd)
+            outs = [run_op(meth, fs, "grad", fd), run_op(meth, fs, "div", uvd), run_op(meth, fs, "curl", uvd),
+                    run_op(meth, fs, "lap", fd), d, z]
+            got[pairs] = [o[:, :nlev].clone() for o in outs]
+    finally:
+        meth.set_kernel(nabla.KERNEL_AUTO, 0)
+        meth.set_node_pairs(-1)
+    assert all(torch.equal(a, b) for a, b in zip(got[0], got[1]))
+    # and the paired results meet the oracle gate
+    for out, op, x in ((got[1][0], "grad", f), (got[1][1], "div", uv), (got[1][3], "lap", f)):
+        ref = oracle_op(om, op, x.astype(np.float64))
+        assert rel_l2(to_grid(out, perm), ref) <= TOL[torch.float32], op
