@@ -586,6 +586,7 @@ def bench_batched(a, nabla, synth, stream):
             "speedup_vs_single_op": round(t_single / t_graph, 3),
             "speedup_vs_fp64": round(t_f64 / t_graph, 3),
             "units": int(info["units"]), "tune_s": round(tune_s, 2),
+            "graph_nodes": int(info["graph_nodes"]), "graph_kernel_nodes": int(info["graph_kernels"]),
             "nodes_per_warp": sorted(set(int(v) for v in info["nodes_per_warp"])),
             "levels_per_block": sorted(set(int(v) for v in info["levels_per_block"]))}
 

@@ -456,6 +456,12 @@ int nb_batch_set_compensated(nb_batch *batch, int on);
 int nb_batch_info(const nb_batch *batch, int64_t *units, int64_t *node_levels,
                   int32_t *nodes_per_warp, int32_t *levels_per_block);
 
+/* Nodes of the batch's captured CUDA graph, and how many of them are kernel
+ * launches (the rest: the counter reset and the events that fork and join
+ * the staged branches); both 0 before the first nb_batch_run or
+ * nb_batch_tune captures it.  Host only.  Errors: NB_EINVAL. */
+int nb_batch_graph_nodes(const nb_batch *batch, int64_t *nodes, int64_t *kernels);
+
 /* ---------------------------------------------------------------- serving
  * Continuous-batching server for derived-field requests (the serving pattern
  * named for this hot path; the paper has no server).  Grids are registered

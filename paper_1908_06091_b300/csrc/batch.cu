@@ -465,6 +465,7 @@ struct nb_batch : nb::RefCounted {
   int comp = 1;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  int64_t graph_nodes = 0, graph_kernels = 0;  // of the captured graph
   int grid = 0;
   ~nb_batch() override {
     if (exec) cudaGraphExecDestroy(exec);
@@ -719,6 +720,17 @@ static int batch_capture(nb_batch *bt) {
   }
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
   bt->graph = g;
+  size_t nn = 0;
+  NB_CUDA(cudaGraphGetNodes(g, nullptr, &nn));
+  std::vector<cudaGraphNode_t> nodes(nn);
+  if (nn) NB_CUDA(cudaGraphGetNodes(g, nodes.data(), &nn));
+  bt->graph_nodes = (int64_t)nn;
+  bt->graph_kernels = 0;
+  for (cudaGraphNode_t node : nodes) {
+    cudaGraphNodeType ty;
+    NB_CUDA(cudaGraphNodeGetType(node, &ty));
+    bt->graph_kernels += ty == cudaGraphNodeTypeKernel;
+  }
   NB_CUDA(cudaGraphInstantiate(&bt->exec, g, 0));
   return NB_OK;
 }
@@ -845,6 +857,16 @@ int nb_batch_info(const nb_batch *b, int64_t *units, int64_t *node_levels, int32
     if (nodes_per_warp) nodes_per_warp[k] = b->shape[k].second;
     if (levels_per_block) levels_per_block[k] = b->shape[k].first;
   }
+  return NB_OK;
+}
+
+int nb_batch_graph_nodes(const nb_batch *b, int64_t *nodes, int64_t *kernels) {
+  if (!b || !nodes || !kernels) {
+    nb::set_error("nb_batch_graph_nodes: NULL argument");
+    return NB_EINVAL;
+  }
+  *nodes = b->graph_nodes;
+  *kernels = b->graph_kernels;
   return NB_OK;
 }
 

@@ -144,6 +144,7 @@ SIGNATURES = {
     "nb_batch_run": [_P, _P],
     "nb_batch_set_compensated": [_P, _I],
     "nb_batch_info": [_P, _I64P, _I64P, _P, _P],
+    "nb_batch_graph_nodes": [_P, _P, _P],
     "nb_server_create": [ctypes.c_int64, _I, _I, ctypes.POINTER(_P)],
     "nb_server_release": [_P],
     "nb_server_add_grid": [_P, _P, _P, _P],
@@ -610,8 +611,10 @@ class Batch(_Handle):
         lpb = np.zeros(self.n, dtype=np.int32)
         check(lib().nb_batch_info(self._h, ctypes.byref(u), ctypes.byref(nl), npw.ctypes.data,
                                   lpb.ctypes.data))
+        gn, gk = ctypes.c_int64(), ctypes.c_int64()
+        check(lib().nb_batch_graph_nodes(self._h, ctypes.byref(gn), ctypes.byref(gk)))
         return {"units": u.value, "node_levels": nl.value, "nodes_per_warp": npw.tolist(),
-                "levels_per_block": lpb.tolist()}
+                "levels_per_block": lpb.tolist(), "graph_nodes": gn.value, "graph_kernels": gk.value}
 
 
 class Server(_Handle):

@@ -266,6 +266,7 @@ def test_new_control_calls_check_their_arguments_on_the_host():
     assert L.nb_method_set_wait_limit(None, 0) == nabla.NB_EINVAL
     assert L.nb_method_set_item_shape(None, 0, -1) == nabla.NB_EINVAL
     assert L.nb_method_set_node_pairs(None, -1) == nabla.NB_EINVAL
+    assert L.nb_batch_graph_nodes(None, None, None) == nabla.NB_EINVAL
     assert L.nb_mesh_node_pairs(None, None) == nabla.NB_EINVAL
     assert L.nb_method_set_laplacian_route(None, 0) == nabla.NB_EINVAL
     assert L.nb_check_tile_plan(None, 1, None, None, None, None) == nabla.NB_EINVAL

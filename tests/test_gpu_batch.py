@@ -134,6 +134,11 @@ def test_large_items_take_the_staged_route_and_match_single_ops():
     torch.cuda.synchronize()
     assert nabla.device_status() == 0
     assert nabla.launch_count() > launches
+    # the captured graph: two persistent phases (the small Laplacian's
+    # gradient and divergence), the staged launches (grad, div, curl and two
+    # for the Laplacian), plus the counter reset and the fork / join
+    g = b.info()
+    assert g["graph_kernels"] == 2 + 3 + 2 and g["graph_nodes"] > g["graph_kernels"]
     for k, ((op, meth, x, out), (N, nlev, _, fs)) in enumerate(zip(items, meta)):
         ref = _single_for_route(meth, fs, op, x, info["levels_per_block"][k])
         torch.cuda.synchronize()
