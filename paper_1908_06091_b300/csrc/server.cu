@@ -69,9 +69,14 @@ __global__ void __launch_bounds__(256) synth_weights_kernel(uint64_t seed, int n
 // operator arithmetic).  A CTA takes kSynthNodes consecutive nodes: it
 // stages the block's mixing weights (transposed, [b][level], zero past nlev)
 // and its nodes' basis values in shared memory.  A lane owns one level of a
-// 32-level chunk (its 8 weights in registers) and a warp walks the nodes, so
-// stores are contiguous and basis loads are broadcasts.  Each level's sum
-// runs b = 0..7 in order.  Levels from nlev up to the padded stride get 0.
+// 32-level chunk (its 8 weights in registers, each duplicated into a packed
+// pair) and a warp walks the nodes, so stores are contiguous and basis loads
+// are broadcasts.  Packed FMAs (__ffma2_rn) carry two sums at once: a wind's
+// (u, v), whose basis values sit side by side; for a scalar, the same level
+// of two consecutive nodes, whose basis values are staged interleaved.
+// Each sum still runs b = 0..7 in order with one rounding per FMA, so the
+// values are those of scalar FMAs.  Levels from nlev up to the padded
+// stride get 0.
 constexpr int kSynthNodes = 64;
 constexpr int kSynthThreads = 256;
 template <class T>
@@ -81,49 +86,64 @@ __global__ void __launch_bounds__(kSynthThreads) synth_fields_kernel(const float
   extern __shared__ __align__(16) float sm[];
   const int lb = (int)(stride / nvar);           // padded levels of the column block
   float *wT = sm;                                // [8][lb]
-  float *bs = sm + 8 * lb;                       // [kSynthNodes][8][nvar]
+  float *bs = sm + 8 * lb;                       // wind [node][8][2]; scalar [node pair][8][2]
   const int64_t n0 = (int64_t)blockIdx.x * kSynthNodes;
   const int nn = (int)min((int64_t)kSynthNodes, V - n0);
   for (int t = threadIdx.x; t < 8 * lb; t += blockDim.x) {
     const int b = t / lb, k = t - b * lb;
     wT[t] = k < nlev ? __ldg(wts + 8 * k + b) : 0.f;
   }
-  for (int t = threadIdx.x; t < nn * 8 * nvar; t += blockDim.x) bs[t] = __ldg(basis + n0 * 8 * nvar + t);
+  if (nvar == 2) {
+    for (int t = threadIdx.x; t < nn * 16; t += blockDim.x) bs[t] = __ldg(basis + n0 * 16 + t);
+  } else {
+    // node i's basis b at (i / 2) * 16 + 2 b + (i & 1); a missing odd node gets 0
+    const int np = (nn + 1) >> 1;
+    for (int t = threadIdx.x; t < np * 16; t += blockDim.x) {
+      const int pr = t >> 4, b = (t >> 1) & 7, i = 2 * pr + (t & 1);
+      bs[t] = i < nn ? __ldg(basis + (n0 + i) * 8 + b) : 0.f;
+    }
+  }
   __syncthreads();
   // lane = level within a 32-level chunk (weights held in registers), warp
-  // = a stride over the CTA's nodes
+  // = a stride over the CTA's nodes (scalar: node pairs)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   for (int k = lane; k - lane < lb; k += 32) {
     if (k >= lb) continue;
-    float w[8];
+    float2 w[8];
 #pragma unroll
-    for (int b = 0; b < 8; ++b) w[b] = wT[b * lb + k];
-    for (int il = warp; il < nn; il += nwarps) {
-      // the node's basis values: 16-byte broadcast loads (bs and each node's
-      // 8 x nvar floats start on 32 bytes)
-      const float4 *bi = reinterpret_cast<const float4 *>(bs + il * 8 * nvar);
-      float acc0 = 0.f, acc1 = 0.f;
-      if (nvar == 1) {
-        const float4 p = bi[0], q = bi[1];
-        const float v[8] = {p.x, p.y, p.z, p.w, q.x, q.y, q.z, q.w};
-#pragma unroll
-        for (int b = 0; b < 8; ++b) acc0 = __fmaf_rn(w[b], v[b], acc0);
-      } else {
+    for (int b = 0; b < 8; ++b) {
+      const float x = wT[b * lb + k];
+      w[b] = make_float2(x, x);
+    }
+    if (nvar == 2) {
+      for (int il = warp; il < nn; il += nwarps) {
+        // the node's (u, v) of bases 2h and 2h + 1: 16-byte broadcast loads
+        const float4 *bi = reinterpret_cast<const float4 *>(bs + il * 16);
+        float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
-          const float4 p = bi[h];  // (u, v) of bases 2h and 2h + 1
-          acc0 = __fmaf_rn(w[2 * h], p.x, acc0);
-          acc1 = __fmaf_rn(w[2 * h], p.y, acc1);
-          acc0 = __fmaf_rn(w[2 * h + 1], p.z, acc0);
-          acc1 = __fmaf_rn(w[2 * h + 1], p.w, acc1);
+          const float4 p = bi[h];
+          acc = __ffma2_rn(w[2 * h], make_float2(p.x, p.y), acc);
+          acc = __ffma2_rn(w[2 * h + 1], make_float2(p.z, p.w), acc);
         }
+        T *o = out + (n0 + il) * stride + (int64_t)k * 2;
+        if constexpr (sizeof(T) == 4) *reinterpret_cast<float2 *>(o) = acc;
+        else *reinterpret_cast<double2 *>(o) = make_double2((double)acc.x, (double)acc.y);
       }
-      T *o = out + (n0 + il) * stride + (int64_t)k * nvar;
-      if (nvar == 2) {
-        if constexpr (sizeof(T) == 4) *reinterpret_cast<float2 *>(o) = make_float2(acc0, acc1);
-        else *reinterpret_cast<double2 *>(o) = make_double2((double)acc0, (double)acc1);
-      } else {
-        o[0] = (T)acc0;
+    } else {
+      for (int ip = warp; 2 * ip < nn; ip += nwarps) {
+        // bases b, b + 1 of nodes 2 ip and 2 ip + 1, interleaved
+        const float4 *bi = reinterpret_cast<const float4 *>(bs + ip * 16);
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          const float4 p = bi[h];
+          acc = __ffma2_rn(w[2 * h], make_float2(p.x, p.y), acc);
+          acc = __ffma2_rn(w[2 * h + 1], make_float2(p.z, p.w), acc);
+        }
+        const int64_t i = n0 + 2 * ip;
+        out[i * stride + k] = (T)acc.x;
+        if (2 * ip + 1 < nn) out[(i + 1) * stride + k] = (T)acc.y;
       }
     }
   }
