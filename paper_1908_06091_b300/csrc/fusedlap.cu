@@ -49,8 +49,7 @@ struct LapArgs {
   int64_t out_stride;
   int nlev;
   int G;
-  uint64_t g_magic;
-  uint32_t g_shift;
+  uint32_t g_magic32;
   // gradient phase
   int Gg;
   uint64_t gg_magic;
@@ -380,7 +379,7 @@ __global__ void __launch_bounds__(kLapThreads, 1)
     v.s = stage + a.off_sd - 8u * (uint32_t)(n0 & ~1);
     v.p = 0u;  // every node alone
     v.npairs = 0;
-    divcurl_tile<COMP, false, KU, false>(a, v, t >= a.ntiles_main, a.g_pitch, warp, W);
+    divcurl_tile<COMP, false, KU, false, 0>(a, v, t >= a.ntiles_main, a.g_pitch, warp, W);
     __syncwarp();
     if (lane == 0) {
       mbar_arrive(emptyb + 8 * s);
@@ -614,7 +613,7 @@ int launch_fused_lap(nb_method *m, const nb_field *f, const nb_field *lap, const
   int KU = 2, G = 0;
   item_shape(m->item_units, m->item_align, (f->nlev + 1) / 2, KU, G);
   a.G = G;
-  magic_div((uint32_t)G, a.g_magic, a.g_shift);
+  a.g_magic32 = magic32((uint32_t)G);
   a.Gg = z.Gg;
   magic_div((uint32_t)z.Gg, a.gg_magic, a.gg_shift);
   a.gout = g ? static_cast<float *>(g->data) : nullptr;

@@ -237,13 +237,16 @@ struct TileView {
 // 14, and each node's sum takes the same terms in the same order as on the
 // single-node path, so the bits are the same.
 //
-// A supplies G, g_magic, g_shift, nlev, the FP64 weights of the pole path
+// A supplies G, g_magic32, nlev, the FP64 weights of the pole path
 // (w64, w64b, s64, s64b), the outputs (out, out2, out_stride), and for the
 // bounds-checked build status and col_area (staged column offsets lie below
 // it); v locates the tile's columns (own node k at v.rows + k rb), staged
 // metadata and slot list; pole tiles run in FP64 (they hold no pairs).
 // PAIRS = false compiles the consumer without the slot list and pair path.
-template <bool COMP, bool FUSED, int KU, bool PAIRS, class A>
+// GC > 0 fixes G at compile time (it must equal a.G): each unit's offset in
+// a column is then a constant the shared-memory loads take as an immediate,
+// instead of an integer add per neighbour and unit.
+template <bool COMP, bool FUSED, int KU, bool PAIRS, int GC, class A>
 __device__ __forceinline__ void divcurl_tile(const A &a, const TileView &v, bool pole, uint32_t rb, int part,
                                              int nparts) {
   const uint32_t n = (uint32_t)(v.n1 - v.n0);
@@ -251,7 +254,7 @@ __device__ __forceinline__ void divcurl_tile(const A &a, const TileView &v, bool
   uint32_t i0, i1;
   warp_share((n - npairs) * (uint32_t)a.G, part, nparts, i0, i1);
   const uint32_t units = (uint32_t)(a.nlev + 1) >> 1;
-  const uint32_t G = (uint32_t)a.G;
+  const uint32_t G = GC > 0 ? (uint32_t)GC : (uint32_t)a.G;
   const uint32_t rs = FUSED ? 16u : 8u;  // bytes of a weight record (and of a self-weight record)
   // weights of staged record `at`: div, and curl when fused
   auto weights = [&](uint32_t at, f2_t &wd, f2_t &wc) {
@@ -265,13 +268,15 @@ __device__ __forceinline__ void divcurl_tile(const A &a, const TileView &v, bool
     return v.rows + (uint32_t)NB_IDX(lds_u32(at), 0, a.col_area, a.status);
   };
   // unit k holds levels 2u, 2u + 1 (u = c + k G)
+  const uint32_t nfull = (uint32_t)a.nlev >> 1;  // units holding two valid levels
   auto put = [&](float *oo, const float (&o)[2 * KU], uint32_t c, const bool (&has)[KU]) {
+    float *ob = oo + 2 * c;
 #pragma unroll
     for (int k = 0; k < KU; ++k) {
       if (!has[k]) continue;
-      const int la = 2 * (int)(c + (uint32_t)k * G);
-      if (la + 1 < a.nlev) __stcs(reinterpret_cast<float2 *>(oo + la), make_float2(o[2 * k], o[2 * k + 1]));
-      else oo[la] = o[2 * k];
+      float *p = ob + 2 * (uint32_t)k * G;
+      if (c + (uint32_t)k * G < nfull) __stcs(reinterpret_cast<float2 *>(p), make_float2(o[2 * k], o[2 * k + 1]));
+      else p[0] = o[2 * k];
     }
   };
   // self terms (su, sv) . (u_i, v_i) of `node`, then the (u, v) halves
@@ -308,7 +313,7 @@ __device__ __forceinline__ void divcurl_tile(const A &a, const TileView &v, bool
       }
   };
   for (uint32_t item = i0 + (threadIdx.x & 31); item < i1; item += 32) {
-    const uint32_t q = (uint32_t)(((uint64_t)item * a.g_magic) >> a.g_shift);
+    const uint32_t q = GC > 0 ? item / (uint32_t)GC : __umulhi(item, a.g_magic32);
     const uint32_t c = item - q * G;
     if (c >= units) continue;  // G * KU may exceed the column's units
     uint32_t il = q, jl = 0;
@@ -535,6 +540,8 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
 EncodeTiledFn encode_fn();  // cuTensorMapEncodeTiled from the driver (NULL if missing)
 // x / d == (x * magic) >> shift for x < 2^24
 void magic_div(uint32_t d, uint64_t &magic, uint32_t &shift);
+// x / d == __umulhi(x, magic32(d)) for 2 <= d and x < 2^32 / d
+uint32_t magic32(uint32_t d);
 int sm_count(int *out);
 // item shape of the div / curl consumers (KU units per item, G items per node)
 void item_shape(int units_req, int align_req, int units, int &KU, int &G);

@@ -59,8 +59,7 @@ struct TiledArgs {
   int64_t out_stride;  // elements
   int nlev;
   int G;               // items per node (4 levels each)
-  uint64_t g_magic;    // item / G == (item * g_magic) >> g_shift, exact for items < 2^24
-  uint32_t g_shift;
+  uint32_t g_magic32;  // item / G == umulhi(item, g_magic32) for item < 2^32 / G (magic32)
   uint32_t copy_bytes; // bytes copied per column: the real data rounded up to 16
   uint32_t gpitch;     // shared-memory pitch of a group of four halo columns
   uint32_t off_w, off_l, off_r;  // stage offsets of the staged weights, offsets, row pointers
@@ -267,7 +266,7 @@ __device__ __forceinline__ void grad_tile(const TiledArgs &a, int t, uint32_t st
     store(node, l0, gx, gy);
   };
   for (uint32_t item = i0 + (threadIdx.x & 31); item < i1; item += 32) {
-    const uint32_t q = (uint32_t)(((uint64_t)item * a.g_magic) >> a.g_shift);
+    const uint32_t q = __umulhi(item, a.g_magic32);
     const uint32_t c = item - q * a.G;
     const int l0 = 4 * (int)c;
     uint32_t il = q, jl = 0;
@@ -417,7 +416,7 @@ __device__ __forceinline__ int tile_at(const TiledArgs &a, int i) {
 // of this CTA's walk into it ("full" barrier, transaction count).  Each of
 // the W consumer warps waits for "full", computes its 1/W share of the
 // tile's items and releases the stage; no block-wide barrier is used.
-template <int OP, bool COMP, int KU, bool PAIRS>
+template <int OP, bool COMP, int KU, bool PAIRS, int GC>
 __global__ void __launch_bounds__(StagedShape<OP>::threads, 1)
     staged_f32(const TiledArgs a, const __grid_constant__ CUtensorMap map) {
   constexpr int W = StagedShape<OP>::warps;
@@ -480,8 +479,8 @@ __global__ void __launch_bounds__(StagedShape<OP>::threads, 1)
     const uint32_t rows = stage0 + (uint32_t)s * a.stage_bytes;
     if (OP == 0) grad_tile<COMP, PAIRS>(a, t, rows, warp, W);
     else if (OP == 1)
-      divcurl_tile<COMP, false, KU, PAIRS>(a, staged_view(a, rows), t >= a.ntiles_main, a.row_bytes, warp, W);
-    else divcurl_tile<COMP, true, KU, PAIRS>(a, staged_view(a, rows), t >= a.ntiles_main, a.row_bytes, warp, W);
+      divcurl_tile<COMP, false, KU, PAIRS, GC>(a, staged_view(a, rows), t >= a.ntiles_main, a.row_bytes, warp, W);
+    else divcurl_tile<COMP, true, KU, PAIRS, GC>(a, staged_view(a, rows), t >= a.ntiles_main, a.row_bytes, warp, W);
     __syncwarp();
     if (lane == 0) mbar_arrive(empty0 + 8 * s);
   }
@@ -619,31 +618,42 @@ void magic_div(uint32_t d, uint64_t &magic, uint32_t &shift) {
   magic = ((1ull << shift) + d - 1) / d;
 }
 
-template <int OP, bool COMP, int KU, bool PAIRS>
+// x / d == umulhi(x, m) with m = ceil(2^32 / d), for 2 <= d and x < 2^32 / d:
+// m = 2^32 / d + e with 0 <= e < 1, so x m / 2^32 = x / d + x e / 2^32, and
+// the excess x e / 2^32 < 1 / d cannot reach the next multiple of 1 / d
+// above x / d.  The staged kernels' items per tile (at most 1024 nodes x
+// d items) stay far below 2^32 / d.
+uint32_t magic32(uint32_t d) { return (uint32_t)(((1ull << 32) + d - 1) / d); }
+
+template <int OP, bool COMP, int KU, bool PAIRS, int GC>
 static int launch_staged_t(const TiledArgs &a, const CUtensorMap &map, int grid, size_t smem,
                            cudaStream_t st) {
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [&] {
-    attr_err = cudaFuncSetAttribute(staged_f32<OP, COMP, KU, PAIRS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    attr_err = cudaFuncSetAttribute(staged_f32<OP, COMP, KU, PAIRS, GC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     227 * 1024);
   });
   NB_CUDA(attr_err);
-  staged_f32<OP, COMP, KU, PAIRS><<<grid, StagedShape<OP>::threads, smem, st>>>(a, map);
+  staged_f32<OP, COMP, KU, PAIRS, GC><<<grid, StagedShape<OP>::threads, smem, st>>>(a, map);
   count_launch(1);
   NB_CUDA(cudaGetLastError());
   return NB_OK;
 }
 
-template <int OP, int KU>
+template <int OP, int KU, int GC = 0>
 static int launch_staged_sel(bool comp, bool pairs, const TiledArgs &a, const CUtensorMap &map, int grid,
                              size_t smem, cudaStream_t st) {
   if (comp)
-    return pairs ? launch_staged_t<OP, true, KU, true>(a, map, grid, smem, st)
-                 : launch_staged_t<OP, true, KU, false>(a, map, grid, smem, st);
-  return pairs ? launch_staged_t<OP, false, KU, true>(a, map, grid, smem, st)
-               : launch_staged_t<OP, false, KU, false>(a, map, grid, smem, st);
+    return pairs ? launch_staged_t<OP, true, KU, true, GC>(a, map, grid, smem, st)
+                 : launch_staged_t<OP, true, KU, false, GC>(a, map, grid, smem, st);
+  return pairs ? launch_staged_t<OP, false, KU, true, GC>(a, map, grid, smem, st)
+               : launch_staged_t<OP, false, KU, false, GC>(a, map, grid, smem, st);
 }
+
+// Items per slot compiled in: 24 is the aligned count of three-unit items
+// for columns of 129 to 144 levels (137 in the benchmark configuration).
+constexpr int kFixedG = 24;
 
 static int g_sm_count = 0;
 
@@ -723,6 +733,7 @@ int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, 
   // units per item (item_shape)
   int KU = 1, G = (in->nlev + 3) / 4;
   if (nvar == 2) item_shape(m->item_units, m->item_align, (in->nlev + 1) / 2, KU, G);
+  if (G < 2) return NB_OK;  // magic32 needs a divisor of at least 2 (nlev >= 16 gives G >= 3)
   // each 16-byte unit must lie inside the staged column
   if ((uint64_t)(nvar == 2 ? (in->nlev + 1) / 2 : G) * 16u > row_bytes) return NB_OK;
   const uint32_t copy_bytes = (uint32_t)(((int64_t)in->nlev * nvar * 4 + 15) / 16 * 16);
@@ -809,7 +820,7 @@ int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, 
   a.out_stride = out->node_stride;
   a.nlev = in->nlev;
   a.G = G;
-  magic_div((uint32_t)a.G, a.g_magic, a.g_shift);
+  a.g_magic32 = magic32((uint32_t)a.G);
   a.copy_bytes = copy_bytes;
   a.gpitch = (4u * copy_bytes + 127u) & ~127u;
   a.off_w = area;
@@ -840,9 +851,13 @@ int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, 
   *handled = true;
   const bool comp = comp_mode < 0 ? m->compensated != 0 : comp_mode != 0;
   if (g) return launch_staged_sel<0, 1>(comp, pairs, a, map, grid, smem, st);
-  if (fused)
+  const bool fixed = KU == 3 && G == kFixedG;
+  if (fused) {
+    if (fixed) return launch_staged_sel<2, 3, kFixedG>(comp, pairs, a, map, grid, smem, st);
     return KU == 3 ? launch_staged_sel<2, 3>(comp, pairs, a, map, grid, smem, st)
                    : launch_staged_sel<2, 2>(comp, pairs, a, map, grid, smem, st);
+  }
+  if (fixed) return launch_staged_sel<1, 3, kFixedG>(comp, pairs, a, map, grid, smem, st);
   return KU == 3 ? launch_staged_sel<1, 3>(comp, pairs, a, map, grid, smem, st)
                  : launch_staged_sel<1, 2>(comp, pairs, a, map, grid, smem, st);
 }
