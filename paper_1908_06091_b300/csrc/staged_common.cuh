@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "kernels_common.cuh"
 
@@ -275,7 +276,10 @@ __device__ __forceinline__ void divcurl_tile(const A &a, const TileView &v, bool
     for (int k = 0; k < KU; ++k) {
       if (!has[k]) continue;
       float *p = ob + 2 * (uint32_t)k * G;
-      if (c + (uint32_t)k * G < nfull) __stcs(reinterpret_cast<float2 *>(p), make_float2(o[2 * k], o[2 * k + 1]));
+      // with G compiled in (more than (KU - 1) G units), every unit but the
+      // last of an item exists and holds two levels
+      if ((GC > 0 && k < KU - 1) || c + (uint32_t)k * G < nfull)
+        __stcs(reinterpret_cast<float2 *>(p), make_float2(o[2 * k], o[2 * k + 1]));
       else p[0] = o[2 * k];
     }
   };
@@ -312,224 +316,231 @@ __device__ __forceinline__ void divcurl_tile(const A &a, const TileView &v, bool
         }
       }
   };
-  for (uint32_t item = i0 + (threadIdx.x & 31); item < i1; item += 32) {
-    const uint32_t q = GC > 0 ? item / (uint32_t)GC : __umulhi(item, a.g_magic32);
-    const uint32_t c = item - q * G;
-    if (c >= units) continue;  // G * KU may exceed the column's units
-    uint32_t il = q, jl = 0;
-    if (PAIRS && v.p) {
-      const uint32_t sl = lds_u32(v.p + 4u * q);
-      il = (uint32_t)NB_IDX(sl & 0xffffu, 0, n, a.status);
-      jl = (uint32_t)NB_IDX(sl >> 16, 0, n, a.status);
-    }
-    // byte offset of each unit in a column; a unit past the column reads
-    // unit c again and is not stored
-    uint32_t uo[KU];
-    bool has[KU];
-#pragma unroll
-    for (int k = 0; k < KU; ++k) {
-      const uint32_t u = c + (uint32_t)k * G;
-      has[k] = u < units;
-      uo[k] = 16u * (has[k] ? u : c);
-    }
-    const int32_t node = v.n0 + (int32_t)il;
-    const uint32_t own = v.rows + il * rb;
-    // terms of the staged neighbour column `col` for a node with own values x
-    auto accumulate = [&](GroupSum<COMP> (&sd)[KU][2], GroupSum<COMP> (&sc)[KU][2], const f2_t (&x)[KU][2],
-                          uint32_t col, f2_t wd, f2_t wc, bool first) {
-#pragma unroll
-      for (int k = 0; k < KU; ++k) {
-        f2_t n0, n1;
-        lds2x64(col + uo[k], n0, n1);
-        const f2_t d0 = sub2(n0, x[k][0]), d1 = sub2(n1, x[k][1]);
-        if (first) {
-          sd[k][0].start(wd, d0);
-          sd[k][1].start(wd, d1);
-          if (FUSED) {
-            sc[k][0].start(wc, d0);
-            sc[k][1].start(wc, d1);
-          }
-        } else {
-          sd[k][0].term(wd, d0);
-          sd[k][1].term(wd, d1);
-          if (FUSED) {
-            sc[k][0].term(wc, d0);
-            sc[k][1].term(wc, d1);
-          }
-        }
+  // the item loop, compiled once for main tiles and once for the pole tiles
+  // (FP64, never pairs); the flag is uniform per tile
+  auto walk = [&](auto pole_tag) {
+    constexpr bool POLE = decltype(pole_tag)::value;
+    for (uint32_t item = i0 + (threadIdx.x & 31); item < i1; item += 32) {
+      const uint32_t q = GC > 0 ? item / (uint32_t)GC : __umulhi(item, a.g_magic32);
+      const uint32_t c = item - q * G;
+      if (GC == 0 && c >= units) continue;  // G * KU may exceed the column's units
+      uint32_t il = q, jl = 0;
+      if (PAIRS && v.p) {
+        const uint32_t sl = lds_u32(v.p + 4u * q);
+        il = (uint32_t)NB_IDX(sl & 0xffffu, 0, n, a.status);
+        jl = (uint32_t)NB_IDX(sl >> 16, 0, n, a.status);
       }
-    };
-    if (PAIRS && q < npairs) {
-      // node pair (il, jl): rows (A, B, partner, three others)
-      const int32_t nodej = v.n0 + (int32_t)jl;
-      const uint32_t pi = (uint32_t)lds_s32(v.r + 4u * (uint32_t)node);
-      const uint32_t pj = (uint32_t)lds_s32(v.r + 4u * (uint32_t)nodej);
-      const uint32_t ownj = v.rows + jl * rb;
-      f2_t xi[KU][2], xj[KU][2];
-#pragma unroll
+      // byte offset of each unit in a column; a unit past the column reads
+      // unit c again and is not stored
+      uint32_t uo[KU];
+      bool has[KU];
+  #pragma unroll
       for (int k = 0; k < KU; ++k) {
-        lds2x64(own + uo[k], xi[k][0], xi[k][1]);
-        lds2x64(ownj + uo[k], xj[k][0], xj[k][1]);
+        const uint32_t u = c + (uint32_t)k * G;
+        has[k] = (GC > 0 && k < KU - 1) || u < units;
+        uo[k] = 16u * (has[k] ? u : c);
       }
-      GroupSum<COMP> sdi[KU][2], sci[KU][2], sdj[KU][2], scj[KU][2];
-      const uint32_t wi = v.w + rs * pi, wj = v.w + rs * pj;
-      const uint32_t li = v.l + 4u * pi, lj = v.l + 4u * pj;
-      // first group of both nodes: the shared neighbours A and B ...
-#pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const uint32_t col = column(li + 4u * e);
-        f2_t wdi, wci, wdj, wcj;
-        weights(wi + rs * e, wdi, wci);
-        weights(wj + rs * e, wdj, wcj);
-#pragma unroll
+      const int32_t node = v.n0 + (int32_t)il;
+      const uint32_t own = v.rows + il * rb;
+      // terms of the staged neighbour column `col` for a node with own values x
+      auto accumulate = [&](GroupSum<COMP> (&sd)[KU][2], GroupSum<COMP> (&sc)[KU][2], const f2_t (&x)[KU][2],
+                            uint32_t col, f2_t wd, f2_t wc, bool first) {
+  #pragma unroll
         for (int k = 0; k < KU; ++k) {
           f2_t n0, n1;
           lds2x64(col + uo[k], n0, n1);
-          const f2_t n[2] = {n0, n1};
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const f2_t di = sub2(n[h], xi[k][h]), dj = sub2(n[h], xj[k][h]);
-            if (e == 0) {
-              sdi[k][h].start(wdi, di);
-              sdj[k][h].start(wdj, dj);
-              if (FUSED) {
-                sci[k][h].start(wci, di);
-                scj[k][h].start(wcj, dj);
-              }
-            } else {
-              sdi[k][h].term(wdi, di);
-              sdj[k][h].term(wdj, dj);
-              if (FUSED) {
-                sci[k][h].term(wci, di);
-                scj[k][h].term(wcj, dj);
-              }
-            }
-          }
-        }
-      }
-      // ... and the partner
-      {
-        f2_t wdi, wci, wdj, wcj;
-        weights(wi + 2u * rs, wdi, wci);
-        weights(wj + 2u * rs, wdj, wcj);
-#pragma unroll
-        for (int k = 0; k < KU; ++k)
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const f2_t d = sub2(xj[k][h], xi[k][h]), nd = make_float2(-d.x, -d.y);
-            sdi[k][h].term(wdi, d);
-            sdj[k][h].term(wdj, nd);
+          const f2_t d0 = sub2(n0, x[k][0]), d1 = sub2(n1, x[k][1]);
+          if (first) {
+            sd[k][0].start(wd, d0);
+            sd[k][1].start(wd, d1);
             if (FUSED) {
-              sci[k][h].term(wci, d);
-              scj[k][h].term(wcj, nd);
+              sc[k][0].start(wc, d0);
+              sc[k][1].start(wc, d1);
+            }
+          } else {
+            sd[k][0].term(wd, d0);
+            sd[k][1].term(wd, d1);
+            if (FUSED) {
+              sc[k][0].term(wc, d0);
+              sc[k][1].term(wc, d1);
             }
           }
-      }
-      close_all(sdi, sci, 0);
-      close_all(sdj, scj, 0);
-      // second group of node i, then of node j
-#pragma unroll
-      for (int e = 3; e < 6; ++e) {
-        f2_t wd, wc;
-        weights(wi + rs * e, wd, wc);
-        accumulate(sdi, sci, xi, column(li + 4u * e), wd, wc, e == 3);
-      }
-      close_all(sdi, sci, 1);
-      {
-        float r[2 * KU], z[2 * KU];
-        finish_node(node, xi, sdi, sci, r, z);
-        put(a.out + (int64_t)node * a.out_stride, r, c, has);
-        if (FUSED) put(a.out2 + (int64_t)node * a.out_stride, z, c, has);
-      }
-#pragma unroll
-      for (int e = 3; e < 6; ++e) {
-        f2_t wd, wc;
-        weights(wj + rs * e, wd, wc);
-        accumulate(sdj, scj, xj, column(lj + 4u * e), wd, wc, e == 3);
-      }
-      close_all(sdj, scj, 1);
-      {
-        float r[2 * KU], z[2 * KU];
-        finish_node(nodej, xj, sdj, scj, r, z);
-        put(a.out + (int64_t)nodej * a.out_stride, r, c, has);
-        if (FUSED) put(a.out2 + (int64_t)nodej * a.out_stride, z, c, has);
-      }
-      continue;
-    }
-    const int32_t p0 = lds_s32(v.r + 4u * (uint32_t)node), p1 = lds_s32(v.r + 4u * (uint32_t)node + 4u);
-    float r[2 * KU], z[2 * KU];
-    if (!pole) {
-      f2_t x[KU][2];  // own (u, v) at levels 2u and 2u + 1 of each unit
-#pragma unroll
-      for (int k = 0; k < KU; ++k) lds2x64(own + uo[k], x[k][0], x[k][1]);
-      GroupSum<COMP> sd[KU][2], sc[KU][2];
-      // weights of entry e: single pass, 8-byte (w.x, w.y) at pw + 8 e; fused,
-      // 16-byte (div, curl) records at pw + 16 e
-      const uint32_t pw = v.w + rs * (uint32_t)p0;
-      const uint32_t pl = v.l + 4u * (uint32_t)p0;
-      // neighbour entry e: its units minus the node's own, times the weights
-      auto nbr = [&](uint32_t e, bool first) {
-        const uint32_t col = column(pl + 4u * e);
-        f2_t wd, wc;
-        weights(pw + rs * e, wd, wc);
-        accumulate(sd, sc, x, col, wd, wc, first);
+        }
       };
-      const int deg = p1 - p0;
-      if (deg == 6) {
-        nbr(0, true), nbr(1, false), nbr(2, false);
-        close_all(sd, sc, 0);
-        nbr(3, true), nbr(4, false), nbr(5, false);
-        close_all(sd, sc, 1);
-      } else {
-        int e = 0;
-        for (; e + 1 < deg; e += 2) {
-          nbr((uint32_t)e, true), nbr((uint32_t)e + 1, false);
-          close_all(sd, sc, e == 0 ? 0 : 2);
-        }
-        if (e < deg) {
-          nbr((uint32_t)e, true);
-          close_all(sd, sc, e == 0 ? 0 : 2);
-        }
-      }
-      finish_node(node, x, sd, sc, r, z);
-    } else {
-      float iu[2 * KU], iv[2 * KU];
-#pragma unroll
-      for (int k = 0; k < KU; ++k) {
-        const float4 x4 = lds128(own + uo[k]);
-        iu[2 * k] = x4.x, iv[2 * k] = x4.y, iu[2 * k + 1] = x4.z, iv[2 * k + 1] = x4.w;
-      }
-      double sacc[2 * KU], zacc[2 * KU];
-#pragma unroll
-      for (int j = 0; j < 2 * KU; ++j) sacc[j] = zacc[j] = 0.0;
-      for (int32_t p = p0; p < p1; ++p) {
-        const double2 w = __ldg(a.w64 + p);
-        const double2 qw = FUSED ? __ldg(a.w64b + p) : w;
-        const uint32_t col = column(v.l + 4u * (uint32_t)p);
-#pragma unroll
+      if (!POLE && PAIRS && q < npairs) {
+        // node pair (il, jl): rows (A, B, partner, three others)
+        const int32_t nodej = v.n0 + (int32_t)jl;
+        const uint32_t pi = (uint32_t)lds_s32(v.r + 4u * (uint32_t)node);
+        const uint32_t pj = (uint32_t)lds_s32(v.r + 4u * (uint32_t)nodej);
+        const uint32_t ownj = v.rows + jl * rb;
+        f2_t xi[KU][2], xj[KU][2];
+  #pragma unroll
         for (int k = 0; k < KU; ++k) {
-          const float4 C = lds128(col + uo[k]);
-          const float ju[2] = {C.x, C.z}, jv[2] = {C.y, C.w};
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const double du = (double)ju[h] - (double)iu[2 * k + h];
-            const double dv = (double)jv[h] - (double)iv[2 * k + h];
-            sacc[2 * k + h] = fma(w.y, dv, fma(w.x, du, sacc[2 * k + h]));
-            if (FUSED) zacc[2 * k + h] = fma(qw.y, dv, fma(qw.x, du, zacc[2 * k + h]));
+          lds2x64(own + uo[k], xi[k][0], xi[k][1]);
+          lds2x64(ownj + uo[k], xj[k][0], xj[k][1]);
+        }
+        GroupSum<COMP> sdi[KU][2], sci[KU][2], sdj[KU][2], scj[KU][2];
+        const uint32_t wi = v.w + rs * pi, wj = v.w + rs * pj;
+        const uint32_t li = v.l + 4u * pi, lj = v.l + 4u * pj;
+        // first group of both nodes: the shared neighbours A and B ...
+  #pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const uint32_t col = column(li + 4u * e);
+          f2_t wdi, wci, wdj, wcj;
+          weights(wi + rs * e, wdi, wci);
+          weights(wj + rs * e, wdj, wcj);
+  #pragma unroll
+          for (int k = 0; k < KU; ++k) {
+            f2_t n0, n1;
+            lds2x64(col + uo[k], n0, n1);
+            const f2_t n[2] = {n0, n1};
+  #pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const f2_t di = sub2(n[h], xi[k][h]), dj = sub2(n[h], xj[k][h]);
+              if (e == 0) {
+                sdi[k][h].start(wdi, di);
+                sdj[k][h].start(wdj, dj);
+                if (FUSED) {
+                  sci[k][h].start(wci, di);
+                  scj[k][h].start(wcj, dj);
+                }
+              } else {
+                sdi[k][h].term(wdi, di);
+                sdj[k][h].term(wdj, dj);
+                if (FUSED) {
+                  sci[k][h].term(wci, di);
+                  scj[k][h].term(wcj, dj);
+                }
+              }
+            }
           }
         }
+        // ... and the partner
+        {
+          f2_t wdi, wci, wdj, wcj;
+          weights(wi + 2u * rs, wdi, wci);
+          weights(wj + 2u * rs, wdj, wcj);
+  #pragma unroll
+          for (int k = 0; k < KU; ++k)
+  #pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const f2_t d = sub2(xj[k][h], xi[k][h]), nd = make_float2(-d.x, -d.y);
+              sdi[k][h].term(wdi, d);
+              sdj[k][h].term(wdj, nd);
+              if (FUSED) {
+                sci[k][h].term(wci, d);
+                scj[k][h].term(wcj, nd);
+              }
+            }
+        }
+        close_all(sdi, sci, 0);
+        close_all(sdj, scj, 0);
+        // second group of node i, then of node j
+  #pragma unroll
+        for (int e = 3; e < 6; ++e) {
+          f2_t wd, wc;
+          weights(wi + rs * e, wd, wc);
+          accumulate(sdi, sci, xi, column(li + 4u * e), wd, wc, e == 3);
+        }
+        close_all(sdi, sci, 1);
+        {
+          float r[2 * KU], z[2 * KU];
+          finish_node(node, xi, sdi, sci, r, z);
+          put(a.out + (int64_t)node * a.out_stride, r, c, has);
+          if (FUSED) put(a.out2 + (int64_t)node * a.out_stride, z, c, has);
+        }
+  #pragma unroll
+        for (int e = 3; e < 6; ++e) {
+          f2_t wd, wc;
+          weights(wj + rs * e, wd, wc);
+          accumulate(sdj, scj, xj, column(lj + 4u * e), wd, wc, e == 3);
+        }
+        close_all(sdj, scj, 1);
+        {
+          float r[2 * KU], z[2 * KU];
+          finish_node(nodej, xj, sdj, scj, r, z);
+          put(a.out + (int64_t)nodej * a.out_stride, r, c, has);
+          if (FUSED) put(a.out2 + (int64_t)nodej * a.out_stride, z, c, has);
+        }
+        continue;
       }
-      const double2 sw = __ldg(a.s64 + node);
-      const double2 sx = FUSED ? __ldg(a.s64b + node) : sw;
-#pragma unroll
-      for (int j = 0; j < 2 * KU; ++j) {
-        r[j] = (float)fma(sw.y, (double)iv[j], fma(sw.x, (double)iu[j], sacc[j]));
-        if (FUSED) z[j] = (float)fma(sx.y, (double)iv[j], fma(sx.x, (double)iu[j], zacc[j]));
+      const int32_t p0 = lds_s32(v.r + 4u * (uint32_t)node), p1 = lds_s32(v.r + 4u * (uint32_t)node + 4u);
+      float r[2 * KU], z[2 * KU];
+      if constexpr (!POLE) {
+        f2_t x[KU][2];  // own (u, v) at levels 2u and 2u + 1 of each unit
+  #pragma unroll
+        for (int k = 0; k < KU; ++k) lds2x64(own + uo[k], x[k][0], x[k][1]);
+        GroupSum<COMP> sd[KU][2], sc[KU][2];
+        // weights of entry e: single pass, 8-byte (w.x, w.y) at pw + 8 e; fused,
+        // 16-byte (div, curl) records at pw + 16 e
+        const uint32_t pw = v.w + rs * (uint32_t)p0;
+        const uint32_t pl = v.l + 4u * (uint32_t)p0;
+        // neighbour entry e: its units minus the node's own, times the weights
+        auto nbr = [&](uint32_t e, bool first) {
+          const uint32_t col = column(pl + 4u * e);
+          f2_t wd, wc;
+          weights(pw + rs * e, wd, wc);
+          accumulate(sd, sc, x, col, wd, wc, first);
+        };
+        const int deg = p1 - p0;
+        if (deg == 6) {
+          nbr(0, true), nbr(1, false), nbr(2, false);
+          close_all(sd, sc, 0);
+          nbr(3, true), nbr(4, false), nbr(5, false);
+          close_all(sd, sc, 1);
+        } else {
+          int e = 0;
+          for (; e + 1 < deg; e += 2) {
+            nbr((uint32_t)e, true), nbr((uint32_t)e + 1, false);
+            close_all(sd, sc, e == 0 ? 0 : 2);
+          }
+          if (e < deg) {
+            nbr((uint32_t)e, true);
+            close_all(sd, sc, e == 0 ? 0 : 2);
+          }
+        }
+        finish_node(node, x, sd, sc, r, z);
+      } else {
+        float iu[2 * KU], iv[2 * KU];
+  #pragma unroll
+        for (int k = 0; k < KU; ++k) {
+          const float4 x4 = lds128(own + uo[k]);
+          iu[2 * k] = x4.x, iv[2 * k] = x4.y, iu[2 * k + 1] = x4.z, iv[2 * k + 1] = x4.w;
+        }
+        double sacc[2 * KU], zacc[2 * KU];
+  #pragma unroll
+        for (int j = 0; j < 2 * KU; ++j) sacc[j] = zacc[j] = 0.0;
+        for (int32_t p = p0; p < p1; ++p) {
+          const double2 w = __ldg(a.w64 + p);
+          const double2 qw = FUSED ? __ldg(a.w64b + p) : w;
+          const uint32_t col = column(v.l + 4u * (uint32_t)p);
+  #pragma unroll
+          for (int k = 0; k < KU; ++k) {
+            const float4 C = lds128(col + uo[k]);
+            const float ju[2] = {C.x, C.z}, jv[2] = {C.y, C.w};
+  #pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const double du = (double)ju[h] - (double)iu[2 * k + h];
+              const double dv = (double)jv[h] - (double)iv[2 * k + h];
+              sacc[2 * k + h] = fma(w.y, dv, fma(w.x, du, sacc[2 * k + h]));
+              if (FUSED) zacc[2 * k + h] = fma(qw.y, dv, fma(qw.x, du, zacc[2 * k + h]));
+            }
+          }
+        }
+        const double2 sw = __ldg(a.s64 + node);
+        const double2 sx = FUSED ? __ldg(a.s64b + node) : sw;
+  #pragma unroll
+        for (int j = 0; j < 2 * KU; ++j) {
+          r[j] = (float)fma(sw.y, (double)iv[j], fma(sw.x, (double)iu[j], sacc[j]));
+          if (FUSED) z[j] = (float)fma(sx.y, (double)iv[j], fma(sx.x, (double)iu[j], zacc[j]));
+        }
       }
+      put(a.out + (int64_t)node * a.out_stride, r, c, has);
+      if (FUSED) put(a.out2 + (int64_t)node * a.out_stride, z, c, has);
     }
-    put(a.out + (int64_t)node * a.out_stride, r, c, has);
-    if (FUSED) put(a.out2 + (int64_t)node * a.out_stride, z, c, has);
-  }
+  };
+  if (pole) walk(std::true_type{});
+  else walk(std::false_type{});
 }
 
 // Host helpers of the staged kernels (tiled.cu).

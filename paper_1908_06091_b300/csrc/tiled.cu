@@ -851,7 +851,9 @@ int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, 
   *handled = true;
   const bool comp = comp_mode < 0 ? m->compensated != 0 : comp_mode != 0;
   if (g) return launch_staged_sel<0, 1>(comp, pairs, a, map, grid, smem, st);
-  const bool fixed = KU == 3 && G == kFixedG;
+  // compiled-in G: the consumers then skip the checks of an item's first
+  // KU - 1 units, which needs more than (KU - 1) G units in a column
+  const bool fixed = KU == 3 && G == kFixedG && (in->nlev + 1) / 2 > (KU - 1) * kFixedG;
   if (fused) {
     if (fixed) return launch_staged_sel<2, 3, kFixedG>(comp, pairs, a, map, grid, smem, st);
     return KU == 3 ? launch_staged_sel<2, 3>(comp, pairs, a, map, grid, smem, st)
