@@ -265,115 +265,122 @@ __device__ __forceinline__ void grad_tile(const TiledArgs &a, int t, uint32_t st
     upk(s.y23.finish(), gy[2], gy[3]);
     store(node, l0, gx, gy);
   };
-  for (uint32_t item = i0 + (threadIdx.x & 31); item < i1; item += 32) {
-    const uint32_t q = __umulhi(item, a.g_magic32);
-    const uint32_t c = item - q * a.G;
-    const int l0 = 4 * (int)c;
-    uint32_t il = q, jl = 0;
-    if (PAIRS && v.p) {
-      const uint32_t sl = lds_u32(v.p + 4u * q);
-      il = (uint32_t)NB_IDX(sl & 0xffffu, 0, n, a.status);
-      jl = (uint32_t)NB_IDX(sl >> 16, 0, n, a.status);
-    }
-    const int32_t node = v.n0 + (int32_t)il;
-    const uint32_t col = v.rows + c * 16u;
-    auto column = [&](uint32_t at) { return col + (uint32_t)NB_IDX(lds_u32(at), 0, a.col_area, a.status); };
-    if (PAIRS && q < npairs) {
-      // node pair (il, jl): rows (A, B, partner, three others)
-      const int32_t nodej = v.n0 + (int32_t)jl;
-      const uint32_t pi = (uint32_t)lds_s32(v.r + 4u * (uint32_t)node);
-      const uint32_t pj = (uint32_t)lds_s32(v.r + 4u * (uint32_t)nodej);
-      f2_t xi01, xi23, xj01, xj23;
-      lds2x64(col + il * rb, xi01, xi23);
-      lds2x64(col + jl * rb, xj01, xj23);
-      Acc si, sj;
-      const uint32_t wi = v.w + 8u * pi, wj = v.w + 8u * pj, li = v.l + 4u * pi, lj = v.l + 4u * pj;
-#pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        f2_t f01, f23;
-        lds2x64(column(li + 4u * e), f01, f23);
-        term(si, lds64(wi + 8u * e), sub2(f01, xi01), sub2(f23, xi23), e == 0);
-        term(sj, lds64(wj + 8u * e), sub2(f01, xj01), sub2(f23, xj23), e == 0);
+  // the item loop, compiled once for main tiles and once for the pole tiles
+  // (FP64, never pairs); the flag is uniform per tile
+  auto walk = [&](auto pole_tag) {
+    constexpr bool POLE = decltype(pole_tag)::value;
+    for (uint32_t item = i0 + (threadIdx.x & 31); item < i1; item += 32) {
+      const uint32_t q = __umulhi(item, a.g_magic32);
+      const uint32_t c = item - q * a.G;
+      const int l0 = 4 * (int)c;
+      uint32_t il = q, jl = 0;
+      if (PAIRS && v.p) {
+        const uint32_t sl = lds_u32(v.p + 4u * q);
+        il = (uint32_t)NB_IDX(sl & 0xffffu, 0, n, a.status);
+        jl = (uint32_t)NB_IDX(sl >> 16, 0, n, a.status);
       }
-      {
-        const f2_t d01 = sub2(xj01, xi01), d23 = sub2(xj23, xi23);
-        term(si, lds64(wi + 16u), d01, d23, false);
-        term(sj, lds64(wj + 16u), make_float2(-d01.x, -d01.y), make_float2(-d23.x, -d23.y), false);
+      const int32_t node = v.n0 + (int32_t)il;
+      const uint32_t col = v.rows + c * 16u;
+      auto column = [&](uint32_t at) { return col + (uint32_t)NB_IDX(lds_u32(at), 0, a.col_area, a.status); };
+      if (!POLE && PAIRS && q < npairs) {
+        // node pair (il, jl): rows (A, B, partner, three others)
+        const int32_t nodej = v.n0 + (int32_t)jl;
+        const uint32_t pi = (uint32_t)lds_s32(v.r + 4u * (uint32_t)node);
+        const uint32_t pj = (uint32_t)lds_s32(v.r + 4u * (uint32_t)nodej);
+        f2_t xi01, xi23, xj01, xj23;
+        lds2x64(col + il * rb, xi01, xi23);
+        lds2x64(col + jl * rb, xj01, xj23);
+        Acc si, sj;
+        const uint32_t wi = v.w + 8u * pi, wj = v.w + 8u * pj, li = v.l + 4u * pi, lj = v.l + 4u * pj;
+  #pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          f2_t f01, f23;
+          lds2x64(column(li + 4u * e), f01, f23);
+          term(si, lds64(wi + 8u * e), sub2(f01, xi01), sub2(f23, xi23), e == 0);
+          term(sj, lds64(wj + 8u * e), sub2(f01, xj01), sub2(f23, xj23), e == 0);
+        }
+        {
+          const f2_t d01 = sub2(xj01, xi01), d23 = sub2(xj23, xi23);
+          term(si, lds64(wi + 16u), d01, d23, false);
+          term(sj, lds64(wj + 16u), make_float2(-d01.x, -d01.y), make_float2(-d23.x, -d23.y), false);
+        }
+        close(si, 0);
+        close(sj, 0);
+  #pragma unroll
+        for (int e = 3; e < 6; ++e) {
+          f2_t f01, f23;
+          lds2x64(column(li + 4u * e), f01, f23);
+          term(si, lds64(wi + 8u * e), sub2(f01, xi01), sub2(f23, xi23), e == 3);
+        }
+        close(si, 1);
+        finish(node, l0, si);
+  #pragma unroll
+        for (int e = 3; e < 6; ++e) {
+          f2_t f01, f23;
+          lds2x64(column(lj + 4u * e), f01, f23);
+          term(sj, lds64(wj + 8u * e), sub2(f01, xj01), sub2(f23, xj23), e == 3);
+        }
+        close(sj, 1);
+        finish(nodej, l0, sj);
+        continue;
       }
-      close(si, 0);
-      close(sj, 0);
-#pragma unroll
-      for (int e = 3; e < 6; ++e) {
-        f2_t f01, f23;
-        lds2x64(column(li + 4u * e), f01, f23);
-        term(si, lds64(wi + 8u * e), sub2(f01, xi01), sub2(f23, xi23), e == 3);
-      }
-      close(si, 1);
-      finish(node, l0, si);
-#pragma unroll
-      for (int e = 3; e < 6; ++e) {
-        f2_t f01, f23;
-        lds2x64(column(lj + 4u * e), f01, f23);
-        term(sj, lds64(wj + 8u * e), sub2(f01, xj01), sub2(f23, xj23), e == 3);
-      }
-      close(sj, 1);
-      finish(nodej, l0, sj);
-      continue;
-    }
-    const int32_t p0 = lds_s32(v.r + 4u * (uint32_t)node), p1 = lds_s32(v.r + 4u * (uint32_t)node + 4u);
-    if (!pole) {
-      f2_t fi01, fi23;
-      lds2x64(col + il * rb, fi01, fi23);
-      Acc s;
-      const uint32_t pw = v.w + 8u * (uint32_t)p0, pl = v.l + 4u * (uint32_t)p0;
-      auto nbr = [&](uint32_t e, bool first) {
-        const float2 w = lds64(pw + 8u * e);
-        f2_t f01, f23;
-        lds2x64(column(pl + 4u * e), f01, f23);
-        term(s, w, sub2(f01, fi01), sub2(f23, fi23), first);
-      };
-      const int deg = p1 - p0;
-      if (deg == 6) {
-        nbr(0, true), nbr(1, false), nbr(2, false);
-        close(s, 0);
-        nbr(3, true), nbr(4, false), nbr(5, false);
-        close(s, 1);
+      const int32_t p0 = lds_s32(v.r + 4u * (uint32_t)node), p1 = lds_s32(v.r + 4u * (uint32_t)node + 4u);
+      if constexpr (!POLE) {
+        f2_t fi01, fi23;
+        lds2x64(col + il * rb, fi01, fi23);
+        Acc s;
+        const uint32_t pw = v.w + 8u * (uint32_t)p0, pl = v.l + 4u * (uint32_t)p0;
+        auto nbr = [&](uint32_t e, bool first) {
+          const float2 w = lds64(pw + 8u * e);
+          f2_t f01, f23;
+          lds2x64(column(pl + 4u * e), f01, f23);
+          term(s, w, sub2(f01, fi01), sub2(f23, fi23), first);
+        };
+        const int deg = p1 - p0;
+        if (deg == 6) {
+          nbr(0, true), nbr(1, false), nbr(2, false);
+          close(s, 0);
+          nbr(3, true), nbr(4, false), nbr(5, false);
+          close(s, 1);
+        } else {
+          int e = 0;
+          for (; e + 1 < deg; e += 2) {
+            nbr((uint32_t)e, true), nbr((uint32_t)e + 1, false);
+            close(s, e == 0 ? 0 : 2);
+          }
+          if (e < deg) {
+            nbr((uint32_t)e, true);
+            close(s, e == 0 ? 0 : 2);
+          }
+        }
+        finish(node, l0, s);
       } else {
-        int e = 0;
-        for (; e + 1 < deg; e += 2) {
-          nbr((uint32_t)e, true), nbr((uint32_t)e + 1, false);
-          close(s, e == 0 ? 0 : 2);
+        const float4 fi = lds128(col + il * rb);
+        double sx[4] = {0, 0, 0, 0}, sy[4] = {0, 0, 0, 0};
+        const float fiv[4] = {fi.x, fi.y, fi.z, fi.w};
+        for (int32_t p = p0; p < p1; ++p) {
+          const double2 w = __ldg(a.w64 + p);
+          const float4 fj = lds128(column(v.l + 4u * (uint32_t)p));
+          const float fjv[4] = {fj.x, fj.y, fj.z, fj.w};
+  #pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const double d = (double)fjv[k] - (double)fiv[k];
+            sx[k] = fma(w.x, d, sx[k]);
+            sy[k] = fma(w.y, d, sy[k]);
+          }
         }
-        if (e < deg) {
-          nbr((uint32_t)e, true);
-          close(s, e == 0 ? 0 : 2);
-        }
-      }
-      finish(node, l0, s);
-    } else {
-      const float4 fi = lds128(col + il * rb);
-      double sx[4] = {0, 0, 0, 0}, sy[4] = {0, 0, 0, 0};
-      const float fiv[4] = {fi.x, fi.y, fi.z, fi.w};
-      for (int32_t p = p0; p < p1; ++p) {
-        const double2 w = __ldg(a.w64 + p);
-        const float4 fj = lds128(column(v.l + 4u * (uint32_t)p));
-        const float fjv[4] = {fj.x, fj.y, fj.z, fj.w};
-#pragma unroll
+        float gx[4], gy[4];
+  #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          const double d = (double)fjv[k] - (double)fiv[k];
-          sx[k] = fma(w.x, d, sx[k]);
-          sy[k] = fma(w.y, d, sy[k]);
+          gx[k] = (float)sx[k];
+          gy[k] = (float)sy[k];
         }
+        store(node, l0, gx, gy);
       }
-      float gx[4], gy[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        gx[k] = (float)sx[k];
-        gy[k] = (float)sy[k];
-      }
-      store(node, l0, gx, gy);
     }
-  }
+  };
+  if (pole) walk(std::true_type{});
+  else walk(std::false_type{});
 }
 
 
