@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <mutex>
 #include <string>
@@ -753,19 +754,13 @@ int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, 
   // ranges, 16-byte aligned).
   const int nstages = m->nstages > 0 ? m->nstages : 2;
   const int stage_kb = m->stage_kb > 0 ? m->stage_kb : 112;
-  // Metadata reservation: a tile holds at most area / row_bytes own nodes;
-  // the plan caps its CSR entries at 7 per such node (tiles are cut earlier
-  // otherwise), so the reservation follows the columns that fit.
+  // Metadata reservation: the plan caps a tile's own nodes at nmax and its
+  // CSR entries at 7 per own node (tiles are cut earlier otherwise), and the
+  // stage reserves that much metadata after the column area.
   auto up16 = [](uint32_t x) { return (x + 15u) & ~15u; };
   const uint32_t stage_target = (uint32_t)stage_kb * 1024u;
   const int nmax_req = m->tile_nodes > 0 ? m->tile_nodes : 256;
-  const int fit_nodes = (int)(stage_target / row_bytes) + 1;
-  const int nmax = std::max(1, std::min(nmax_req, fit_nodes));
-  const int ecap = 7 * nmax + 16;
   const uint32_t rec = fused ? 16u : 8u;  // bytes per weight record and per self-weight record
-  const uint32_t wsz = up16((uint32_t)(ecap + 2) * rec), lsz = up16((uint32_t)(ecap + 8) * 4u),
-                 rsz = up16((uint32_t)(nmax + 8) * 4u);
-  const uint32_t ssz = op == NB_OP_GRAD ? 0u : up16((uint32_t)(nmax + 2) * rec), hsz = 16u;
   // slot list of the node pairs: at most nmax slots plus padding.  By
   // default (-1) every pass but the fused div+curl evaluates node pairs:
   // timed at O1280 x 137, pairs took grad from 2.14 to 2.03 ms and div from
@@ -773,6 +768,37 @@ int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, 
   // fewer registers for a second node (157-168 a thread), ran 3.78 ms with
   // pairs against 3.66 ms without.
   const bool pairs = m->node_pairs > 0 || (m->node_pairs < 0 && !fused);
+  // metadata bytes of a stage for at most nn own nodes
+  auto meta_bytes = [&](int nn) {
+    const int ec = 7 * nn + 16;
+    return up16((uint32_t)(ec + 2) * rec) + up16((uint32_t)(ec + 8) * 4u) + up16((uint32_t)(nn + 8) * 4u) +
+           (op == NB_OP_GRAD ? 0u : up16((uint32_t)(nn + 2) * rec)) + (pairs ? up16((uint32_t)(nn + 4) * 4u) : 0u) +
+           16u;
+  };
+  // Own nodes a tile can reach: a tile of C staged columns has about
+  // 6 sqrt(n) halo columns around its n own nodes (Hilbert tiles of
+  // octahedral meshes; O1280: 45.8 own + 40.1 halo at 87 columns, ~130 +
+  // ~69 at ~200), so n + 6 sqrt(n) = C.  The metadata is reserved for a cap
+  // 25 % above that (a tile reaching it is cut there), C taken from the
+  // column area left by a first reservation, rather than for a stage of own
+  // nodes only: more of the stage holds columns.  Timed at O1280 x 137 for
+  // the vector columns of div and div+curl: 2.26 -> 2.24 and 3.37 -> 3.29 ms;
+  // the scalar columns of grad keep a stage of own nodes (the cap made its
+  // tiles smaller: 2.00 -> 2.02 ms).
+  auto own_cap = [&](double ccols) {
+    const double rn = (-6.0 + std::sqrt(36.0 + 4.0 * ccols)) / 2.0;
+    return std::max(1, std::min((int)(1.25 * rn * rn) + 8, (int)ccols + 1));
+  };
+  int nmax = std::min(nmax_req, (int)(stage_target / row_bytes) + 1);
+  if (nvar == 2) {
+    nmax = std::min(nmax_req, own_cap((double)stage_target / row_bytes));
+    if (stage_target > meta_bytes(nmax))
+      nmax = std::min(nmax_req, own_cap((double)(stage_target - meta_bytes(nmax)) / row_bytes));
+  }
+  const int ecap = 7 * nmax + 16;
+  const uint32_t wsz = up16((uint32_t)(ecap + 2) * rec), lsz = up16((uint32_t)(ecap + 8) * 4u),
+                 rsz = up16((uint32_t)(nmax + 8) * 4u);
+  const uint32_t ssz = op == NB_OP_GRAD ? 0u : up16((uint32_t)(nmax + 2) * rec), hsz = 16u;
   const uint32_t psz = pairs ? up16((uint32_t)(nmax + 4) * 4u) : 0u;
   const uint32_t meta = wsz + lsz + rsz + ssz + psz + hsz;
   if (stage_target <= meta + 4096u) return NB_OK;
