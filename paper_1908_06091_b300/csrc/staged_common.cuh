@@ -265,9 +265,8 @@ __device__ __forceinline__ void divcurl_tile(const A &a, const TileView &v, bool
       wc = make_float2(0.f, 0.f);
     }
   };
-  auto column = [&](uint32_t at) {
-    return v.rows + (uint32_t)NB_IDX(lds_u32(at), 0, a.col_area, a.status);
-  };
+  // a neighbour's staged column offset (relative to v.rows)
+  auto column = [&](uint32_t at) { return (uint32_t)NB_IDX(lds_u32(at), 0, a.col_area, a.status); };
   // unit k holds levels 2u, 2u + 1 (u = c + k G)
   const uint32_t nfull = (uint32_t)a.nlev >> 1;  // units holding two valid levels
   auto put = [&](float *oo, const float (&o)[2 * KU], uint32_t c, const bool (&has)[KU]) {
@@ -341,14 +340,19 @@ __device__ __forceinline__ void divcurl_tile(const A &a, const TileView &v, bool
         uo[k] = 16u * (has[k] ? u : c);
       }
       const int32_t node = v.n0 + (int32_t)il;
-      const uint32_t own = v.rows + il * rb;
+      // unit c of a column at (column offset) + cb; unit k at + rel[k]
+      const uint32_t cb = v.rows + 16u * c;
+      uint32_t rel[KU];
+#pragma unroll
+      for (int k = 0; k < KU; ++k) rel[k] = uo[k] - 16u * c;
+      const uint32_t own = cb + il * rb;
       // terms of the staged neighbour column `col` for a node with own values x
       auto accumulate = [&](GroupSum<COMP> (&sd)[KU][2], GroupSum<COMP> (&sc)[KU][2], const f2_t (&x)[KU][2],
                             uint32_t col, f2_t wd, f2_t wc, bool first) {
   #pragma unroll
         for (int k = 0; k < KU; ++k) {
           f2_t n0, n1;
-          lds2x64(col + uo[k], n0, n1);
+          lds2x64(col + rel[k], n0, n1);
           const f2_t d0 = sub2(n0, x[k][0]), d1 = sub2(n1, x[k][1]);
           if (first) {
             sd[k][0].start(wd, d0);
@@ -372,12 +376,12 @@ __device__ __forceinline__ void divcurl_tile(const A &a, const TileView &v, bool
         const int32_t nodej = v.n0 + (int32_t)jl;
         const uint32_t pi = (uint32_t)lds_s32(v.r + 4u * (uint32_t)node);
         const uint32_t pj = (uint32_t)lds_s32(v.r + 4u * (uint32_t)nodej);
-        const uint32_t ownj = v.rows + jl * rb;
+        const uint32_t ownj = cb + jl * rb;
         f2_t xi[KU][2], xj[KU][2];
   #pragma unroll
         for (int k = 0; k < KU; ++k) {
-          lds2x64(own + uo[k], xi[k][0], xi[k][1]);
-          lds2x64(ownj + uo[k], xj[k][0], xj[k][1]);
+          lds2x64(own + rel[k], xi[k][0], xi[k][1]);
+          lds2x64(ownj + rel[k], xj[k][0], xj[k][1]);
         }
         GroupSum<COMP> sdi[KU][2], sci[KU][2], sdj[KU][2], scj[KU][2];
         const uint32_t wi = v.w + rs * pi, wj = v.w + rs * pj;
@@ -385,14 +389,14 @@ __device__ __forceinline__ void divcurl_tile(const A &a, const TileView &v, bool
         // first group of both nodes: the shared neighbours A and B ...
   #pragma unroll
         for (int e = 0; e < 2; ++e) {
-          const uint32_t col = column(li + 4u * e);
+          const uint32_t col = cb + column(li + 4u * e);
           f2_t wdi, wci, wdj, wcj;
           weights(wi + rs * e, wdi, wci);
           weights(wj + rs * e, wdj, wcj);
   #pragma unroll
           for (int k = 0; k < KU; ++k) {
             f2_t n0, n1;
-            lds2x64(col + uo[k], n0, n1);
+            lds2x64(col + rel[k], n0, n1);
             const f2_t n[2] = {n0, n1};
   #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -440,7 +444,7 @@ __device__ __forceinline__ void divcurl_tile(const A &a, const TileView &v, bool
         for (int e = 3; e < 6; ++e) {
           f2_t wd, wc;
           weights(wi + rs * e, wd, wc);
-          accumulate(sdi, sci, xi, column(li + 4u * e), wd, wc, e == 3);
+          accumulate(sdi, sci, xi, cb + column(li + 4u * e), wd, wc, e == 3);
         }
         close_all(sdi, sci, 1);
         {
@@ -453,7 +457,7 @@ __device__ __forceinline__ void divcurl_tile(const A &a, const TileView &v, bool
         for (int e = 3; e < 6; ++e) {
           f2_t wd, wc;
           weights(wj + rs * e, wd, wc);
-          accumulate(sdj, scj, xj, column(lj + 4u * e), wd, wc, e == 3);
+          accumulate(sdj, scj, xj, cb + column(lj + 4u * e), wd, wc, e == 3);
         }
         close_all(sdj, scj, 1);
         {
@@ -469,7 +473,7 @@ __device__ __forceinline__ void divcurl_tile(const A &a, const TileView &v, bool
       if constexpr (!POLE) {
         f2_t x[KU][2];  // own (u, v) at levels 2u and 2u + 1 of each unit
   #pragma unroll
-        for (int k = 0; k < KU; ++k) lds2x64(own + uo[k], x[k][0], x[k][1]);
+        for (int k = 0; k < KU; ++k) lds2x64(own + rel[k], x[k][0], x[k][1]);
         GroupSum<COMP> sd[KU][2], sc[KU][2];
         // weights of entry e: single pass, 8-byte (w.x, w.y) at pw + 8 e; fused,
         // 16-byte (div, curl) records at pw + 16 e
@@ -477,7 +481,7 @@ __device__ __forceinline__ void divcurl_tile(const A &a, const TileView &v, bool
         const uint32_t pl = v.l + 4u * (uint32_t)p0;
         // neighbour entry e: its units minus the node's own, times the weights
         auto nbr = [&](uint32_t e, bool first) {
-          const uint32_t col = column(pl + 4u * e);
+          const uint32_t col = cb + column(pl + 4u * e);
           f2_t wd, wc;
           weights(pw + rs * e, wd, wc);
           accumulate(sd, sc, x, col, wd, wc, first);
@@ -504,7 +508,7 @@ __device__ __forceinline__ void divcurl_tile(const A &a, const TileView &v, bool
         float iu[2 * KU], iv[2 * KU];
   #pragma unroll
         for (int k = 0; k < KU; ++k) {
-          const float4 x4 = lds128(own + uo[k]);
+          const float4 x4 = lds128(own + rel[k]);
           iu[2 * k] = x4.x, iv[2 * k] = x4.y, iu[2 * k + 1] = x4.z, iv[2 * k + 1] = x4.w;
         }
         double sacc[2 * KU], zacc[2 * KU];
@@ -513,10 +517,10 @@ __device__ __forceinline__ void divcurl_tile(const A &a, const TileView &v, bool
         for (int32_t p = p0; p < p1; ++p) {
           const double2 w = __ldg(a.w64 + p);
           const double2 qw = FUSED ? __ldg(a.w64b + p) : w;
-          const uint32_t col = column(v.l + 4u * (uint32_t)p);
+          const uint32_t col = cb + column(v.l + 4u * (uint32_t)p);
   #pragma unroll
           for (int k = 0; k < KU; ++k) {
-            const float4 C = lds128(col + uo[k]);
+            const float4 C = lds128(col + rel[k]);
             const float ju[2] = {C.x, C.z}, jv[2] = {C.y, C.w};
   #pragma unroll
             for (int h = 0; h < 2; ++h) {
