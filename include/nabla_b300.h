@@ -572,7 +572,7 @@ enum { NB_KERNEL_AUTO = 0, NB_KERNEL_DIRECT = 1, NB_KERNEL_TILED = 2, NB_KERNEL_
 int nb_method_set_kernel(nb_method *method, int variant, int tile_nodes);
 
 /* Pipeline shape of the shared-memory staged kernels: nstages stages of
- * stage_kb KB each (nstages * stage_kb <= 224; 0 = defaults 2 x 112 KB).
+ * stage_kb KB each (nstages * stage_kb <= 226; 0 = defaults 2 x 113 KB).
  * Tile plans are sized so that a tile's own columns plus its halo columns
  * fill one stage. */
 int nb_method_set_staging(nb_method *method, int nstages, int stage_kb);

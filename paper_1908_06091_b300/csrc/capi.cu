@@ -470,8 +470,8 @@ int nb_method_set_kernel(nb_method *m, int variant, int tile_nodes) {
 int nb_method_set_staging(nb_method *m, int nstages, int stage_kb) {
   NB_REQUIRE(m, NB_EINVAL, "nb_method_set_staging: NULL method");
   NB_REQUIRE((nstages == 0 && stage_kb == 0) ||
-                 (nstages >= 2 && nstages <= 8 && stage_kb >= 8 && nstages * stage_kb <= 224),
-             NB_EINVAL, "nb_method_set_staging: need 2 <= nstages <= 8, stage_kb >= 8, product <= 224");
+                 (nstages >= 2 && nstages <= 8 && stage_kb >= 8 && nstages * stage_kb <= 226),
+             NB_EINVAL, "nb_method_set_staging: need 2 <= nstages <= 8, stage_kb >= 8, product <= 226");
   m->nstages = nstages;
   m->stage_kb = stage_kb;
   return NB_OK;

@@ -753,7 +753,10 @@ int launch_tiled(nb_method *m, int op, const nb_field *in, const nb_field *out, 
   // columns, then the tile's weights, offsets and row pointers (bounding
   // ranges, 16-byte aligned).
   const int nstages = m->nstages > 0 ? m->nstages : 2;
-  const int stage_kb = m->stage_kb > 0 ? m->stage_kb : 112;
+  // two stages of 113 KB and their 32 bytes of barriers fill the 227 KB a CTA
+  // may hold (timed at O1280 x 137 against 112 KB: grad 2.00 -> 1.98,
+  // div+curl 3.25 -> 3.23 ms)
+  const int stage_kb = m->stage_kb > 0 ? m->stage_kb : 113;
   // Metadata reservation: the plan caps a tile's own nodes at nmax and its
   // CSR entries at 7 per own node (tiles are cut earlier otherwise), and the
   // stage reserves that much metadata after the column area.
