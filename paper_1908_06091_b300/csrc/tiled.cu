@@ -392,8 +392,9 @@ __device__ __forceinline__ void grad_tile(const TiledArgs &a, int t, uint32_t st
 // thread.
 // The producer also prefetches into L2 the column block of the tile
 // `ahead` steps further along the CTA's walk, so that its stage copy reads
-// L2 instead of HBM (timed: 1-3 % per launch; 1 step for the single
-// operators, 2 for the fused pass).
+// L2 instead of HBM (timed: 1-3 % per launch for the single operators).
+// The fused pass used 2 steps until its tiles grew; at O1280 x 137 it then
+// timed 3.10 ms with 1 step or none against 3.22 with 2 and 3.33 with 3.
 #ifndef NB_GRAD_WARPS
 #define NB_GRAD_WARPS 12
 #endif
@@ -407,7 +408,7 @@ template <int OP>
 struct StagedShape {
   static constexpr int warps = OP == 0 ? NB_GRAD_WARPS : OP == 1 ? NB_DIV_WARPS : NB_DIVCURL_WARPS;
   static constexpr int threads = 32 * (warps + 1);
-  static constexpr int ahead = OP == 2 ? 2 : 1;
+  static constexpr int ahead = 1;
 };
 
 // Tile of the i-th position in the walk: the pole tiles first (FP64 and
