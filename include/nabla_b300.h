@@ -227,6 +227,21 @@ int nb_mesh_tile_plan(const nb_mesh *mesh, int rcap, int nmax, int32_t *ntiles,
 int nb_check_tile_plan(const nb_mesh *mesh, int32_t ntiles, const int32_t *node0, const int32_t *halo_ptr,
                        const int32_t *halo, const uint16_t *lnbr);
 
+/* Host-side check of the slot lists of a staged plan (ntiles tiles over
+ * node0[ntiles + 1]; tile t's slots are slots[slot_ptr[t] ..
+ * slot_ptr[t + 1]), its first npairs[t] of them node pairs): each slot is
+ * own node li | lj << 16 (li == lj for a single node), every own node of a
+ * tile is in exactly one of the tile's first n - npairs[t] slots, slot_ptr
+ * entries are multiples of 4, and each pair holds two mates
+ * (nb_mesh_node_pairs) whose rows have six entries, the same two shared
+ * neighbours first and the partner third.  The library runs the same check
+ * on each staged plan before uploading it.  nslots is the length of the
+ * slots array; the slot ranges are checked against it before any slot is
+ * read.  Host only.  Errors: NB_EINVAL with the first violation in
+ * nb_last_error. */
+int nb_check_slot_lists(const nb_mesh *mesh, int32_t ntiles, const int32_t *node0, const int32_t *slot_ptr,
+                        const int32_t *npairs, const uint32_t *slots, int64_t nslots);
+
 /* Host-side statistics of the tile plan the single-pass Laplacian
  * (NB_LAP_FUSED) builds for FP32 columns of nlev levels at the padded
  * stride: tiles, tiles before the pole-row tiles, the largest number of

@@ -365,6 +365,26 @@ int nb_check_tile_plan(const nb_mesh *m, int32_t ntiles, const int32_t *node0, c
   NB_GUARD_END
 }
 
+int nb_check_slot_lists(const nb_mesh *m, int32_t ntiles, const int32_t *node0, const int32_t *slot_ptr,
+                        const int32_t *npairs, const uint32_t *slots, int64_t nslots) {
+  NB_REQUIRE(m && node0 && slot_ptr && npairs && slots && ntiles >= 1, NB_EINVAL,
+             "nb_check_slot_lists: NULL argument or no tiles");
+  NB_GUARD_BEGIN
+  std::string why;
+  NB_REQUIRE(node0[0] == 0 && node0[ntiles] == m->V, NB_EINVAL, "nb_check_slot_lists: tiles do not cover the nodes");
+  for (int32_t t = 0; t < ntiles; ++t)
+    NB_REQUIRE(node0[t + 1] > node0[t], NB_EINVAL, "nb_check_slot_lists: tiles out of order");
+  // slot ranges inside the caller's array before any slot is read
+  NB_REQUIRE(slot_ptr[0] >= 0 && (int64_t)slot_ptr[ntiles] <= nslots, NB_EINVAL,
+             "nb_check_slot_lists: slot ranges leave the slot array");
+  for (int32_t t = 0; t < ntiles; ++t)
+    NB_REQUIRE(slot_ptr[t + 1] >= slot_ptr[t], NB_EINVAL, "nb_check_slot_lists: slot ranges out of order");
+  const bool ok = nb::check_slot_lists(m, ntiles, node0, slot_ptr, npairs, slots, why);
+  NB_REQUIRE(ok, NB_EINVAL, "nb_check_slot_lists: " + why);
+  return NB_OK;
+  NB_GUARD_END
+}
+
 int nb_mesh_lap_plan(const nb_mesh *m, int nlev, int32_t *ntiles, int32_t *ntiles_main, int32_t *max_gnodes,
                      int32_t *fits) {
   NB_REQUIRE(m && ntiles && ntiles_main && max_gnodes && fits, NB_EINVAL, "nb_mesh_lap_plan: NULL argument");

@@ -103,6 +103,7 @@ SIGNATURES = {
     "nb_mesh_cap_begin": [_P, _I64P],
     "nb_mesh_lap_plan": [_P, _I] + [ctypes.POINTER(ctypes.c_int32)] * 4,
     "nb_check_tile_plan": [_P, ctypes.c_int32, _P, _P, _P, _P],
+    "nb_check_slot_lists": [_P, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_int64],
     "nb_mesh_csr": [_P, _P, _P],
     "nb_mesh_node_pairs": [_P, _P],
     "nb_mesh_tile_plan": [_P, _I, _I, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
@@ -397,6 +398,19 @@ class Mesh(_Handle):
         ln = np.ascontiguousarray(lnbr, dtype=np.uint16)
         check(lib().nb_check_tile_plan(self._h, len(n0) - 1, n0.ctypes.data, hp.ctypes.data, h.ctypes.data,
                                        ln.ctypes.data))
+
+    def check_slot_lists(self, node0, slot_ptr, npairs, slots) -> None:
+        """Raise NablaError unless the slot lists of a staged plan are valid
+        (nb_check_slot_lists)."""
+        n0 = np.ascontiguousarray(node0, dtype=np.int32)
+        sp = np.ascontiguousarray(slot_ptr, dtype=np.int32)
+        npr = np.ascontiguousarray(npairs, dtype=np.int32)
+        sl = np.ascontiguousarray(slots, dtype=np.uint32)
+        n = len(sl)
+        if n == 0:
+            sl = np.zeros(4, dtype=np.uint32)
+        check(lib().nb_check_slot_lists(self._h, len(n0) - 1, n0.ctypes.data, sp.ctypes.data, npr.ctypes.data,
+                                        sl.ctypes.data, n))
 
 
 class Method(_Handle):

@@ -337,3 +337,59 @@ def test_node_pairs_are_adjacent_six_neighbour_nodes_with_reordered_rows(N, reor
         for j in adj[i]:
             if j in free and j < m.cap_begin and abs(j - i) <= 16 and len(adj[j]) == 6:
                 assert len(adj[i] & adj[j]) != 2, (i, j)
+
+
+def _slot_lists(node0, mate):
+    """Slot lists in the format the staged plans use: per tile its pairs of
+    mates that are both own nodes (li | lj << 16), then its other nodes
+    (li | li << 16), each list padded to a multiple of 4."""
+    sptr, npairs, slots = [], [], []
+    for t in range(len(node0) - 1):
+        a, b = int(node0[t]), int(node0[t + 1])
+        sptr.append(len(slots))
+        for k in range(a, b):
+            j = int(mate[k])
+            if k < j < b:
+                slots.append((k - a) | (j - a) << 16)
+        npairs.append(len(slots) - sptr[-1])
+        for k in range(a, b):
+            j = int(mate[k])
+            if not (a <= j < b):
+                slots.append((k - a) * 0x10001)
+        while len(slots) % 4:
+            slots.append(0)
+    sptr.append(len(slots))
+    return (np.array(sptr, dtype=np.int32), np.array(npairs, dtype=np.int32), np.array(slots, dtype=np.uint32))
+
+
+def test_slot_lists_are_checked_on_the_host():
+    """nb_check_slot_lists accepts slot lists built from a tile plan and the
+    node pairs, and refuses each kind of corruption the pair path relies on
+    (NB_EINVAL, nothing launched): a node left out, a pair of non-mates, a
+    pair count beyond the tile's pairs, a slot range past the array."""
+    m = nabla.Mesh(nabla.Grid(24), 1)
+    mate = m.node_pairs()
+    node0, hptr, halo, lnbr, _ = m.tile_plan(rcap=160, nmax=64)
+    sptr, npairs, slots = _slot_lists(node0, mate)
+    assert npairs.sum() > 0.3 * m.V
+    m.check_slot_lists(node0, sptr, npairs, slots)
+    t = int(np.argmax(npairs))  # a tile with pairs
+    q0 = int(sptr[t])
+    cases = {}
+    s = slots.copy()
+    s[q0 + npairs[t]] = s[q0]  # a single slot repeating a pair's node: one node twice, one left out
+    cases["node left out"] = (sptr, npairs, s)
+    s = slots.copy()
+    li, lj = int(s[q0] & 0xFFFF), int(s[q0] >> 16)
+    s[q0] = li | ((lj + 1) % (int(node0[t + 1]) - int(node0[t])) << 16)
+    cases["non-mates"] = (sptr, npairs, s)
+    npr = npairs.copy()
+    npr[t] += 1
+    cases["pair count"] = (sptr, npr, slots)
+    sp = sptr.copy()
+    sp[-1] += 4
+    cases["range"] = (sp, npairs, slots)
+    for what, (a, b, c) in cases.items():
+        with pytest.raises(nabla.NablaError) as ei:
+            m.check_slot_lists(node0, a, b, c)
+        assert ei.value.code == nabla.NB_EINVAL, what
